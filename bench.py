@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of Strassen's block-recursive inversion on GB300.
+
+One step = one inversion of one synthetic matrix through the library's C ABI
+(the whole recursion: leaves, level products, subtractions).  The metric is
+the effective rate 2 n^3 / t (the exact flop count of the method, since the
+six products per level and the 2 L^3 leaves sum to 2 n^3).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--n N --leaf L] [--impl ours|reference]
+
+Workloads:
+  plain_fp64   A = G G^T / n + I (G ~ N(0,1), seeded), n = 32768, leaf 512,
+               every product in FP64 (the plain method at scale).
+  small_fp64   U(-1,1) + n on the diagonal, n = 1024, leaf 128.
+
+With N > 1 (torchrun) every rank inverts its own matrix (independent
+replicas, weak scaling); `value` is the sum of all ranks' flops over the
+slowest rank's time.  `--impl reference` times the CPU oracle on this
+host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2n³/t TFLOP/s vs FP64/BF16 peak at residual ≤1e-10; served req/s with p50/p99"
+SEED_BASE = 0x5EED0000
+
+WORKLOADS = {
+    "plain_fp64": dict(n=32768, leaf=512, precision="fp64", family="spd_gram", seed=SEED_BASE + 1,
+                       desc="plain method, one FP64 SPD matrix A = G G^T/n + I, n = 32768, leaf 512"),
+    "small_fp64": dict(n=1024, leaf=128, precision="fp64", family="sdd", seed=SEED_BASE,
+                       desc="plain method, one FP64 SDD matrix (U(-1,1) + n I), n = 1024, leaf 128"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="plain_fp64", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=0, help="override the order (development runs)")
+    ap.add_argument("--leaf", type=int, default=-1, help="override the leaf order")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--probes", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-json", default="", help="write per-launch records here")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ inputs --
+
+def make_input(w: dict, n: int, device):
+    from paper_1801_04723_gb300 import inputs
+
+    if w["family"] == "spd_gram":
+        return inputs.spd_gram_device(n, w["seed"], device)
+    if w["family"] == "sdd":
+        return inputs.sdd_device(n, w["seed"], device)
+    raise ValueError(w["family"])
+
+
+def freivalds_rel(A, X, k: int, seed: int) -> float:
+    """Relative residual estimate sqrt(mean ||(AX - I) v||^2) / (||A||_F ||X||_F)
+    with k N(0,1) probe vectors (E||Rv||^2 = ||R||_F^2), FP64 on the device."""
+    import torch
+    from paper_1801_04723_gb300 import inputs
+
+    n = A.shape[0]
+    V = inputs.normal_torch(seed, n, k, 0, A.device)
+    R = A @ (X @ V) - V
+    est = math.sqrt(float((R * R).sum()) / k)
+    return est / (float(torch.linalg.norm(A)) * float(torch.linalg.norm(X)))
+
+
+# --------------------------------------------------------------- baseline --
+
+def cpu_baseline(w: dict, seconds_hint: float = 15.0) -> dict:
+    """The oracle, as it stands, on this host's cores: one inversion of a
+    bounded sample of the workload (same family and leaf, smaller order)."""
+    import numpy as np
+
+    import oracle
+    from paper_1801_04723_gb300 import inputs
+
+    n_s = 4096 if w["n"] >= 4096 else w["n"]
+    leaf = min(w["leaf"], n_s)
+    A = inputs.spd_gram(n_s, seed=w["seed"]) if w["family"] == "spd_gram" else inputs.sdd(n_s, seed=w["seed"])
+    oracle.strassen_inv(np.eye(8), 2)  # build / load outside the timing
+    t0 = time.perf_counter()
+    oracle.strassen_inv(A, leaf)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * n_s ** 3 / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"one inversion, n={n_s}, leaf {leaf}, {w['family']} input, "
+                                        f"{dt:.1f} s on {oracle.num_threads()} threads"}
+
+
+def run_reference(args, w: dict, n: int, leaf: int):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1801_04723_gb300 import inputs
+
+    n_s = min(n, 4096)
+    leaf_s = min(leaf, n_s)
+    A = inputs.spd_gram(n_s, seed=w["seed"]) if w["family"] == "spd_gram" else inputs.sdd(n_s, seed=w["seed"])
+    oracle.strassen_inv(np.eye(8), 2)
+    for _ in range(args.warmup):
+        oracle.strassen_inv(A, leaf_s)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.strassen_inv(A, leaf_s)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    val = 2.0 * n_s ** 3 / dt / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "leaf": leaf, "precision": w["precision"],
+                   "sample_n": n_s, "sample_leaf": leaf_s},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"one oracle inversion per step at n={n_s}, leaf {leaf_s} (bounded sample "
+                                   f"of the n={n} workload)"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- ours --
+
+def run_ours(args, w: dict, n: int, leaf: int):
+    import torch
+
+    import paper_1801_04723_gb300 as spin
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=device)
+    spin.build()
+    spin.lib()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    A = make_input(w, n, device)
+    X = torch.empty_like(A)
+    stream = torch.cuda.current_stream()
+    flops = 2.0 * float(n) ** 3
+
+    # warm-up through the host API: each is also an end-to-end measurement
+    # (pinned host buffers, H2D of A and D2H of X inside the call)
+    Ah = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    Ah.copy_(A)
+    Xh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    e2e_times = []
+    for i in range(args.warmup):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        spin.invert_host(Ah.numpy(), leaf=leaf, precision=w["precision"], out=Xh.numpy())
+        e2e_times.append(time.perf_counter() - t0)
+    if args.warmup == 0:
+        spin.invert(A, leaf=leaf, precision=w["precision"], out=X)  # at least one warm call
+    peak_fp64 = spin.probe_fp64_peak()
+
+    with ClockSampler(local) as clk:
+        barrier()
+        spin.profile_start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            spin.invert(A, leaf=leaf, precision=w["precision"], out=X, blocking=False)
+        e1.record(stream)
+        barrier()
+        recs = spin.profile_collect()
+        info = spin.sync(check=False)
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    rel = freivalds_rel(A, X, args.probes, SEED_BASE + 77) if args.probes > 0 else None
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel, from the in-region launch records
+    by_kind: dict = {}
+    for r in recs:
+        d = by_kind.setdefault(r["kind"], {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 0})
+        d["ms"] += r["ms"]
+        d["flops"] += r["flops"]
+        d["bytes"] += r["bytes"]
+        d["launches"] += 1
+    top = max(by_kind, key=lambda k: by_kind[k]["ms"]) if by_kind else None
+    roof = None
+    if top is not None:
+        d = by_kind[top]
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+                "frac": achieved / peak_fp64, "traffic": None,
+                "peak_source": "FP64 FMA rate measured live by spin_probe_fp64_peak on this GPU",
+                "launches": d["launches"], "share_of_step": d["ms"] / (ms * args.steps)}
+    e2e_ok = e2e_times[1:] if len(e2e_times) > 1 else e2e_times
+    e2e_t = statistics.median(e2e_ok) if e2e_ok else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "leaf": leaf, "precision": w["precision"],
+                   "matrices_per_gpu": 1, "parallelism": f"replicas{world}",
+                   "l2": f"inputs larger than L2 ({8 * n * n / 1e9:.1f} GB per matrix)" if n >= 4096 else
+                   "inputs smaller than L2; no flush between steps", "desc": w["desc"]},
+        "clocks": clk.summary(),
+        "e2e": {"value": flops / e2e_t / 1e12 if e2e_t else None, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n * n,
+                "how": "spin_invert_host on pinned host buffers, warm-up steps 2..W, host wall clock"},
+        "gpu_launches": len(recs),
+        "roofline": roof,
+        "status": info["status"],
+        "rel_residual_est": rel,
+        "fp64_peak_tflops": peak_fp64,
+        "frac_of_fp64_peak": value / world / peak_fp64,
+        "kernels": {k: {"launches": v["launches"], "ms": v["ms"], "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9}
+                    for k, v in by_kind.items()},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if args.profile_json:
+        with open(args.profile_json, "w") as f:
+            json.dump(recs, f)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    w = dict(WORKLOADS[args.workload])
+    n = args.n if args.n > 0 else w["n"]
+    leaf = args.leaf if args.leaf >= 0 else w["leaf"]
+    w["n"], w["leaf"] = n, leaf
+    if args.impl == "reference":
+        return run_reference(args, w, n, leaf)
+    return run_ours(args, w, n, leaf)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

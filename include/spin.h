@@ -1,0 +1,220 @@
+/*
+ * spin.h -- C ABI of the GB300 (sm_103a) library for Strassen's
+ * block-recursive matrix inversion (Misra, Haldar, Bhattacharya, Ghosh,
+ * "SPIN: A Fast and Scalable Matrix Inversion Method in Apache Spark",
+ * ICDCN'18, arXiv 1801.04723).
+ *
+ * Problem statement (Sec. 3.1, Algorithm 1; Sec. 3.3, Algorithm 2): given a
+ * square n x n matrix A and a threshold (block size), return C = A^-1.  A is
+ * split into quadrants A11, A12, A21, A22 and
+ *     I = A11^-1, II = A21 I, III = I A12, IV = A21 III, V = IV - A22,
+ *     VI = V^-1, C12 = III VI, C21 = VI II, VII = III C21, C11 = I - VII,
+ *     C22 = -VI,
+ * recursing on A11 and V until the block order reaches the threshold, where
+ * the block is inverted directly.  The method has no pivoting across blocks:
+ * A11 and every Schur complement must be invertible (Sec. 2.1 restricts the
+ * method to positive definite invertible matrices; strictly diagonally
+ * dominant matrices qualify as well).
+ *
+ * Conventions shared by every call:
+ *   - Matrices are FP64, row-major, with a leading dimension (elements
+ *     between consecutive rows) >= the number of columns.  The paper stores
+ *     blocks column-major (Sec. 3.2); since (A^T)^-1 = (A^-1)^T a column-major
+ *     caller passes its buffers unchanged and reads a column-major inverse.
+ *   - Device pointers are CUDA device (or managed) memory of the current
+ *     device, 8-byte aligned.  The caller owns A and X; A is never written.
+ *     A and X must not overlap (the paper's inversion is out of place).
+ *   - Work is enqueued on the given stream (0 = legacy default stream).
+ *   - Return values are spin_status codes.  Argument errors are detected on
+ *     the host before anything is enqueued.  Numerical failure (a zero or
+ *     non-finite pivot in a leaf, i.e. a singular A11 or Schur complement
+ *     somewhere in the recursion) is detected on the device and reported
+ *     through the info record; X is then undefined, but the call never
+ *     returns SPIN_OK with a result it knows to be wrong.
+ *   - Split rule for orders that are not powers of two (the paper treats
+ *     n = 2^p only, Sec. 4): n1 = 32*ceil(n/64) when n > 64, else ceil(n/2);
+ *     n2 = n - n1.  A block is a leaf when its order is <= the leaf size.
+ */
+#ifndef SPIN_H
+#define SPIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* spin_stream_t; /* == cudaStream_t */
+
+typedef enum {
+    SPIN_OK = 0,
+    SPIN_ERR_INVALID_ARG = 1,   /* bad size, leading dimension, pointer or option          */
+    SPIN_ERR_SINGULAR = 2,      /* zero or non-finite leaf pivot (A11 or a Schur complement) */
+    SPIN_ERR_NOT_CONVERGED = 3, /* refinement did not reach the requested residual           */
+    SPIN_ERR_OOM = 4,           /* device memory for the workspace could not be obtained      */
+    SPIN_ERR_CUDA = 5,          /* a CUDA call failed (launch, copy, event)                   */
+    SPIN_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up                         */
+    SPIN_ERR_BUSY = 7,          /* serving: the request is not finished yet                   */
+    SPIN_ERR_NOT_IMPLEMENTED = 8
+} spin_status;
+
+typedef enum {
+    SPIN_FP64 = 0,         /* every product in FP64 (plain method)                           */
+    SPIN_MIXED_BF16X3 = 1, /* products on BF16 tensor cores with 3-term splits, FP32 accumulate,
+                              then Newton-Schulz refinement to opts.tol                       */
+    SPIN_MIXED_TF32 = 2    /* as above with TF32 operands                                     */
+} spin_precision;
+
+/* Options of spin_invert_ex.  Zero-initialise and set what you need;
+ * spin_opts_default() returns the defaults. */
+typedef struct spin_opts {
+    int32_t precision;         /* spin_precision; default SPIN_FP64                            */
+    int32_t leaf;              /* leaf block order; 0 = library choice for this n and precision */
+    double tol;                /* mixed modes: target ||AX-I||_F/(||A||_F||X||_F); default 1e-10 */
+    int32_t max_refine;        /* mixed modes: Newton-Schulz iteration cap; default 6          */
+    int32_t fp64_levels;       /* mixed modes: top recursion levels whose Schur complement
+                                  V = IV - A22 is formed FP64-accurately; default 2            */
+    int32_t blocking;          /* 1: synchronise the stream and fill *info before returning    */
+    int32_t reserved0;
+    void* workspace;           /* optional caller device buffer (>= spin_workspace_bytes);
+                                  NULL: the library uses its own cached per-device buffer     */
+    size_t workspace_bytes;
+} spin_opts;
+
+/* Result record of one inversion. */
+typedef struct spin_info {
+    int32_t status;            /* spin_status of the numerical work                            */
+    int32_t refine_iters;      /* Newton-Schulz iterations taken (mixed modes)                 */
+    int64_t fail_leaf;         /* leaf index (execution order) whose pivot failed, else -1     */
+    int64_t fail_col;          /* pivot column inside that leaf, else -1                       */
+    double rel_residual;       /* last computed ||AX-I||_F/(||A||_F||X||_F); -1 if none        */
+} spin_info;
+
+spin_opts spin_opts_default(void);
+
+/*
+ * spin_invert: X = A^-1 by the plain method (Algorithm 1, every product in
+ * FP64; leaves by Gauss-Jordan with partial pivoting, the paper's "any
+ * approach" leaf, Alg. 1 / Alg. 2 "locInverse").
+ *   A    device, n x n, leading dimension lda >= n, read only.
+ *   X    device, n x n, leading dimension n, written.
+ *   n    order, >= 1.
+ *   leaf leaf block order, 1 <= leaf; 0 = library choice.  leaf >= n inverts
+ *        A directly.
+ * Blocking: returns after the stream has finished the inversion, with the
+ * numerical status (SPIN_OK or SPIN_ERR_SINGULAR) as the return value.
+ * Workspace: the library's cached per-device buffer (grown on demand).
+ */
+int spin_invert(const double* A, double* X, int64_t n, int64_t lda, int leaf, spin_stream_t stream);
+
+/*
+ * spin_invert_ex: the general form.  X (n x n, leading dimension ldx >= n).
+ * opts may be NULL (defaults).  With opts->blocking, or when info is not
+ * NULL, the call synchronises the stream and fills *info; otherwise it
+ * returns once the work is enqueued and spin_sync() reads the status later.
+ * Mixed precisions refine until opts->tol or opts->max_refine.
+ */
+int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n,
+                   const spin_opts* opts, spin_info* info, spin_stream_t stream);
+
+/* Synchronise the stream and fill *info with the status of the latest
+ * non-blocking spin_invert_ex enqueued on it by this thread. */
+int spin_sync(spin_stream_t stream, spin_info* info);
+
+/* Device workspace, in bytes, that spin_invert_ex needs for this order and
+ * these options (the value to pass as opts->workspace_bytes). */
+size_t spin_workspace_bytes(int64_t n, const spin_opts* opts);
+
+/* The leaf order the library picks for n and a precision when leaf = 0. */
+int spin_default_leaf(int64_t n, int precision);
+
+/*
+ * spin_invert_host: X_host = A_host^-1 with both matrices in host memory
+ * (pinned memory gives full copy bandwidth).  Copies A to the device, runs
+ * spin_invert_ex on `stream`, copies X back, synchronises.  Device buffers
+ * are the library's (cached per device).  lda/ldx as above.
+ */
+int spin_invert_host(const double* A_host, int64_t lda, double* X_host, int64_t ldx, int64_t n,
+                     const spin_opts* opts, spin_info* info, spin_stream_t stream);
+
+/* Human-readable name of a spin_status. */
+const char* spin_status_string(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int spin_version(void);
+
+/* Text of the last CUDA failure seen by this thread (SPIN_ERR_CUDA), or "". */
+const char* spin_last_error(void);
+
+/* ---------------------------------------------------------------------
+ * Building blocks, exposed for testing and for callers that compose the
+ * recursion themselves.  All are asynchronous on `stream`.
+ * ------------------------------------------------------------------- */
+
+/*
+ * spin_leaf_inverse: X = A^-1 for one leaf block by Gauss-Jordan with
+ * partial pivoting (largest |a_ik|, lowest row position on ties), the
+ * paper's direct leaf inversion (Alg. 1 "invert A in any approach";
+ * Alg. 2 locInverse).  A: device n x n (lda), X: device n x n (ldx).
+ * info_dev: device int32[4] {status, leaf_index, column, 0}; the first
+ * failure is recorded (status 0 -> SPIN_ERR_SINGULAR) and later ones are
+ * ignored; pass NULL to use the library's slot.  n <= 4096.
+ */
+int spin_leaf_inverse(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n,
+                      int32_t* info_dev, spin_stream_t stream);
+
+/*
+ * spin_gemm_f64: D = beta*C + alpha*(A B) in FP64 (the paper's `multiply`
+ * and `subtract` fused, Sec. 3.3), A m x k (lda), B k x n (ldb),
+ * C and D m x n (ldc, ldd).  alpha in {+1,-1}; beta in {0, 1}; with beta = 0
+ * C is not read (may be NULL).  D may equal C (in-place update) but must not
+ * overlap A or B.
+ */
+int spin_gemm_f64(int64_t m, int64_t n, int64_t k, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb,
+                  double beta, const double* C, int64_t ldc, double* D, int64_t ldd,
+                  spin_stream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Instrumentation: the paper times each method of the recursion
+ * separately (Sec. 5, Table 3: leafNode, multiply, subtract, ...).  With
+ * profiling on, every kernel the library enqueues on the stream is
+ * bracketed by CUDA events and described by one record.
+ * ------------------------------------------------------------------- */
+typedef enum {
+    SPIN_KERNEL_LEAF = 0,      /* Gauss-Jordan leaf inversion                     */
+    SPIN_KERNEL_GEMM_F64 = 1,  /* FP64 fused level product                        */
+    SPIN_KERNEL_GEMM_TC = 2,   /* tensor-core level product (mixed precisions)    */
+    SPIN_KERNEL_SPLIT = 3,     /* FP64 -> low-precision operand split             */
+    SPIN_KERNEL_RESIDUAL = 4,  /* refinement residual R = I - A X                 */
+    SPIN_KERNEL_UPDATE = 5,    /* refinement update X <- X + X R                  */
+    SPIN_KERNEL_OTHER = 6
+} spin_kernel_kind;
+
+typedef struct spin_prof_record {
+    int32_t kind;     /* spin_kernel_kind                                          */
+    int32_t depth;    /* recursion depth of the issuing node (root 0), -1 if none  */
+    int64_t m, n, k;  /* GEMM m x n x k; leaf: m = n = order, k = 0                */
+    double flops;     /* algorithmic flops: 2 m n k per product, 2 L^3 per leaf    */
+    double bytes;     /* algorithmic bytes: operands read once, result written once */
+    double ms;        /* device time between the bracketing events                 */
+} spin_prof_record;
+
+/* Start recording launches on `stream` (up to max_records; older ones are
+ * kept, later ones dropped).  Host-side only; no device work. */
+int spin_profile_start(spin_stream_t stream, int max_records);
+
+/* Synchronise `stream`, stop recording, copy up to `max` records into out
+ * (may be NULL) and the number recorded into *count. */
+int spin_profile_stop(spin_stream_t stream, spin_prof_record* out, int max, int* count);
+
+/* Measure the FP64 FMA throughput of this GPU with a DFMA-bound kernel on
+ * every SM (about 0.1 s); *tflops receives 2 * FMAs / s / 1e12. */
+int spin_probe_fp64_peak(double* tflops, spin_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPIN_H */

@@ -1,0 +1,301 @@
+"""Thin ctypes binding of the C ABI in ``include/spin.h``.
+
+Argument marshalling only: tensors become device pointers and leading
+dimensions, the current torch stream becomes the ``cudaStream_t``.  Every
+step of the inversion runs in the CUDA library; if the library is missing
+the calls raise instead of computing anything elsewhere.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB
+
+SPIN_OK = 0
+SPIN_ERR_INVALID_ARG = 1
+SPIN_ERR_SINGULAR = 2
+SPIN_ERR_NOT_CONVERGED = 3
+SPIN_ERR_NOT_IMPLEMENTED = 8
+
+SPIN_FP64 = 0
+SPIN_MIXED_BF16X3 = 1
+SPIN_MIXED_TF32 = 2
+
+PRECISIONS = {"fp64": SPIN_FP64, "bf16x3": SPIN_MIXED_BF16X3, "tf32": SPIN_MIXED_TF32}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("leaf", ctypes.c_int32),
+        ("tol", ctypes.c_double),
+        ("max_refine", ctypes.c_int32),
+        ("fp64_levels", ctypes.c_int32),
+        ("blocking", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("refine_iters", ctypes.c_int32),
+        ("fail_leaf", ctypes.c_int64),
+        ("fail_col", ctypes.c_int64),
+        ("rel_residual", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ProfRecord(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("depth", ctypes.c_int32),
+        ("m", ctypes.c_int64),
+        ("n", ctypes.c_int64),
+        ("k", ctypes.c_int64),
+        ("flops", ctypes.c_double),
+        ("bytes", ctypes.c_double),
+        ("ms", ctypes.c_double),
+    ]
+
+
+KERNEL_KINDS = {0: "leaf_gj", 1: "gemm_f64", 2: "gemm_tc", 3: "split", 4: "residual", 5: "update", 6: "other"}
+
+
+class SpinError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = status_string(code)
+        if what:
+            msg = f"{what}: {msg}"
+        if code == 5:
+            msg += f" ({last_error()})"
+        super().__init__(msg)
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"CUDA library not built ({LIB}); run paper_1801_04723_gb300.build()")
+        L = ctypes.CDLL(LIB)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        L.spin_opts_default.restype = Opts
+        L.spin_invert.argtypes = [vp, vp, i64, i64, ctypes.c_int, vp]
+        L.spin_invert.restype = ctypes.c_int
+        L.spin_invert_ex.argtypes = [vp, i64, vp, i64, i64, ctypes.POINTER(Opts), ctypes.POINTER(Info), vp]
+        L.spin_invert_ex.restype = ctypes.c_int
+        L.spin_sync.argtypes = [vp, ctypes.POINTER(Info)]
+        L.spin_sync.restype = ctypes.c_int
+        L.spin_workspace_bytes.argtypes = [i64, ctypes.POINTER(Opts)]
+        L.spin_workspace_bytes.restype = ctypes.c_size_t
+        L.spin_default_leaf.argtypes = [i64, ctypes.c_int]
+        L.spin_default_leaf.restype = ctypes.c_int
+        L.spin_invert_host.argtypes = [vp, i64, vp, i64, i64, ctypes.POINTER(Opts), ctypes.POINTER(Info), vp]
+        L.spin_invert_host.restype = ctypes.c_int
+        L.spin_status_string.argtypes = [ctypes.c_int]
+        L.spin_status_string.restype = ctypes.c_char_p
+        L.spin_version.restype = ctypes.c_int
+        L.spin_last_error.restype = ctypes.c_char_p
+        L.spin_leaf_inverse.argtypes = [vp, i64, vp, i64, i64, vp, vp]
+        L.spin_leaf_inverse.restype = ctypes.c_int
+        L.spin_gemm_f64.argtypes = [i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp, i64, vp]
+        L.spin_gemm_f64.restype = ctypes.c_int
+        L.spin_profile_start.argtypes = [vp, ctypes.c_int]
+        L.spin_profile_start.restype = ctypes.c_int
+        L.spin_profile_stop.argtypes = [vp, ctypes.POINTER(ProfRecord), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.spin_profile_stop.restype = ctypes.c_int
+        L.spin_probe_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+        L.spin_probe_fp64_peak.restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def status_string(code: int) -> str:
+    try:
+        return lib().spin_status_string(int(code)).decode()
+    except RuntimeError:
+        return f"status {code}"
+
+
+def last_error() -> str:
+    return lib().spin_last_error().decode()
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _check_matrix(t, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or t.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D float64 CUDA tensor")
+    if t.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major (unit column stride)")
+
+
+def make_opts(precision="fp64", leaf=0, tol=1e-10, max_refine=6, fp64_levels=2, blocking=True,
+              workspace=None) -> Opts:
+    o = lib().spin_opts_default()
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.leaf = int(leaf)
+    o.tol = float(tol)
+    o.max_refine = int(max_refine)
+    o.fp64_levels = int(fp64_levels)
+    o.blocking = 1 if blocking else 0
+    if workspace is not None:
+        o.workspace = ctypes.c_void_p(workspace.data_ptr())
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def invert(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e-10, max_refine: int = 6,
+           fp64_levels: int = 2, stream=None, check: bool = True, workspace=None, blocking: bool = True):
+    """X = A^-1 on the device (spin_invert_ex).  Returns (X, info dict).
+
+    With ``blocking=False`` the call only enqueues the work on the stream and
+    returns (X, None); :func:`sync` reads the status afterwards.  Raises
+    :class:`SpinError` on an argument/CUDA error, and on a numerical failure
+    when ``check``."""
+    import torch
+
+    _check_matrix(A, "A")
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("A must be square")
+    X = out if out is not None else torch.empty((n, n), dtype=torch.float64, device=A.device)
+    _check_matrix(X, "X")
+    o = make_opts(precision, leaf, tol, max_refine, fp64_levels, blocking, workspace)
+    if not blocking:
+        rc = lib().spin_invert_ex(ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(X.data_ptr()),
+                                  X.stride(0), n, ctypes.byref(o), None, _stream(stream))
+        if rc != SPIN_OK:
+            raise SpinError(rc, "spin_invert_ex")
+        return X, None
+    info = Info()
+    rc = lib().spin_invert_ex(ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(X.data_ptr()),
+                              X.stride(0), n, ctypes.byref(o), ctypes.byref(info), _stream(stream))
+    if rc not in (SPIN_OK, SPIN_ERR_SINGULAR, SPIN_ERR_NOT_CONVERGED) or (check and rc != SPIN_OK):
+        raise SpinError(rc, "spin_invert_ex")
+    return X, info.as_dict()
+
+
+def sync(stream=None, check: bool = True) -> dict:
+    """Wait for the stream and return the info of its latest non-blocking
+    inversion (spin_sync)."""
+    info = Info()
+    rc = lib().spin_sync(_stream(stream), ctypes.byref(info))
+    if rc not in (SPIN_OK, SPIN_ERR_SINGULAR, SPIN_ERR_NOT_CONVERGED) or (check and rc != SPIN_OK):
+        raise SpinError(rc, "spin_sync")
+    return info.as_dict()
+
+
+def invert_host(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e-10, stream=None):
+    """X = A^-1 with host (numpy or CPU torch, float64, C-contiguous) buffers."""
+    import numpy as np
+
+    A = np.ascontiguousarray(A, dtype=np.float64) if not hasattr(A, "data_ptr") else A
+    n = A.shape[0]
+    if out is None:
+        out = np.empty((n, n), dtype=np.float64)
+    pa = A.ctypes.data if isinstance(A, np.ndarray) else A.data_ptr()
+    px = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
+    o = make_opts(precision, leaf, tol)
+    info = Info()
+    rc = lib().spin_invert_host(ctypes.c_void_p(pa), n, ctypes.c_void_p(px), n, n, ctypes.byref(o),
+                                ctypes.byref(info), _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_invert_host")
+    return out, info.as_dict()
+
+
+def workspace_bytes(n: int, *, leaf: int = 0, precision="fp64") -> int:
+    o = make_opts(precision, leaf)
+    return int(lib().spin_workspace_bytes(int(n), ctypes.byref(o)))
+
+
+def default_leaf(n: int, precision="fp64") -> int:
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return int(lib().spin_default_leaf(int(n), p))
+
+
+def leaf_inverse(A, out=None, info_dev=None, stream=None):
+    """Gauss-Jordan leaf inversion of one block (spin_leaf_inverse); async."""
+    import torch
+
+    _check_matrix(A, "A")
+    n = A.shape[0]
+    X = out if out is not None else torch.empty((n, n), dtype=torch.float64, device=A.device)
+    pinfo = ctypes.c_void_p(info_dev.data_ptr()) if info_dev is not None else None
+    rc = lib().spin_leaf_inverse(ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(X.data_ptr()),
+                                 X.stride(0), n, pinfo, _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_leaf_inverse")
+    return X
+
+
+def gemm_f64(A, B, *, alpha=1.0, beta=0.0, C=None, out=None, stream=None):
+    """D = beta*C + alpha*(A @ B) in FP64 (spin_gemm_f64); async."""
+    import torch
+
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2
+    D = out if out is not None else torch.empty((m, n), dtype=torch.float64, device=A.device)
+    pc = ctypes.c_void_p(C.data_ptr()) if C is not None else None
+    ldc = C.stride(0) if C is not None else 0
+    rc = lib().spin_gemm_f64(m, n, k, float(alpha), ctypes.c_void_p(A.data_ptr()), A.stride(0),
+                             ctypes.c_void_p(B.data_ptr()), B.stride(0), float(beta), pc, ldc,
+                             ctypes.c_void_p(D.data_ptr()), D.stride(0), _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_gemm_f64")
+    return D
+
+
+def profile_start(max_records: int = 1 << 20, stream=None) -> None:
+    rc = lib().spin_profile_start(_stream(stream), int(max_records))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_profile_start")
+
+
+def profile_collect(stream=None, max_records: int = 1 << 20) -> list[dict]:
+    """Stop recording and return the records (see :func:`profile_stop`)."""
+    buf = (ProfRecord * max_records)()
+    cnt = ctypes.c_int(0)
+    rc = lib().spin_profile_stop(_stream(stream), buf, max_records, ctypes.byref(cnt))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_profile_stop")
+    out = []
+    for i in range(min(cnt.value, max_records)):
+        r = buf[i]
+        out.append({"kind": KERNEL_KINDS.get(r.kind, str(r.kind)), "depth": r.depth, "m": r.m, "n": r.n, "k": r.k,
+                    "flops": r.flops, "bytes": r.bytes, "ms": r.ms})
+    return out
+
+
+def probe_fp64_peak(stream=None) -> float:
+    """FP64 FMA throughput of this GPU in TFLOP/s (DFMA-bound probe kernel)."""
+    v = ctypes.c_double(0.0)
+    rc = lib().spin_probe_fp64_peak(ctypes.byref(v), _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_probe_fp64_peak")
+    return v.value

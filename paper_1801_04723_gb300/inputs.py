@@ -91,20 +91,69 @@ def spd_gram(n: int, seed: int = SEED_BASE + 1, alpha: float = 1.0) -> np.ndarra
     return A
 
 
+# ---- the same counter-based draws with torch (any device, same bits) ----
+
+def _i64(c: int) -> int:
+    """A uint64 constant as the int64 with the same bits."""
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def _srl(z, s: int):
+    """Logical right shift of int64 tensors (torch's >> is arithmetic)."""
+    return (z >> s) & ((1 << (64 - s)) - 1)
+
+
+def splitmix64_torch(seed: int, counters):
+    """Same as :func:`splitmix64` on an int64 torch tensor of counters
+    (int64 arithmetic wraps modulo 2^64, so the bits agree)."""
+    z = counters + 1
+    z = z * _i64(0x9E3779B97F4A7C15) + _i64(seed & 0xFFFFFFFFFFFFFFFF)
+    z = (z ^ _srl(z, 30)) * _i64(0xBF58476D1CE4E5B9)
+    z = (z ^ _srl(z, 27)) * _i64(0x94D049BB133111EB)
+    return z ^ _srl(z, 31)
+
+
+def uniform01_torch(seed: int, counters):
+    return _srl(splitmix64_torch(seed, counters), 11).to(torch.float64) * _TWO53
+
+
+def normal_torch(seed: int, rows: int, cols: int, row0: int, device, dtype=None):
+    """N(0,1) block of rows [row0, row0+rows) of an n x cols matrix drawn as
+    :func:`normal` draws it (Box-Muller on counters 2c, 2c+1, c = i*cols+j).
+    The transcendental functions are torch's, so values may differ from the
+    numpy draw in the last bits; the device inputs are only ever drawn here."""
+    c = torch.arange(row0 * cols, (row0 + rows) * cols, dtype=torch.int64, device=device) * 2
+    u1 = uniform01_torch(seed, c)
+    u2 = uniform01_torch(seed, c + 1)
+    g = torch.sqrt(-2.0 * torch.log1p(-u1)) * torch.cos(2.0 * math.pi * u2)
+    g = g.reshape(rows, cols)
+    return g if dtype is None else g.to(dtype)
+
+
+def sdd_device(n: int, seed: int, device):
+    """:func:`sdd` drawn on the device (bit-identical to the host draw)."""
+    A = torch.empty((n, n), dtype=torch.float64, device=device)
+    step = max(1, (1 << 24) // max(n, 1))
+    for r0 in range(0, n, step):
+        r1 = min(n, r0 + step)
+        c = torch.arange(r0 * n, r1 * n, dtype=torch.int64, device=device)
+        A[r0:r1] = (-1.0 + 2.0 * uniform01_torch(seed, c)).reshape(r1 - r0, n)
+    A.diagonal().add_(float(n))
+    return A
+
+
 def spd_gram_device(n: int, seed: int, device, alpha: float = 1.0, chunk_rows: int = 2048):
-    """Large-n form of :func:`spd_gram`: G is drawn on the host in row chunks
-    (same counters, hence the same G), the product G G^T is formed on the
-    device with torch in FP32 (input preparation only; the inversion never
-    runs here), symmetrised, shifted by alpha I and stored as FP64.  The
-    returned device tensor is the input; host-side checks read its bytes
-    back rather than recomputing it."""
+    """Large-n form of :func:`spd_gram`: G is drawn on the device, the
+    product G G^T is formed there with torch in FP32 (input preparation only;
+    the inversion never runs here), symmetrised, shifted by alpha I and
+    stored as FP64.  The returned device tensor is the input; host-side
+    checks read its bytes back rather than recomputing it."""
     if torch is None:
         raise RuntimeError("torch is required for device-side input generation")
     G = torch.empty((n, n), dtype=torch.float32, device=device)
     for r0 in range(0, n, chunk_rows):
         r1 = min(n, r0 + chunk_rows)
-        blk = normal(seed, (r1 - r0, n), offset=r0 * n).astype(np.float32)
-        G[r0:r1].copy_(torch.from_numpy(blk))
+        G[r0:r1] = normal_torch(seed, r1 - r0, n, r0, device, torch.float32)
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
@@ -115,8 +164,7 @@ def spd_gram_device(n: int, seed: int, device, alpha: float = 1.0, chunk_rows: i
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
     del G
-    # symmetrise by blocks to avoid a second full temporary
-    for r0 in range(0, n, chunk_rows):
+    for r0 in range(0, n, chunk_rows):  # symmetrise block by block
         r1 = min(n, r0 + chunk_rows)
         for c0 in range(r0, n, chunk_rows):
             c1 = min(n, c0 + chunk_rows)

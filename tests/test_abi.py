@@ -1,0 +1,95 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, exports every function ``include/spin.h`` declares, and its
+host logic (defaults, workspace sizing, argument validation) behaves."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1801_04723_gb300 as spin
+from paper_1801_04723_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    spin.build()
+    return binding.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "spin.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(spin_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("spin_invert", "spin_invert_ex", "spin_workspace_bytes", "spin_leaf_inverse", "spin_gemm_f64",
+                 "spin_invert_host", "spin_status_string"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_defaults(L):
+    o = L.spin_opts_default()
+    assert o.precision == 0 and o.leaf == 0 and o.tol == 1e-10 and o.max_refine == 6
+    assert o.fp64_levels == 2 and o.blocking == 1 and o.workspace is None
+    assert L.spin_version() >= 100
+    assert L.spin_status_string(0) == b"SPIN_OK"
+    assert L.spin_status_string(2) == b"SPIN_ERR_SINGULAR"
+
+
+def split(n):
+    return 32 * ((n + 63) // 64) if n > 64 else (n + 1) // 2
+
+
+def ws_elems(n, leaf):
+    if n <= leaf:
+        return n * n if n > 256 else 0
+    n1 = split(n)
+    n2 = n - n1
+    return max(ws_elems(n1, leaf), n1 * n2 + n2 * n2 + ws_elems(n2, leaf))
+
+
+@pytest.mark.parametrize("n,leaf", [(1, 1), (2, 1), (1024, 128), (1000, 64), (777, 100), (32768, 512),
+                                    (8192, 2048), (4096, 4096), (65, 8)])
+def test_workspace_bytes(L, n, leaf):
+    assert spin.workspace_bytes(n, leaf=leaf) == 8 * ws_elems(n, leaf)
+
+
+def test_workspace_power_of_two_is_two_thirds_n2(L):
+    n, leaf = 1 << 14, 1 << 7
+    assert abs(spin.workspace_bytes(n, leaf=leaf) / 8 - 2 * n * n / 3) < n * n / 1000
+
+
+def test_invalid_arguments_rejected_on_host(L):
+    o = binding.make_opts()
+    info = binding.Info()
+    vp = ctypes.c_void_p
+    buf = (ctypes.c_double * 64)()
+    a = vp(ctypes.addressof(buf))
+    x = vp(ctypes.addressof(buf) + 8 * 32)
+    # n < 1, lda < n, NULL pointers, misaligned pointer, negative leaf, overlap, bad precision
+    assert L.spin_invert_ex(a, 4, x, 4, 0, ctypes.byref(o), ctypes.byref(info), None) == 1
+    assert L.spin_invert_ex(a, 3, x, 4, 4, ctypes.byref(o), ctypes.byref(info), None) == 1
+    assert L.spin_invert_ex(None, 4, x, 4, 4, ctypes.byref(o), ctypes.byref(info), None) == 1
+    assert L.spin_invert_ex(vp(ctypes.addressof(buf) + 4), 4, x, 4, 4, ctypes.byref(o), ctypes.byref(info), None) == 1
+    assert L.spin_invert_ex(a, 4, vp(ctypes.addressof(buf) + 8), 4, 4, ctypes.byref(o), ctypes.byref(info), None) == 1
+    o.leaf = -3
+    assert L.spin_invert_ex(a, 4, x, 4, 4, ctypes.byref(o), ctypes.byref(info), None) == 1
+    o.leaf = 0
+    o.precision = 9
+    assert L.spin_invert_ex(a, 4, x, 4, 4, ctypes.byref(o), ctypes.byref(info), None) == 1
+    # gemm: alpha/beta outside {+-1} x {0,1}
+    assert L.spin_gemm_f64(4, 4, 4, 2.0, a, 4, a, 4, 0.0, None, 0, x, 4, None) == 1
+    assert L.spin_gemm_f64(4, 4, 4, 1.0, a, 4, a, 4, 1.0, None, 0, x, 4, None) == 1
+    # leaf order above the supported maximum
+    assert L.spin_leaf_inverse(a, 5000, x, 5000, 5000, None, None) == 1
