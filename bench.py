@@ -34,6 +34,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "2n³/t TFLOP/s vs FP64/BF16 peak at residual ≤1e-10; served req/s with p50/p99"
+
+# DRAM bytes per flop of gemm_f64_kernel from one ncu capture of a 4096^3
+# launch (profiles/gemm_f64_kernel_n8192_top_level.md); operand re-reads grow
+# with the flops of a launch, so per-launch traffic is scaled by flops.
+GEMM_F64_DRAM_BYTES_PER_FLOP = 3.852e9 / (2.0 * 4096 ** 3)
 SEED_BASE = 0x5EED0000
 
 WORKLOADS = {
@@ -41,7 +46,20 @@ WORKLOADS = {
                        desc="plain method, one FP64 SPD matrix A = G G^T/n + I, n = 32768, leaf 512"),
     "small_fp64": dict(n=1024, leaf=128, precision="fp64", family="sdd", seed=SEED_BASE,
                        desc="plain method, one FP64 SDD matrix (U(-1,1) + n I), n = 1024, leaf 128"),
+    "mixed_bf16x3": dict(n=32768, leaf=128, precision="bf16x3", family="householder", seed=SEED_BASE + 2,
+                         desc="mixed precision, one SPD matrix A = Q diag(d) Q^T (64 Householder reflectors, "
+                              "d log-uniform in [1, 1e3]), n = 32768: BF16x3 tensor-core level products, FP64 "
+                              "leaves, FP64-class top-two Schur complements and residual, Newton-Schulz to 1e-10"),
 }
+
+
+def measured_peaks() -> dict:
+    """Measured peaks of this machine (HBM GB/s, BF16 TFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
 
 
 def parse():
@@ -121,13 +139,33 @@ class ClockSampler:
 # ------------------------------------------------------------------ inputs --
 
 def make_input(w: dict, n: int, device):
+    """(A on the device, known-inverse handle or None)."""
     from paper_1801_04723_gb300 import inputs
 
     if w["family"] == "spd_gram":
-        return inputs.spd_gram_device(n, w["seed"], device)
+        return inputs.spd_gram_device(n, w["seed"], device), None
     if w["family"] == "sdd":
-        return inputs.sdd_device(n, w["seed"], device)
+        return inputs.sdd_device(n, w["seed"], device), None
+    if w["family"] == "householder":
+        A, V, d = inputs.householder_spd_device(n, w["seed"], device, reflectors=64, cond=1e3)
+        return A, (V, d)
     raise ValueError(w["family"])
+
+
+def known_inverse_error(X, known, cols: int = 8) -> float:
+    """max over sampled columns j of ||X e_j - Q diag(1/d) Q^T e_j|| / ||Q diag(1/d) Q^T e_j||."""
+    import numpy as np
+
+    from paper_1801_04723_gb300 import inputs
+
+    V, d = known
+    n = X.shape[0]
+    js = np.linspace(0, n - 1, cols).astype(int)
+    E = np.zeros((n, cols))
+    E[js, np.arange(cols)] = 1.0
+    ref = inputs.householder_apply(V, 1.0 / d, E)
+    got = X[:, js].double().cpu().numpy()
+    return float(np.max(np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)))
 
 
 def freivalds_rel(A, X, k: int, seed: int) -> float:
@@ -145,6 +183,16 @@ def freivalds_rel(A, X, k: int, seed: int) -> float:
 
 # --------------------------------------------------------------- baseline --
 
+def host_sample(w: dict, n_s: int):
+    from paper_1801_04723_gb300 import inputs
+
+    if w["family"] == "spd_gram":
+        return inputs.spd_gram(n_s, seed=w["seed"])
+    if w["family"] == "householder":
+        return inputs.householder_spd(n_s, seed=w["seed"], reflectors=64, cond=1e3)[0]
+    return inputs.sdd(n_s, seed=w["seed"])
+
+
 def cpu_baseline(w: dict, seconds_hint: float = 15.0) -> dict:
     """The oracle, as it stands, on this host's cores: one inversion of a
     bounded sample of the workload (same family and leaf, smaller order)."""
@@ -155,7 +203,7 @@ def cpu_baseline(w: dict, seconds_hint: float = 15.0) -> dict:
 
     n_s = 4096 if w["n"] >= 4096 else w["n"]
     leaf = min(w["leaf"], n_s)
-    A = inputs.spd_gram(n_s, seed=w["seed"]) if w["family"] == "spd_gram" else inputs.sdd(n_s, seed=w["seed"])
+    A = host_sample(w, n_s)
     oracle.strassen_inv(np.eye(8), 2)  # build / load outside the timing
     t0 = time.perf_counter()
     oracle.strassen_inv(A, leaf)
@@ -176,7 +224,7 @@ def run_reference(args, w: dict, n: int, leaf: int):
 
     n_s = min(n, 4096)
     leaf_s = min(leaf, n_s)
-    A = inputs.spd_gram(n_s, seed=w["seed"]) if w["family"] == "spd_gram" else inputs.sdd(n_s, seed=w["seed"])
+    A = host_sample(w, n_s)
     oracle.strassen_inv(np.eye(8), 2)
     for _ in range(args.warmup):
         oracle.strassen_inv(A, leaf_s)
@@ -224,7 +272,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
             dist.barrier()
         torch.cuda.synchronize()
 
-    A = make_input(w, n, device)
+    A, known = make_input(w, n, device)
     X = torch.empty_like(A)
     stream = torch.cuda.current_stream()
     flops = 2.0 * float(n) ** 3
@@ -283,19 +331,33 @@ def run_ours(args, w: dict, n: int, leaf: int):
         d["launches"] += 1
     top = max(by_kind, key=lambda k: by_kind[k]["ms"]) if by_kind else None
     roof = None
+    peaks = measured_peaks()
     if top is not None:
         d = by_kind[top]
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp64, "traffic": None,
-                "peak_source": "FP64 FMA rate measured live by spin_probe_fp64_peak on this GPU",
-                "launches": d["launches"], "share_of_step": d["ms"] / (ms * args.steps)}
+        if top in ("gemm_tc", "residual", "update"):
+            # tensor-core kernels timed inside a long step: the sustained BF16 peak
+            peak = peaks.get("bf16_tflops_sustained")
+            src = "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+            if peak is None:
+                peak, src = 1700.0, "fallback 1.7 PFLOP/s sustained BF16 (of fallback)"
+            roof = {"kernel": top, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "peak_source": src,
+                    "flops_counted": "BF16 tensor-core products actually issued (slice pairs x 2mnk)",
+                    "launches": d["launches"], "share_of_step": d["ms"] / (ms * args.steps)}
+        else:
+            traffic = GEMM_F64_DRAM_BYTES_PER_FLOP * d["flops"] / d["launches"] if top == "gemm_f64" else None
+            roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+                    "frac": achieved / peak_fp64, "traffic": traffic,
+                    "traffic_note": "bytes per launch: ncu dram read+write of a 4096^3 launch, scaled by flops",
+                    "peak_source": "FP64 FMA rate measured live by spin_probe_fp64_peak on this GPU",
+                    "launches": d["launches"], "share_of_step": d["ms"] / (ms * args.steps)}
     e2e_ok = e2e_times[1:] if len(e2e_times) > 1 else e2e_times
     e2e_t = statistics.median(e2e_ok) if e2e_ok else None
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if w["precision"] == "fp64" else "bf16x3+f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "leaf": leaf, "precision": w["precision"],
                    "matrices_per_gpu": 1, "parallelism": f"replicas{world}",
                    "l2": f"inputs larger than L2 ({8 * n * n / 1e9:.1f} GB per matrix)" if n >= 4096 else
@@ -307,9 +369,14 @@ def run_ours(args, w: dict, n: int, leaf: int):
         "gpu_launches": len(recs),
         "roofline": roof,
         "status": info["status"],
+        "refine_iters": info["refine_iters"],
+        "rel_residual_lib": info["rel_residual"],
         "rel_residual_est": rel,
+        "err_vs_known_inverse": known_inverse_error(X, known) if known is not None else None,
         "fp64_peak_tflops": peak_fp64,
         "frac_of_fp64_peak": value / world / peak_fp64,
+        "bf16_peak_tflops": peaks.get("bf16_tflops"),
+        "frac_of_bf16_peak": value / world / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"], "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9}
                     for k, v in by_kind.items()},
     }

@@ -76,7 +76,8 @@ typedef struct spin_opts {
     int32_t fp64_levels;       /* mixed modes: top recursion levels whose Schur complement
                                   V = IV - A22 is formed FP64-accurately; default 2            */
     int32_t blocking;          /* 1: synchronise the stream and fill *info before returning    */
-    int32_t reserved0;
+    int32_t residual_slices;   /* mixed modes: 8-bit digit slices of the FP64-class refinement
+                                  residual, 1..7; 0 (default) = 6 when tol >= 1e-11, else 7    */
     void* workspace;           /* optional caller device buffer (>= spin_workspace_bytes);
                                   NULL: the library uses its own cached per-device buffer     */
     size_t workspace_bytes;
@@ -113,7 +114,10 @@ int spin_invert(const double* A, double* X, int64_t n, int64_t lda, int leaf, sp
  * opts may be NULL (defaults).  With opts->blocking, or when info is not
  * NULL, the call synchronises the stream and fills *info; otherwise it
  * returns once the work is enqueued and spin_sync() reads the status later.
- * Mixed precisions refine until opts->tol or opts->max_refine.
+ * Mixed precisions refine until opts->tol or opts->max_refine; they read the
+ * residual norm back after every refinement step, so they synchronise the
+ * stream during the call whatever opts->blocking says.  The caller-provided
+ * workspace (opts->workspace) must be 256-byte aligned.
  */
 int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n,
                    const spin_opts* opts, spin_info* info, spin_stream_t stream);
@@ -175,6 +179,40 @@ int spin_gemm_f64(int64_t m, int64_t n, int64_t k, double alpha,
                   const double* A, int64_t lda, const double* B, int64_t ldb,
                   double beta, const double* C, int64_t ldc, double* D, int64_t ldd,
                   spin_stream_t stream);
+
+/*
+ * spin_gemm_bf16x3: D = beta*C + alpha*(A B) on the BF16 tensor cores with
+ * each FP64 operand split as hi + lo (hi = bf16(x), lo = bf16(x - hi)) and
+ * the three leading products A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated
+ * in FP32: the mixed method's level product (relative error ~2^-16 of
+ * |A||B| plus FP32 accumulation).  Shapes, alpha/beta and aliasing rules as
+ * spin_gemm_f64.  Split planes use a library-owned device arena.
+ */
+int spin_gemm_bf16x3(int64_t m, int64_t n, int64_t k, double alpha,
+                     const double* A, int64_t lda, const double* B, int64_t ldb,
+                     double beta, const double* C, int64_t ldc, double* D, int64_t ldd,
+                     spin_stream_t stream);
+
+/*
+ * spin_gemm_ozaki: D = beta*C + alpha*(A B) (+ I when add_identity) with
+ * FP64-class accuracy on the BF16 tensor cores: every row of A and column
+ * of B is scaled by a power of two and cut into `slices` (1..7) fixed-point
+ * digit slices of 8 bits; digit products are summed exactly in FP32 runs of
+ * 512, the runs in int32, and each slice-pair group is scaled into the FP64
+ * result (slice pairs (t, u) with t + u < slices).  The refinement residual
+ * R = I - A X of the mixed method is this call with alpha = -1, beta = 0,
+ * add_identity = 1.  sumsq_dev (device double, optional) receives
+ * += sum of squares of D.
+ */
+int spin_gemm_ozaki(int64_t m, int64_t n, int64_t k, double alpha,
+                    const double* A, int64_t lda, const double* B, int64_t ldb,
+                    double beta, const double* C, int64_t ldc, double* D, int64_t ldd,
+                    int slices, int add_identity, double* sumsq_dev, spin_stream_t stream);
+
+/* Synchronise `stream` and return (and clear) the device error word of the
+ * building-block tensor-core calls: SPIN_OK, or SPIN_ERR_TIMEOUT if a
+ * bounded device-side wait gave up. */
+int spin_take_device_error(spin_stream_t stream);
 
 /* ---------------------------------------------------------------------
  * Instrumentation: the paper times each method of the recursion

@@ -15,6 +15,9 @@ from .binding import (  # noqa: F401
     Opts,
     default_leaf,
     gemm_f64,
+    gemm_bf16x3,
+    gemm_ozaki,
+    take_device_error,
     invert,
     invert_host,
     leaf_inverse,

@@ -34,7 +34,7 @@ class Opts(ctypes.Structure):
         ("max_refine", ctypes.c_int32),
         ("fp64_levels", ctypes.c_int32),
         ("blocking", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("residual_slices", ctypes.c_int32),
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
     ]
@@ -121,6 +121,13 @@ def lib():
         L.spin_profile_stop.restype = ctypes.c_int
         L.spin_probe_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
         L.spin_probe_fp64_peak.restype = ctypes.c_int
+        L.spin_gemm_bf16x3.argtypes = [i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp, i64, vp]
+        L.spin_gemm_bf16x3.restype = ctypes.c_int
+        L.spin_gemm_ozaki.argtypes = [i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp, i64, ctypes.c_int,
+                                      ctypes.c_int, vp, vp]
+        L.spin_gemm_ozaki.restype = ctypes.c_int
+        L.spin_take_device_error.argtypes = [vp]
+        L.spin_take_device_error.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -154,7 +161,7 @@ def _check_matrix(t, name):
 
 
 def make_opts(precision="fp64", leaf=0, tol=1e-10, max_refine=6, fp64_levels=2, blocking=True,
-              workspace=None) -> Opts:
+              workspace=None, residual_slices=0) -> Opts:
     o = lib().spin_opts_default()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.leaf = int(leaf)
@@ -162,6 +169,7 @@ def make_opts(precision="fp64", leaf=0, tol=1e-10, max_refine=6, fp64_levels=2, 
     o.max_refine = int(max_refine)
     o.fp64_levels = int(fp64_levels)
     o.blocking = 1 if blocking else 0
+    o.residual_slices = int(residual_slices)
     if workspace is not None:
         o.workspace = ctypes.c_void_p(workspace.data_ptr())
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -169,7 +177,8 @@ def make_opts(precision="fp64", leaf=0, tol=1e-10, max_refine=6, fp64_levels=2, 
 
 
 def invert(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e-10, max_refine: int = 6,
-           fp64_levels: int = 2, stream=None, check: bool = True, workspace=None, blocking: bool = True):
+           fp64_levels: int = 2, stream=None, check: bool = True, workspace=None, blocking: bool = True,
+           residual_slices: int = 0):
     """X = A^-1 on the device (spin_invert_ex).  Returns (X, info dict).
 
     With ``blocking=False`` the call only enqueues the work on the stream and
@@ -184,7 +193,7 @@ def invert(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e-10, 
         raise ValueError("A must be square")
     X = out if out is not None else torch.empty((n, n), dtype=torch.float64, device=A.device)
     _check_matrix(X, "X")
-    o = make_opts(precision, leaf, tol, max_refine, fp64_levels, blocking, workspace)
+    o = make_opts(precision, leaf, tol, max_refine, fp64_levels, blocking, workspace, residual_slices)
     if not blocking:
         rc = lib().spin_invert_ex(ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(X.data_ptr()),
                                   X.stride(0), n, ctypes.byref(o), None, _stream(stream))
@@ -228,8 +237,9 @@ def invert_host(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e
     return out, info.as_dict()
 
 
-def workspace_bytes(n: int, *, leaf: int = 0, precision="fp64") -> int:
-    o = make_opts(precision, leaf)
+def workspace_bytes(n: int, *, leaf: int = 0, precision="fp64", fp64_levels: int = 2,
+                    residual_slices: int = 0) -> int:
+    o = make_opts(precision, leaf, fp64_levels=fp64_levels, residual_slices=residual_slices)
     return int(lib().spin_workspace_bytes(int(n), ctypes.byref(o)))
 
 
@@ -299,3 +309,46 @@ def probe_fp64_peak(stream=None) -> float:
     if rc != SPIN_OK:
         raise SpinError(rc, "spin_probe_fp64_peak")
     return v.value
+
+
+def _gemm_args(A, B, C, out):
+    import torch
+
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ")
+    D = out if out is not None else torch.empty((m, n), dtype=torch.float64, device=A.device)
+    pc = ctypes.c_void_p(C.data_ptr()) if C is not None else None
+    ldc = C.stride(0) if C is not None else 0
+    return m, n, k, D, pc, ldc
+
+
+def gemm_bf16x3(A, B, *, alpha=1.0, beta=0.0, C=None, out=None, stream=None):
+    """D = beta*C + alpha*(A @ B) on the BF16 tensor cores, 3-term split (spin_gemm_bf16x3)."""
+    m, n, k, D, pc, ldc = _gemm_args(A, B, C, out)
+    rc = lib().spin_gemm_bf16x3(m, n, k, float(alpha), ctypes.c_void_p(A.data_ptr()), A.stride(0),
+                                ctypes.c_void_p(B.data_ptr()), B.stride(0), float(beta), pc, ldc,
+                                ctypes.c_void_p(D.data_ptr()), D.stride(0), _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_gemm_bf16x3")
+    return D
+
+
+def gemm_ozaki(A, B, *, slices=7, alpha=1.0, beta=0.0, C=None, out=None, add_identity=False, sumsq=None,
+               stream=None):
+    """D = beta*C + alpha*(A @ B) (+ I) with FP64-class accuracy from fixed-point
+    BF16 digit slices (spin_gemm_ozaki)."""
+    m, n, k, D, pc, ldc = _gemm_args(A, B, C, out)
+    ps = ctypes.c_void_p(sumsq.data_ptr()) if sumsq is not None else None
+    rc = lib().spin_gemm_ozaki(m, n, k, float(alpha), ctypes.c_void_p(A.data_ptr()), A.stride(0),
+                               ctypes.c_void_p(B.data_ptr()), B.stride(0), float(beta), pc, ldc,
+                               ctypes.c_void_p(D.data_ptr()), D.stride(0), int(slices), 1 if add_identity else 0,
+                               ps, _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_gemm_ozaki")
+    return D
+
+
+def take_device_error(stream=None) -> int:
+    return int(lib().spin_take_device_error(_stream(stream)))

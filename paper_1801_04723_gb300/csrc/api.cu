@@ -24,6 +24,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <string>
@@ -31,6 +33,8 @@
 #include <vector>
 
 #include "common.cuh"
+#include "mixed.h"
+#include "tc_gemm.h"
 
 namespace spin {
 
@@ -87,6 +91,11 @@ struct StreamState {
     double* hostA = nullptr;       // device staging for spin_invert_host
     double* hostX = nullptr;
     size_t host_elems = 0;
+    double* norms_host = nullptr;  // pinned: ||A||^2, ||X||^2, ||R||^2 of the refinement
+    int* err_dev = nullptr;        // device: tensor-core bounded-wait failures
+    int last_refine_iters = 0;     // host: result of the latest mixed-precision call
+    double last_rel = -1.0;
+    int last_host_status = 0;      // host-detected status (e.g. not converged)
 };
 
 std::mutex g_mu;
@@ -100,6 +109,9 @@ int get_state(cudaStream_t s, StreamState** out) {
     if (st.info_dev == nullptr) {
         SPIN_CUDA_TRY(cudaMalloc(&st.info_dev, INFO_WORDS * sizeof(int32_t)));
         SPIN_CUDA_TRY(cudaMallocHost(&st.info_host, INFO_WORDS * sizeof(int32_t)));
+        SPIN_CUDA_TRY(cudaMallocHost(&st.norms_host, 4 * sizeof(double)));
+        SPIN_CUDA_TRY(cudaMalloc(&st.err_dev, sizeof(int)));
+        SPIN_CUDA_TRY(cudaMemset(st.err_dev, 0, sizeof(int)));
     }
     *out = &st;
     return SPIN_OK;
@@ -127,7 +139,16 @@ struct Run {
     int leaf_counter;
     int64_t leaf;
     Profiler* prof;  // nullptr when not recording
+    // mixed precision only
+    int precision = SPIN_FP64;
+    int fp64_levels = 0;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int* err = nullptr;
 };
+
+constexpr int kTcMin = 128;     // products smaller than this in m or n stay in FP64
+constexpr int kSchurSlices = 7; // digit slices of the FP64-class Schur complements
 
 // Bracket one launch with events when the stream's profiler is on.
 struct ProfScope {
@@ -170,7 +191,49 @@ int leaf_prof(Run& r, int depth, const double* A, int64_t lda, double* X, int64_
         if (_r != SPIN_OK) return _r; \
     } while (0)
 
-int inv_fp64(Run& r, int depth, const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, double* W) {
+// One level product D = beta*C + alpha*(A B).  FP64 for the plain method
+// (and for small products in mixed mode); in mixed mode bf16x3 on the
+// tensor cores, or FP64-class digit slices for the Schur complement of the
+// top fp64_levels levels.
+int level_gemm(Run& r, int depth, bool schur, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+               int64_t lda, const double* B, int64_t ldb, double beta, const double* C, int64_t ldc, double* D,
+               int64_t ldd) {
+    if (r.precision == SPIN_FP64 || m < kTcMin || n < kTcMin || k < 64)
+        return gemm_f64_prof(r, depth, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
+    const double f = 2.0 * (double)m * (double)n * (double)k;
+    SplitPlan sp;
+    int rc;
+    if (schur && depth < r.fp64_levels) {
+        RET(plan_ozaki(m, n, k, kSchurSlices, r.scratch, r.scratch_bytes, &sp));
+        {
+            ProfScope ps(r.prof, r.s, SPIN_KERNEL_SPLIT, depth, m, k, 0, 0.0, 8.0 * m * k + 2.0 * kSchurSlices * m * k);
+            RET(split_a_ozaki(sp, A, lda, m, k, nullptr, r.s));
+        }
+        {
+            ProfScope ps(r.prof, r.s, SPIN_KERNEL_SPLIT, depth, k, n, 0, 0.0, 8.0 * k * n + 2.0 * kSchurSlices * k * n);
+            RET(split_b_ozaki(sp, B, ldb, k, n, nullptr, r.s));
+        }
+        const int pairs = kSchurSlices * (kSchurSlices + 1) / 2;
+        ProfScope ps(r.prof, r.s, SPIN_KERNEL_GEMM_TC, depth, m, n, k, pairs * f,
+                     2.0 * kSchurSlices * (m * k + k * n) + 8.0 * m * n * (beta != 0.0 ? 2 : 1));
+        rc = product_ozaki(sp, m, n, k, alpha, beta, C, ldc, D, ldd, 0, nullptr, r.err, r.s);
+        return rc;
+    }
+    RET(plan_bf16x3(m, n, k, r.scratch, r.scratch_bytes, &sp));
+    {
+        ProfScope ps(r.prof, r.s, SPIN_KERNEL_SPLIT, depth, m, k, 0, 0.0, 12.0 * m * k);
+        RET(split_a_bf16x3(sp, A, lda, m, k, r.s));
+    }
+    {
+        ProfScope ps(r.prof, r.s, SPIN_KERNEL_SPLIT, depth, k, n, 0, 0.0, 12.0 * k * n);
+        RET(split_b_bf16x3(sp, B, ldb, k, n, r.s));
+    }
+    ProfScope ps(r.prof, r.s, SPIN_KERNEL_GEMM_TC, depth, m, n, k, 3.0 * f,
+                 4.0 * (m * k + k * n) + 8.0 * m * n * (beta != 0.0 ? 2 : 1));
+    return product_bf16x3(sp, m, n, k, alpha, beta, C, ldc, D, ldd, r.err, r.s);
+}
+
+int inv_rec(Run& r, int depth, const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, double* W) {
     if (n <= r.leaf) return leaf_prof(r, depth, A, lda, X, ldx, n, W);
     const int64_t n1 = split_order(n), n2 = n - n1;
     const double* A11 = A;
@@ -185,14 +248,14 @@ int inv_fp64(Run& r, int depth, const double* A, int64_t lda, double* X, int64_t
     double* S = W + n1 * n2;
     double* Wsub = S + n2 * n2;
     const int d = depth;
-    RET(inv_fp64(r, d + 1, A11, lda, X11, ldx, n1, W));                                      // I
-    RET(gemm_f64_prof(r, d, n1, n2, n1, 1.0, X11, ldx, A12, lda, 0.0, nullptr, 0, T, n2));   // III
-    RET(gemm_f64_prof(r, d, n2, n2, n1, -1.0, A21, lda, T, n2, 1.0, A22, lda, S, n2));      // -V
-    RET(inv_fp64(r, d + 1, S, n2, X22, ldx, n2, Wsub));                                     // C22
-    RET(gemm_f64_prof(r, d, n1, n2, n2, -1.0, T, n2, X22, ldx, 0.0, nullptr, 0, X12, ldx)); // C12
-    RET(gemm_f64_prof(r, d, n2, n1, n1, 1.0, A21, lda, X11, ldx, 0.0, nullptr, 0, T, n1));  // II
-    RET(gemm_f64_prof(r, d, n2, n1, n2, -1.0, X22, ldx, T, n1, 0.0, nullptr, 0, X21, ldx)); // C21
-    RET(gemm_f64_prof(r, d, n1, n1, n2, -1.0, X12, ldx, T, n1, 1.0, X11, ldx, X11, ldx));   // C11
+    RET(inv_rec(r, d + 1, A11, lda, X11, ldx, n1, W));                                         // I
+    RET(level_gemm(r, d, false, n1, n2, n1, 1.0, X11, ldx, A12, lda, 0.0, nullptr, 0, T, n2));   // III
+    RET(level_gemm(r, d, true, n2, n2, n1, -1.0, A21, lda, T, n2, 1.0, A22, lda, S, n2));       // -V
+    RET(inv_rec(r, d + 1, S, n2, X22, ldx, n2, Wsub));                                        // C22
+    RET(level_gemm(r, d, false, n1, n2, n2, -1.0, T, n2, X22, ldx, 0.0, nullptr, 0, X12, ldx)); // C12
+    RET(level_gemm(r, d, false, n2, n1, n1, 1.0, A21, lda, X11, ldx, 0.0, nullptr, 0, T, n1));  // II
+    RET(level_gemm(r, d, false, n2, n1, n2, -1.0, X22, ldx, T, n1, 0.0, nullptr, 0, X21, ldx)); // C21
+    RET(level_gemm(r, d, false, n1, n1, n2, -1.0, X12, ldx, T, n1, 1.0, X11, ldx, X11, ldx));   // C11
     return SPIN_OK;
 }
 
@@ -226,33 +289,158 @@ int read_info(StreamState* st, cudaStream_t s, spin_info* info) {
                                   cudaMemcpyDeviceToHost, s));
     SPIN_CUDA_TRY(cudaStreamSynchronize(s));
     const int32_t* h = st->info_host;
+    int status = h[INFO_STATUS] ? h[INFO_STATUS] : st->last_host_status;
     if (info) {
-        info->status = h[INFO_STATUS];
-        info->refine_iters = 0;
+        info->status = status;
+        info->refine_iters = st->last_refine_iters;
         info->fail_leaf = h[INFO_STATUS] ? h[INFO_LEAF] : -1;
         info->fail_col = h[INFO_STATUS] ? h[INFO_COL] : -1;
-        info->rel_residual = -1.0;
+        info->rel_residual = st->last_rel;
     }
-    return h[INFO_STATUS];
+    return status;
+}
+
+// Workspace of the mixed-precision form: the FP64 recursion workspace (later
+// reused for the residual R), the split arena, and the cached digit planes
+// of A for the refinement residual.
+struct MixLayout {
+    size_t region0, scratch, apl, off_scratch, off_apl, off_norms, total;
+    int sr;
+};
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+MixLayout mix_layout(int64_t n, int64_t leaf, const spin_opts& o) {
+    MixLayout L;
+    // 8-bit digits are relative to the largest entry of each row (column), so
+    // the residual is accurate to ~2^(-8 s) * sqrt(n) in the normalised
+    // measure: 6 slices certify down to ~1e-12, 7 below that.
+    L.sr = o.residual_slices > 0 ? o.residual_slices : (o.tol >= 1e-11 ? 6 : 7);
+    const size_t nn = (size_t)n * (size_t)n;
+    L.region0 = round256(std::max(ws_fp64_elems(n, leaf), nn) * sizeof(double));
+    size_t sc = 0;
+    if (n > leaf) {
+        const int64_t n1 = split_order(n);
+        sc = bf16x3_scratch_bytes(n1, n1, n1);
+        if (o.fp64_levels > 0) sc = std::max(sc, ozaki_scratch_bytes(n1, n1, n1, kSchurSlices));
+    }
+    sc = std::max(sc, ozaki_scratch_bytes(0, n, n, L.sr));
+    sc = std::max(sc, bf16x3_scratch_bytes(n, n, n));
+    L.scratch = round256(sc);
+    L.apl = round256((size_t)L.sr * (size_t)n * (size_t)tc_ld(n) * 2 + (size_t)n * 4 + 512);
+    L.off_scratch = L.region0;
+    L.off_apl = L.off_scratch + L.scratch;
+    L.off_norms = L.off_apl + L.apl;
+    L.total = L.off_norms + 256;
+    return L;
+}
+
+size_t workspace_bytes_for(int64_t n, int64_t leaf, const spin_opts& o) {
+    if (o.precision == SPIN_FP64) return ws_fp64_elems(n, leaf) * sizeof(double);
+    return mix_layout(n, leaf, o).total;
+}
+
+// Newton-Schulz refinement X <- X + X (I - A X) (Bailey-style stabilisation
+// of Strassen's inversion, cited in Sec. 2.1): the residual is FP64-class
+// (digit slices of A, cached, and of X), the correction X R is bf16x3.
+// Stops when ||AX - I||_F / (||A||_F ||X||_F) <= tol.
+int refine(Run& r, StreamState* st, const double* A, int64_t lda, double* X, int64_t ldx, int64_t n,
+           const spin_opts& o, const MixLayout& L, unsigned char* ws) {
+    cudaStream_t s = r.s;
+    double* R = (double*)ws;
+    double* norms = (double*)(ws + L.off_norms);
+    const int64_t ld = tc_ld(n);
+    OzakiCachedA ca{(uint16_t*)(ws + L.off_apl), (int*)(ws + L.off_apl + (size_t)L.sr * n * ld * 2)};
+    void* scratch = ws + L.off_scratch;
+    SPIN_CUDA_TRY(cudaMemsetAsync(norms, 0, 3 * sizeof(double), s));
+    {
+        ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 8.0 * n * n + 2.0 * L.sr * n * n);
+        RET(ozaki_split_a(A, lda, n, n, L.sr, &ca, &norms[0], s));
+    }
+    const double f = 2.0 * (double)n * n * n;
+    const int pairs = L.sr * (L.sr + 1) / 2;
+    st->last_refine_iters = 0;
+    st->last_rel = -1.0;
+    for (int it = 0;; it++) {
+        SPIN_CUDA_TRY(cudaMemsetAsync(norms + 1, 0, 2 * sizeof(double), s));
+        SplitPlan sp;
+        RET(plan_ozaki(0, n, n, L.sr, scratch, L.scratch, &sp));
+        sp.a = ca.planes;
+        sp.ea = ca.exps;
+        {
+            ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 8.0 * n * n + 2.0 * L.sr * n * n);
+            RET(split_b_ozaki(sp, X, ldx, n, n, &norms[1], s));
+        }
+        {
+            ProfScope ps(r.prof, s, SPIN_KERNEL_RESIDUAL, -1, n, n, n, pairs * f,
+                         2.0 * L.sr * 2.0 * n * n + 8.0 * n * n);
+            RET(product_ozaki(sp, n, n, n, -1.0, 0.0, nullptr, 0, R, n, 1, &norms[2], r.err, s));
+        }
+        SPIN_CUDA_TRY(cudaMemcpyAsync(st->norms_host, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        SPIN_CUDA_TRY(cudaStreamSynchronize(s));
+        const double* h = st->norms_host;
+        const double rel = std::sqrt(h[2]) / (std::sqrt(h[0]) * std::sqrt(h[1]));
+        st->last_rel = rel;
+        st->last_refine_iters = it;
+        if (rel <= o.tol) return SPIN_OK;
+        if (!(rel == rel) || it >= o.max_refine) {
+            st->last_host_status = SPIN_ERR_NOT_CONVERGED;
+            return SPIN_OK;
+        }
+        SplitPlan up;
+        RET(plan_bf16x3(n, n, n, scratch, L.scratch, &up));
+        {
+            ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 24.0 * n * n);
+            RET(split_a_bf16x3(up, X, ldx, n, n, s));
+            RET(split_b_bf16x3(up, R, n, n, n, s));
+        }
+        ProfScope ps(r.prof, s, SPIN_KERNEL_UPDATE, -1, n, n, n, 3.0 * f, 8.0 * n * n + 16.0 * n * n);
+        RET(product_bf16x3(up, n, n, n, 1.0, 1.0, X, ldx, X, ldx, r.err, s));
+    }
 }
 
 int enqueue(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, const spin_opts& o,
             StreamState* st, cudaStream_t s) {
     const int64_t leaf = resolve_leaf(n, o.leaf, o.precision);
     RET(check_common(A, lda, X, ldx, n, leaf));
-    if (o.precision != SPIN_FP64) return SPIN_ERR_NOT_IMPLEMENTED;
-    const size_t need = ws_fp64_elems(n, leaf) * sizeof(double);
-    double* W;
+    if (o.precision == SPIN_MIXED_TF32) return SPIN_ERR_NOT_IMPLEMENTED;
+    const bool mixed = o.precision != SPIN_FP64;
+    if (mixed && (o.residual_slices < 0 || o.residual_slices > 7 || o.max_refine < 0 || !(o.tol > 0.0)))
+        return SPIN_ERR_INVALID_ARG;
+    const size_t need = workspace_bytes_for(n, leaf, o);
+    unsigned char* ws;
     if (o.workspace != nullptr) {
-        if (o.workspace_bytes < need || !aligned8(o.workspace)) return SPIN_ERR_INVALID_ARG;
-        W = (double*)o.workspace;
+        if (o.workspace_bytes < need || ((uintptr_t)o.workspace & 255u) != 0) return SPIN_ERR_INVALID_ARG;
+        ws = (unsigned char*)o.workspace;
     } else {
         RET(ensure_ws(st, need));
-        W = (double*)st->ws;
+        ws = (unsigned char*)st->ws;
     }
+    st->last_host_status = 0;
+    st->last_refine_iters = 0;
+    st->last_rel = -1.0;
     SPIN_CUDA_TRY(cudaMemsetAsync(st->info_dev, 0, INFO_WORDS * sizeof(int32_t), s));
     Run r{s, st->info_dev, 0, leaf, st->prof.on ? &st->prof : nullptr};
-    return inv_fp64(r, 0, A, lda, X, ldx, n, W);
+    if (!mixed) return inv_rec(r, 0, A, lda, X, ldx, n, (double*)ws);
+
+    const MixLayout L = mix_layout(n, leaf, o);
+    r.precision = o.precision;
+    r.fp64_levels = o.fp64_levels;
+    r.scratch = ws + L.off_scratch;
+    r.scratch_bytes = L.scratch;
+    r.err = st->err_dev;
+    SPIN_CUDA_TRY(cudaMemsetAsync(st->err_dev, 0, sizeof(int), s));
+    RET(inv_rec(r, 0, A, lda, X, ldx, n, (double*)ws));
+    // a singular leaf makes the refinement meaningless: stop here
+    SPIN_CUDA_TRY(cudaMemcpyAsync(st->info_host, st->info_dev, INFO_WORDS * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, s));
+    SPIN_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st->info_host[INFO_STATUS] != 0) return SPIN_OK;
+    RET(refine(r, st, A, lda, X, ldx, n, o, L, ws));
+    int err = 0;
+    SPIN_CUDA_TRY(cudaMemcpy(&err, st->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) st->last_host_status = err;
+    return SPIN_OK;
 }
 
 }  // namespace
@@ -271,6 +459,7 @@ spin_opts spin_opts_default(void) {
     o.max_refine = 6;
     o.fp64_levels = 2;
     o.blocking = 1;
+    o.residual_slices = 0;
     return o;
 }
 
@@ -285,7 +474,7 @@ size_t spin_workspace_bytes(int64_t n, const spin_opts* opts) {
     if (n < 1) return 0;
     const int64_t leaf = resolve_leaf(n, o.leaf, o.precision);
     if (leaf < 1 || leaf > kMaxLeaf) return 0;
-    return ws_fp64_elems(n, leaf) * sizeof(double);
+    return workspace_bytes_for(n, leaf, o);
 }
 
 int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, const spin_opts* opts,

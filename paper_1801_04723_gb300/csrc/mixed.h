@@ -1,0 +1,60 @@
+// Mixed-precision level products (mixed.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace spin {
+
+// A growable device arena for split planes.
+struct MixScratch {
+    void* base = nullptr;
+    size_t cap = 0;
+    int reserve(size_t bytes);
+};
+
+// Digit planes and row exponents of an A operand split once and reused
+// (the refinement multiplies by the same A every iteration).
+struct OzakiCachedA {
+    uint16_t* planes;
+    int* exps;
+};
+
+size_t bf16x3_scratch_bytes(int64_t m, int64_t n, int64_t k);
+size_t ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices);
+
+int gemm_bf16x3(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda, const double* B,
+                int64_t ldb, double beta, const double* C, int64_t ldc, double* D, int64_t ldd, void* scratch,
+                size_t scratch_bytes, int* err, cudaStream_t s);
+
+int gemm_ozaki(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda, const double* B,
+               int64_t ldb, double beta, const double* C, int64_t ldc, double* D, int64_t ldd, int slices,
+               int add_identity, double* sumsq, double* sumsq_a, double* sumsq_b, void* scratch,
+               size_t scratch_bytes, int* err, cudaStream_t s, const OzakiCachedA* cached_a);
+
+// Split-then-multiply in two halves so callers can time them separately.
+struct SplitPlan {
+    uint16_t* a;    // A planes (rows of A, K-major)
+    uint16_t* b;    // B planes (columns of B as rows, K-major)
+    int* ea;        // ozaki: row exponents of A
+    int* eb;        // ozaki: column exponents of B
+    int64_t ld;
+    int slices;     // ozaki slice count (bf16x3: 2 planes)
+};
+int plan_bf16x3(int64_t m, int64_t n, int64_t k, void* scratch, size_t bytes, SplitPlan* sp);
+int plan_ozaki(int64_t m, int64_t n, int64_t k, int slices, void* scratch, size_t bytes, SplitPlan* sp);
+int split_a_bf16x3(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, int64_t k, cudaStream_t s);
+int split_b_bf16x3(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, cudaStream_t s);
+int split_a_ozaki(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, int64_t k, double* sumsq,
+                  cudaStream_t s);
+int split_b_ozaki(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, double* sumsq,
+                  cudaStream_t s);
+int product_bf16x3(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
+                   int64_t ldc, double* D, int64_t ldd, int* err, cudaStream_t s);
+int product_ozaki(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
+                  int64_t ldc, double* D, int64_t ldd, int add_identity, double* sumsq, int* err, cudaStream_t s);
+
+int ozaki_split_a(const double* A, int64_t lda, int64_t m, int64_t k, int slices, OzakiCachedA* out,
+                  double* sumsq, cudaStream_t s);
+
+}  // namespace spin

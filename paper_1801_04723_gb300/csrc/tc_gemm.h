@@ -1,0 +1,53 @@
+// Host/device interface of the tensor-core product kernel (tc_gemm.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spin {
+
+constexpr int kTcMaxPairs = 32;
+constexpr int kTcMaxGroups = 16;
+
+// One operand as a stack of BF16 slices: slice s is a rows x K row-major
+// (K-major) matrix at base + s * rows * ld; ld is a multiple of 8 elements.
+struct TcOperand {
+    const uint16_t* base;
+    int rows;    // rows per slice: M for the A operand, N for the B operand (B stored transposed)
+    int slices;
+    int64_t ld;
+};
+
+// D = beta*C + alpha * sum over slice pairs (+ I when add_identity).
+struct TcGemmParams {
+    int M, N, K;
+    int a_rows, b_rows;     // filled by launch_tc_gemm
+    int num_pairs;
+    int8_t pa[kTcMaxPairs];  // A slice of each pair
+    int8_t pb[kTcMaxPairs];  // B slice of each pair
+    int8_t pg[kTcMaxPairs];  // group of each pair (pairs sorted by group)
+    int exact;               // 0: one FP32 accumulation of all pairs; 1: exact integer runs
+    int chunk_kb;            // exact mode: 64-wide k-blocks per exact run
+    int group_shift[kTcMaxGroups];  // exact mode: power-of-two weight of each group
+    double alpha, beta;
+    const double* C;
+    int64_t ldc;
+    double* D;
+    int64_t ldd;
+    const int* row_exp;      // exact mode: 2^row_exp[i] scales row i of A
+    const int* col_exp;      // exact mode: 2^col_exp[j] scales column j of B
+    int add_identity;
+    double* sumsq;           // if set: += sum of squares of the final D values
+    int* err;                // set to SPIN_ERR_TIMEOUT if a bounded wait gives up
+};
+
+int64_t tc_ld(int64_t k);
+int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, cudaStream_t s);
+// FP64 view -> (hi, lo) BF16 planes; transpose=true writes the cols x rows transpose.
+int launch_split_bf16x2(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
+                        int64_t ldd, cudaStream_t s);
+// FP64 view -> nslices fixed-point digit planes plus per-row (or, transposed,
+// per-column) exponents in ex; sumsq (optional) += sum of squares of src.
+int launch_ozaki_split(const double* src, int64_t lds, int rows, int cols, bool transpose, int nslices, int* ex,
+                       uint16_t* dst, int64_t ldd, double* sumsq, cudaStream_t s);
+
+}  // namespace spin
