@@ -46,11 +46,17 @@ WORKLOADS = {
                        desc="plain method, one FP64 SPD matrix A = G G^T/n + I, n = 32768, leaf 512"),
     "small_fp64": dict(n=1024, leaf=128, precision="fp64", family="sdd", seed=SEED_BASE,
                        desc="plain method, one FP64 SDD matrix (U(-1,1) + n I), n = 1024, leaf 128"),
+    "batched_fp64": dict(n=1024, leaf=0, precision="fp64", family="batch_sdd", seed=SEED_BASE + 3,
+                         desc="4096 independent FP64 matrices, orders log-uniform in [32, 1024] rounded to "
+                              "multiples of 32, each U(-1,1) + n I; one spin_invert_batched call (CUDA graph)"),
     "mixed_bf16x3": dict(n=32768, leaf=128, precision="bf16x3", family="householder", seed=SEED_BASE + 2,
                          desc="mixed precision, one SPD matrix A = Q diag(d) Q^T (64 Householder reflectors, "
                               "d log-uniform in [1, 1e3]), n = 32768: BF16x3 tensor-core level products, FP64 "
                               "leaves, FP64-class top-two Schur complements and residual, Newton-Schulz to 1e-10"),
 }
+
+
+BATCH_COUNT = 4096
 
 
 def measured_peaks() -> dict:
@@ -193,6 +199,12 @@ def host_sample(w: dict, n_s: int):
     return inputs.sdd(n_s, seed=w["seed"])
 
 
+def sample_leaf(w: dict, n_s: int) -> int:
+    if w["leaf"] > 0:
+        return min(w["leaf"], n_s)
+    return n_s if n_s <= 128 else 64
+
+
 def cpu_baseline(w: dict, seconds_hint: float = 15.0) -> dict:
     """The oracle, as it stands, on this host's cores: one inversion of a
     bounded sample of the workload (same family and leaf, smaller order)."""
@@ -202,7 +214,7 @@ def cpu_baseline(w: dict, seconds_hint: float = 15.0) -> dict:
     from paper_1801_04723_gb300 import inputs
 
     n_s = 4096 if w["n"] >= 4096 else w["n"]
-    leaf = min(w["leaf"], n_s)
+    leaf = sample_leaf(w, n_s)
     A = host_sample(w, n_s)
     oracle.strassen_inv(np.eye(8), 2)  # build / load outside the timing
     t0 = time.perf_counter()
@@ -223,7 +235,7 @@ def run_reference(args, w: dict, n: int, leaf: int):
     from paper_1801_04723_gb300 import inputs
 
     n_s = min(n, 4096)
-    leaf_s = min(leaf, n_s)
+    leaf_s = sample_leaf(w, n_s)
     A = host_sample(w, n_s)
     oracle.strassen_inv(np.eye(8), 2)
     for _ in range(args.warmup):
@@ -250,6 +262,82 @@ def run_reference(args, w: dict, n: int, leaf: int):
 
 # -------------------------------------------------------------------- ours --
 
+class SingleWork:
+    """One matrix per rank: spin_invert_ex on a device-resident input."""
+
+    def __init__(self, spin, w, n, leaf, device):
+        import torch
+
+        self.spin, self.w, self.n, self.leaf = spin, w, n, leaf
+        self.A, self.known = make_input(w, n, device)
+        self.X = torch.empty_like(self.A)
+        self.flops = 2.0 * float(n) ** 3
+        self.Ah = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        self.Ah.copy_(self.A)
+        self.Xh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        self.h2d = self.d2h = 8 * n * n
+
+    def step(self):
+        self.spin.invert(self.A, leaf=self.leaf, precision=self.w["precision"], out=self.X, blocking=False)
+
+    def finish(self):
+        return self.spin.sync(check=False)
+
+    def e2e_step(self):
+        self.spin.invert_host(self.Ah.numpy(), leaf=self.leaf, precision=self.w["precision"], out=self.Xh.numpy())
+
+    def accuracy(self, probes):
+        out = {"rel_residual_est": freivalds_rel(self.A, self.X, probes, SEED_BASE + 77) if probes > 0 else None}
+        if self.known is not None:
+            out["err_vs_known_inverse"] = known_inverse_error(self.X, self.known)
+        return out
+
+
+class BatchWork:
+    """Thousands of matrices of uneven order: one spin_invert_batched call."""
+
+    def __init__(self, spin, w, n, leaf, device, count):
+        import torch
+
+        from paper_1801_04723_gb300 import inputs
+
+        self.spin, self.leaf = spin, leaf
+        self.orders = [int(v) for v in inputs.batch_orders(count, seed=w["seed"], lo=32, hi=min(1024, n))]
+        self.As = [inputs.sdd_device(m, w["seed"] + 1000 * 3 + j, device) for j, m in enumerate(self.orders)]
+        self.Xs = [torch.empty_like(a) for a in self.As]
+        self.flops = sum(2.0 * float(m) ** 3 for m in self.orders)
+        self.Ahs = [a.cpu().pin_memory() for a in self.As]
+        self.Xhs = [torch.empty_like(a) for a in self.Ahs]
+        self.h2d = self.d2h = sum(8 * m * m for m in self.orders)
+        self.info = None
+
+    def step(self):
+        _, self.info = self.spin.invert_batched(self.As, leaf=self.leaf, outs=self.Xs, blocking=False)
+
+    def finish(self):
+        import torch
+
+        torch.cuda.synchronize()
+        bad = int((self.info != 0).sum())
+        return {"status": 0 if bad == 0 else 2, "refine_iters": 0, "rel_residual": -1.0, "failed": bad}
+
+    def e2e_step(self):
+        import torch
+
+        for a, ah in zip(self.As, self.Ahs):
+            a.copy_(ah, non_blocking=True)
+        self.spin.invert_batched(self.As, leaf=self.leaf, outs=self.Xs, blocking=False)
+        for x, xh in zip(self.Xs, self.Xhs):
+            xh.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+
+    def accuracy(self, probes):
+        worst = 0.0
+        for j in range(0, len(self.As), max(1, len(self.As) // 16)):
+            worst = max(worst, freivalds_rel(self.As[j], self.Xs[j], 4, SEED_BASE + 77))
+        return {"rel_residual_est": worst, "rel_residual_note": "max over 16 sampled matrices, 4 probes each"}
+
+
 def run_ours(args, w: dict, n: int, leaf: int):
     import torch
 
@@ -272,24 +360,24 @@ def run_ours(args, w: dict, n: int, leaf: int):
             dist.barrier()
         torch.cuda.synchronize()
 
-    A, known = make_input(w, n, device)
-    X = torch.empty_like(A)
+    if w["family"] == "batch_sdd":
+        work = BatchWork(spin, w, n, leaf, device, BATCH_COUNT)
+    else:
+        work = SingleWork(spin, w, n, leaf, device)
     stream = torch.cuda.current_stream()
-    flops = 2.0 * float(n) ** 3
+    flops = work.flops
 
-    # warm-up through the host API: each is also an end-to-end measurement
-    # (pinned host buffers, H2D of A and D2H of X inside the call)
-    Ah = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
-    Ah.copy_(A)
-    Xh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    # warm-up through host buffers: each is also an end-to-end measurement
+    # (pinned host memory, H2D of the inputs and D2H of the results inside)
     e2e_times = []
     for i in range(args.warmup):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        spin.invert_host(Ah.numpy(), leaf=leaf, precision=w["precision"], out=Xh.numpy())
+        work.e2e_step()
         e2e_times.append(time.perf_counter() - t0)
     if args.warmup == 0:
-        spin.invert(A, leaf=leaf, precision=w["precision"], out=X)  # at least one warm call
+        work.step()  # at least one warm call
+        work.finish()
     peak_fp64 = spin.probe_fp64_peak()
 
     with ClockSampler(local) as clk:
@@ -299,11 +387,11 @@ def run_ours(args, w: dict, n: int, leaf: int):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            spin.invert(A, leaf=leaf, precision=w["precision"], out=X, blocking=False)
+            work.step()
         e1.record(stream)
         barrier()
         recs = spin.profile_collect()
-        info = spin.sync(check=False)
+        info = work.finish()
     ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
         import torch.distributed as dist
@@ -312,8 +400,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * flops / (ms * 1e-3) / 1e12
-
-    rel = freivalds_rel(A, X, args.probes, SEED_BASE + 77) if args.probes > 0 else None
+    acc = work.accuracy(args.probes)
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -354,25 +441,30 @@ def run_ours(args, w: dict, n: int, leaf: int):
                     "launches": d["launches"], "share_of_step": d["ms"] / (ms * args.steps)}
     e2e_ok = e2e_times[1:] if len(e2e_times) > 1 else e2e_times
     e2e_t = statistics.median(e2e_ok) if e2e_ok else None
+    batch = isinstance(work, BatchWork)
+    config = {"workload": args.workload, "n": n, "leaf": leaf, "precision": w["precision"],
+              "matrices_per_gpu": len(work.orders) if batch else 1, "parallelism": f"replicas{world}",
+              "desc": w["desc"]}
+    if batch:
+        config["l2"] = f"inputs larger than L2 ({work.h2d / 1e9:.1f} GB of matrices)"
+        config["orders"] = {"min": min(work.orders), "max": max(work.orders), "distinct": len(set(work.orders))}
+    else:
+        config["l2"] = (f"inputs larger than L2 ({8 * n * n / 1e9:.1f} GB per matrix)" if n >= 4096 else
+                        "inputs smaller than L2; no flush between steps")
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if w["precision"] == "fp64" else "bf16x3+f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "leaf": leaf, "precision": w["precision"],
-                   "matrices_per_gpu": 1, "parallelism": f"replicas{world}",
-                   "l2": f"inputs larger than L2 ({8 * n * n / 1e9:.1f} GB per matrix)" if n >= 4096 else
-                   "inputs smaller than L2; no flush between steps", "desc": w["desc"]},
+        "config": config,
         "clocks": clk.summary(),
         "e2e": {"value": flops / e2e_t / 1e12 if e2e_t else None, "unit": "TFLOP/s",
-                "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n * n,
-                "how": "spin_invert_host on pinned host buffers, warm-up steps 2..W, host wall clock"},
+                "h2d_bytes_per_step": work.h2d, "d2h_bytes_per_step": work.d2h,
+                "how": "host buffers (pinned), copies inside the timed call, warm-up steps 2..W, host wall clock"},
         "gpu_launches": len(recs),
         "roofline": roof,
         "status": info["status"],
-        "refine_iters": info["refine_iters"],
-        "rel_residual_lib": info["rel_residual"],
-        "rel_residual_est": rel,
-        "err_vs_known_inverse": known_inverse_error(X, known) if known is not None else None,
+        "refine_iters": info.get("refine_iters"),
+        "rel_residual_lib": info.get("rel_residual"),
         "fp64_peak_tflops": peak_fp64,
         "frac_of_fp64_peak": value / world / peak_fp64,
         "bf16_peak_tflops": peaks.get("bf16_tflops"),
@@ -380,6 +472,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"], "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9}
                     for k, v in by_kind.items()},
     }
+    line.update(acc)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if args.profile_json:

@@ -122,6 +122,84 @@ int spin_invert(const double* A, double* X, int64_t n, int64_t lda, int leaf, sp
 int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n,
                    const spin_opts* opts, spin_info* info, spin_stream_t stream);
 
+/*
+ * spin_invert_batched: X[i] = A[i]^-1 for `count` independent matrices of
+ * any orders (the paper inverts one matrix at a time; the batch is this
+ * library's form of its many-block parallelism, Sec. 3.3).  Plain FP64.
+ *   A, X     host arrays of `count` device pointers (X[i] has leading
+ *            dimension n[i]); lda, n: host arrays.  Matrices may not overlap.
+ *   opts     NULL or spin_opts: leaf (0 = n for n <= 128, else 64) and
+ *            blocking are used; precision must be SPIN_FP64.
+ *   info_dev device int32[count] (may be NULL): status of each matrix
+ *            (SPIN_OK or SPIN_ERR_SINGULAR), written when the work ends.
+ * Matrices of equal order form a bucket whose recursion runs in lockstep
+ * (batched products, one leaf cluster per matrix); buckets run concurrently
+ * on streams forked from `stream`.  The launch sequence is captured into a
+ * CUDA graph on the first call and replayed while the arguments (pointers,
+ * orders, leading dimensions, info_dev, leaf) stay the same; the workspace
+ * is library-owned.  count <= 65535, n[i] <= 65536.
+ */
+int spin_invert_batched(const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
+                        int count, const spin_opts* opts, int* info_dev, spin_stream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Serving: inversion requests admitted continuously by device-memory
+ * footprint (the paper runs one job at a time; Sec. 5.1 sizes the Spark
+ * executors so that no task fails for lack of memory -- here requests wait
+ * for memory instead).  A request waits in a FIFO queue until one of
+ * max_slots slots is free and its footprint (device copy of A when A is in
+ * host memory, the result X, the workspace) fits hbm_budget_bytes; it then
+ * runs on that slot's stream while other requests run on theirs.  The
+ * result stays on the device, counted against the budget, until polled.
+ * ------------------------------------------------------------------- */
+typedef struct spin_serve_cfg {
+    size_t hbm_budget_bytes;  /* device memory the server may hold for requests       */
+    int32_t max_slots;        /* requests running at once (one stream and thread each) */
+    int32_t reserved;
+} spin_serve_cfg;
+
+typedef struct spin_result {
+    int32_t status;           /* spin_status of the inversion                          */
+    int32_t refine_iters;
+    int32_t precision;        /* spin_precision the request asked for                  */
+    int32_t reserved;
+    double rel_residual;      /* -1 for SPIN_FP64 (not computed)                       */
+    double queue_ms;          /* submit -> admitted                                    */
+    double run_ms;            /* admitted -> finished                                  */
+    double latency_ms;        /* submit -> finished                                    */
+} spin_result;
+
+typedef struct spin_serve_stats_t {
+    uint64_t submitted, completed, rejected, queued;
+    int32_t running, peak_running;
+    size_t bytes_in_use;
+} spin_serve_stats_t;
+
+typedef struct spin_server spin_server;
+
+/* Create a server on the current device.  SPIN_ERR_INVALID_ARG if
+ * max_slots is outside 1..64 or the budget is 0. */
+int spin_serve_create(const spin_serve_cfg* cfg, spin_server** out);
+
+/* Queue X = A^-1.  A (host or device memory, n x n, leading dimension lda)
+ * must stay valid and unchanged until the request is polled.  precision:
+ * SPIN_FP64 or SPIN_MIXED_BF16X3 (tol applies to the latter).  Returns a
+ * ticket; SPIN_ERR_OOM if the request alone exceeds the budget. */
+int spin_serve_submit(spin_server* sv, const double* A, int64_t lda, int64_t n, int precision, double tol,
+                      uint64_t* ticket);
+
+/* SPIN_ERR_BUSY while the request is queued or running.  When finished:
+ * copies X (host or device memory, leading dimension ldx; NULL to drop the
+ * result), fills *r, releases the request and returns SPIN_OK (the
+ * numerical status is r->status). */
+int spin_serve_poll(spin_server* sv, uint64_t ticket, double* X, int64_t ldx, spin_result* r);
+
+/* Counters: submitted, completed, rejected, queued, running, peak running, bytes held. */
+int spin_serve_stats(spin_server* sv, spin_serve_stats_t* st);
+
+/* Stop the slots (running requests finish), free everything. */
+int spin_serve_destroy(spin_server* sv);
+
 /* Synchronise the stream and fill *info with the status of the latest
  * non-blocking spin_invert_ex enqueued on it by this thread. */
 int spin_sync(spin_stream_t stream, spin_info* info);

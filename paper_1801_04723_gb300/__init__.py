@@ -11,6 +11,7 @@ from .binding import (  # noqa: F401
     SPIN_MIXED_BF16X3,
     SPIN_MIXED_TF32,
     SpinError,
+    Server,
     Info,
     Opts,
     default_leaf,
@@ -20,6 +21,7 @@ from .binding import (  # noqa: F401
     take_device_error,
     invert,
     invert_host,
+    invert_batched,
     leaf_inverse,
     lib,
     status_string,

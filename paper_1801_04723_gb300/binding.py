@@ -69,6 +69,41 @@ class ProfRecord(ctypes.Structure):
 KERNEL_KINDS = {0: "leaf_gj", 1: "gemm_f64", 2: "gemm_tc", 3: "split", 4: "residual", 5: "update", 6: "other"}
 
 
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("refine_iters", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("rel_residual", ctypes.c_double),
+        ("queue_ms", ctypes.c_double),
+        ("run_ms", ctypes.c_double),
+        ("latency_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64),
+        ("completed", ctypes.c_uint64),
+        ("rejected", ctypes.c_uint64),
+        ("queued", ctypes.c_uint64),
+        ("running", ctypes.c_int32),
+        ("peak_running", ctypes.c_int32),
+        ("bytes_in_use", ctypes.c_size_t),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class SpinError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
@@ -126,6 +161,18 @@ def lib():
         L.spin_gemm_ozaki.argtypes = [i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp, i64, ctypes.c_int,
                                       ctypes.c_int, vp, vp]
         L.spin_gemm_ozaki.restype = ctypes.c_int
+        L.spin_invert_batched.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.POINTER(Opts), vp, vp]
+        L.spin_invert_batched.restype = ctypes.c_int
+        L.spin_serve_create.argtypes = [ctypes.POINTER(ServeCfg), ctypes.POINTER(vp)]
+        L.spin_serve_create.restype = ctypes.c_int
+        L.spin_serve_submit.argtypes = [vp, vp, i64, i64, ctypes.c_int, dbl, ctypes.POINTER(ctypes.c_uint64)]
+        L.spin_serve_submit.restype = ctypes.c_int
+        L.spin_serve_poll.argtypes = [vp, ctypes.c_uint64, vp, i64, ctypes.POINTER(Result)]
+        L.spin_serve_poll.restype = ctypes.c_int
+        L.spin_serve_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
+        L.spin_serve_stats.restype = ctypes.c_int
+        L.spin_serve_destroy.argtypes = [vp]
+        L.spin_serve_destroy.restype = ctypes.c_int
         L.spin_take_device_error.argtypes = [vp]
         L.spin_take_device_error.restype = ctypes.c_int
         _lib = L
@@ -352,3 +399,99 @@ def gemm_ozaki(A, B, *, slices=7, alpha=1.0, beta=0.0, C=None, out=None, add_ide
 
 def take_device_error(stream=None) -> int:
     return int(lib().spin_take_device_error(_stream(stream)))
+
+
+def invert_batched(As, *, leaf: int = 0, outs=None, stream=None, blocking: bool = True):
+    """X_i = A_i^-1 for a list of square float64 CUDA tensors of any orders
+    (spin_invert_batched).  Returns (list of X, int32 CUDA tensor of statuses)."""
+    import torch
+
+    count = len(As)
+    if outs is None:
+        outs = [torch.empty((a.shape[0], a.shape[0]), dtype=torch.float64, device=a.device) for a in As]
+    for a, x in zip(As, outs):
+        _check_matrix(a, "A")
+        _check_matrix(x, "X")
+        if x.stride(0) != x.shape[0]:
+            raise ValueError("each X must be contiguous")
+    pa = (ctypes.c_void_p * count)(*[a.data_ptr() for a in As])
+    px = (ctypes.c_void_p * count)(*[x.data_ptr() for x in outs])
+    lda = (ctypes.c_int64 * count)(*[a.stride(0) for a in As])
+    ns = (ctypes.c_int64 * count)(*[a.shape[0] for a in As])
+    info = torch.zeros(count, dtype=torch.int32, device=As[0].device)
+    o = make_opts("fp64", leaf, blocking=blocking)
+    rc = lib().spin_invert_batched(pa, lda, px, ns, count, ctypes.byref(o), ctypes.c_void_p(info.data_ptr()),
+                                   _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_invert_batched")
+    return outs, info
+
+
+SPIN_ERR_BUSY = 7
+
+
+class Server:
+    """Request server (spin_serve_*): submit matrices (host numpy arrays or
+    CUDA tensors, kept alive by the caller until polled), poll results."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 4):
+        cfg = ServeCfg(int(hbm_budget_bytes), int(max_slots), 0)
+        h = ctypes.c_void_p()
+        rc = lib().spin_serve_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != SPIN_OK:
+            raise SpinError(rc, "spin_serve_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, A, precision="bf16x3", tol: float = 1e-10) -> int:
+        import numpy as np
+
+        if hasattr(A, "data_ptr"):
+            ptr, lda, n = A.data_ptr(), A.stride(0), A.shape[0]
+        else:
+            A = np.ascontiguousarray(A, dtype=np.float64)
+            ptr, lda, n = A.ctypes.data, A.shape[1], A.shape[0]
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        t = ctypes.c_uint64(0)
+        rc = lib().spin_serve_submit(self._h, ctypes.c_void_p(ptr), lda, n, p, float(tol), ctypes.byref(t))
+        if rc != SPIN_OK:
+            raise SpinError(rc, "spin_serve_submit")
+        self._keep[t.value] = A
+        return t.value
+
+    def poll(self, ticket: int, out=None):
+        """None while busy; else (X, result dict).  X is a numpy array unless
+        ``out`` (numpy array or CUDA tensor) is given."""
+        import numpy as np
+
+        A = self._keep.get(ticket)
+        n = A.shape[0] if A is not None else 0
+        if out is None:
+            out = np.empty((n, n), dtype=np.float64)
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        ld = out.stride(0) if hasattr(out, "data_ptr") else out.shape[1]
+        r = Result()
+        rc = lib().spin_serve_poll(self._h, ctypes.c_uint64(ticket), ctypes.c_void_p(ptr), ld, ctypes.byref(r))
+        if rc == SPIN_ERR_BUSY:
+            return None
+        if rc != SPIN_OK:
+            raise SpinError(rc, "spin_serve_poll")
+        self._keep.pop(ticket, None)
+        return out, r.as_dict()
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        lib().spin_serve_stats(self._h, ctypes.byref(st))
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().spin_serve_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -444,6 +444,18 @@ int enqueue(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, con
 }
 
 }  // namespace
+
+// Internal entry for other translation units: the FP64 recursion over a
+// caller-supplied workspace W (fp64_workspace_elems(n, leaf) doubles) and
+// info record, no profiling, nothing allocated.
+size_t fp64_workspace_elems(int64_t n, int64_t leaf) { return ws_fp64_elems(n, leaf); }
+
+int run_fp64_inversion(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, int64_t leaf, double* W,
+                       int32_t* info, cudaStream_t s) {
+    Run r{s, info, 0, leaf, nullptr};
+    return inv_rec(r, 0, A, lda, X, ldx, n, W);
+}
+
 }  // namespace spin
 
 using namespace spin;

@@ -11,11 +11,15 @@ namespace spin {
 // Device info record layout: int32[4] = {status, leaf_index, column, spare}.
 enum { INFO_STATUS = 0, INFO_LEAF = 1, INFO_COL = 2, INFO_WORDS = 4 };
 
+// On failure: remember the message, clear the runtime's last-error slot (so
+// that a later, unrelated cudaGetLastError() check does not see it again)
+// and return SPIN_ERR_CUDA.
 #define SPIN_CUDA_TRY(expr)                                                        \
     do {                                                                           \
         cudaError_t _e = (expr);                                                   \
         if (_e != cudaSuccess) {                                                   \
             spin::record_cuda_error(_e, #expr, __FILE__, __LINE__);                \
+            cudaGetLastError();                                                    \
             return SPIN_ERR_CUDA;                                                  \
         }                                                                          \
     } while (0)
@@ -31,15 +35,39 @@ __device__ __forceinline__ void record_failure(int32_t* info, int code, int leaf
     }
 }
 
+// A strided view inside each matrix of a batch: problem z's view starts at
+// base[z] + r0 * ld + c0, with ld = lds[z] when lds is given, else ld.
+struct BatchView {
+    const double* const* base;  // device array of per-problem base pointers
+    const int64_t* lds;         // device array of per-problem leading dims, or nullptr
+    int64_t ld;                 // uniform leading dim when lds == nullptr
+    int64_t r0, c0;
+    __device__ __forceinline__ int64_t ld_of(int z) const { return lds ? lds[z] : ld; }
+    __device__ __forceinline__ const double* ptr(int z, int64_t l) const { return base[z] + r0 * l + c0; }
+};
+
 // ---- kernel launchers (host) ----
 int launch_gemm_f64(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, const double* C, int64_t ldc, double* D,
                     int64_t ldd, cudaStream_t s);
 
-// Leaf Gauss-Jordan: scratch (L*L doubles) is required only when L > 512.
+int launch_gemm_f64_batched(int64_t m, int64_t n, int64_t k, double alpha, const BatchView& a, const BatchView& b,
+                            double beta, const BatchView& c, const BatchView& d, int count, cudaStream_t s);
+// Batched leaf: problem z inverts view src(z) into dst(z); scratch(z) = scratch_base + z * scratch_stride
+// (L*L doubles each when L > 256); info(z) = info + 4 z; leaf index reported = leaf_index.
+int launch_leaf_gj_batched(const BatchView& src, const BatchView& dst, int64_t L, double* scratch_base,
+                           int64_t scratch_stride, int32_t* info, int leaf_index, int count, cudaStream_t s);
+
+// Leaf Gauss-Jordan: scratch (L*L doubles) is required when L > 256 (rows may spill to it).
 int launch_leaf_gj(const double* A, int64_t lda, double* X, int64_t ldx, int64_t L, double* scratch,
                    int32_t* info, int leaf_index, cudaStream_t s);
 size_t leaf_scratch_elems(int64_t L);
 constexpr int64_t kMaxLeaf = 4096;
+
+// FP64 recursion over caller-supplied workspace and info record (api.cu).
+size_t fp64_workspace_elems(int64_t n, int64_t leaf);
+int run_fp64_inversion(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, int64_t leaf, double* W,
+                       int32_t* info, cudaStream_t s);
+int64_t split_order(int64_t n);
 
 }  // namespace spin

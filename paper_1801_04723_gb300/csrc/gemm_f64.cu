@@ -18,10 +18,10 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
-__global__ void __launch_bounds__(NT, 2)
-gemm_f64_kernel(int64_t m, int64_t n, int64_t k, double alpha, const double* __restrict__ A, int64_t lda,
-                const double* __restrict__ B, int64_t ldb, double beta, const double* C, int64_t ldc,
-                double* D, int64_t ldd) {
+__device__ __forceinline__ void gemm_f64_tile(int64_t m, int64_t n, int64_t k, double alpha,
+                                              const double* __restrict__ A, int64_t lda,
+                                              const double* __restrict__ B, int64_t ldb, double beta,
+                                              const double* C, int64_t ldc, double* D, int64_t ldd) {
     __shared__ double As[2][BK][BM + 1];
     __shared__ double Bs[2][BK][BN];
     const int tid = threadIdx.x;
@@ -98,7 +98,42 @@ gemm_f64_kernel(int64_t m, int64_t n, int64_t k, double alpha, const double* __r
     }
 }
 
+__global__ void __launch_bounds__(NT, 2)
+gemm_f64_kernel(int64_t m, int64_t n, int64_t k, double alpha, const double* __restrict__ A, int64_t lda,
+                const double* __restrict__ B, int64_t ldb, double beta, const double* C, int64_t ldc,
+                double* D, int64_t ldd) {
+    gemm_f64_tile(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
+}
+
+// Batched form: problem blockIdx.z uses the views described by the BatchView
+// operands (same shape for every problem, per-problem base and leading dim).
+__global__ void __launch_bounds__(NT, 2)
+gemm_f64_batched_kernel(int64_t m, int64_t n, int64_t k, double alpha, BatchView a, BatchView b, double beta,
+                        BatchView c, BatchView d) {
+    const int z = blockIdx.z;
+    const int64_t lda = a.ld_of(z), ldb = b.ld_of(z), ldd = d.ld_of(z);
+    const double* A = a.ptr(z, lda);
+    const double* B = b.ptr(z, ldb);
+    const double* C = nullptr;
+    int64_t ldc = 0;
+    if (beta != 0.0) {
+        ldc = c.ld_of(z);
+        C = c.ptr(z, ldc);
+    }
+    gemm_f64_tile(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, const_cast<double*>(d.ptr(z, ldd)), ldd);
+}
+
 }  // namespace
+
+int launch_gemm_f64_batched(int64_t m, int64_t n, int64_t k, double alpha, const BatchView& a, const BatchView& b,
+                            double beta, const BatchView& c, const BatchView& d, int count, cudaStream_t s) {
+    if (m <= 0 || n <= 0 || count <= 0) return SPIN_OK;
+    dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)count);
+    if (grid.y > 65535u || grid.z > 65535u) return SPIN_ERR_INVALID_ARG;
+    gemm_f64_batched_kernel<<<grid, NT, 0, s>>>(m, n, k, alpha, a, b, beta, c, d);
+    SPIN_CUDA_TRY(cudaGetLastError());
+    return SPIN_OK;
+}
 
 int launch_gemm_f64(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, const double* C, int64_t ldc, double* D,

@@ -18,7 +18,9 @@
 // distributed shared memory.  Per step: local argmax -> cluster barrier ->
 // every CTA reduces the C candidates identically -> the pivot row's owner
 // scales it -> cluster barrier -> all CTAs eliminate their rows.  Cluster
-// barriers are hardware barriers: there is no spin-wait anywhere.
+// barriers are hardware barriers: there is no spin-wait anywhere.  Per step
+// there is a single cluster barrier: the pivot row is read raw by every CTA
+// through distributed shared memory and scaled on the fly.
 #include <cooperative_groups.h>
 #include <limits.h>
 
@@ -39,7 +41,7 @@ struct Cand {
 };
 
 struct LeafSmemLayout {
-    size_t m_off, prow_off, fcol_off, cand_off, phys_off, lpos_off, piv_off, sig_off, total;
+    size_t m_off, fcol_off, cand_off, phys_off, lpos_off, piv_off, sig_off, total;
 };
 
 __host__ __device__ inline LeafSmemLayout leaf_layout(int L, int R, bool rows_in_smem) {
@@ -47,7 +49,6 @@ __host__ __device__ inline LeafSmemLayout leaf_layout(int L, int R, bool rows_in
     size_t off = 0;
     s.m_off = off;
     if (rows_in_smem) off += (size_t)R * L * sizeof(double);
-    s.prow_off = off; off += (size_t)L * sizeof(double);
     s.fcol_off = off; off += (size_t)R * sizeof(double);
     s.cand_off = off; off += 2 * sizeof(Cand);
     s.phys_off = off; off += (size_t)L * sizeof(int);
@@ -105,9 +106,9 @@ __device__ void local_candidate(const double* M, int L, int nrows, int r0, const
 }
 
 template <bool ROWS_IN_SMEM>
-__global__ void __launch_bounds__(NT, 1)
-leaf_gj_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__ dst, int64_t ldd,
-               double* __restrict__ gwork, int L, int R, int32_t* info, int leaf_index) {
+__device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int64_t lds, double* __restrict__ dst,
+                                             int64_t ldd, double* __restrict__ gwork, int L, int R, int32_t* info,
+                                             int leaf_index) {
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
@@ -116,7 +117,6 @@ leaf_gj_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const LeafSmemLayout lay = leaf_layout(L, R, ROWS_IN_SMEM);
     double* M = ROWS_IN_SMEM ? reinterpret_cast<double*>(smem_raw + lay.m_off) : gwork + (size_t)rank * R * L;
-    double* prow = reinterpret_cast<double*>(smem_raw + lay.prow_off);
     double* fcol = reinterpret_cast<double*>(smem_raw + lay.fcol_off);
     Cand* cand = reinterpret_cast<Cand*>(smem_raw + lay.cand_off);
     int* phys_at = reinterpret_cast<int*>(smem_raw + lay.phys_off);
@@ -139,9 +139,19 @@ leaf_gj_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__
     __syncthreads();
     local_candidate(M, L, nrows, r0, lpos, 0, &cand[0], warp_scratch);
 
+    // One cluster barrier per step.  The pivot row of step k is read raw by
+    // every CTA (and scaled on the fly); its owner scales it in place at the
+    // start of step k+1, after the barrier, when nobody reads it any more and
+    // before it is eliminated like every other row.
     int steps_done = 0;
+    int prev_p = -1;
+    double prev_inv = 0.0;
     for (int k = 0; k < L; k++) {
-        cluster.sync();  // every CTA's candidate for column k is published
+        cluster.sync();  // candidates for column k published; step k-1 finished everywhere
+        if (prev_p >= 0 && prev_p / R == rank) {
+            double* rp = M + (size_t)(prev_p - r0) * L;
+            for (int j = tid; j < L; j += NT) rp[j] = (j == k - 1) ? prev_inv : rp[j] * prev_inv;
+        }
         if (tid < 32) {
             Cand c{-1.0, 0.0, INT_MAX, -1};
             if (tid < C) c = *cluster.map_shared_rank(&cand[0], tid);
@@ -167,7 +177,7 @@ leaf_gj_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__
                 }
             }
         }
-        __syncthreads();
+        __syncthreads();  // pivot decided; the deferred scaling of the previous pivot row is done
         if (s_fail) {  // identical decision in every CTA: all leave the loop together
             if (rank == 0 && tid == 0) record_failure(info, SPIN_ERR_SINGULAR, leaf_index, k);
             break;
@@ -175,20 +185,15 @@ leaf_gj_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__
         const int p = chosen.phys;
         const double inv = 1.0 / chosen.val;
         const int owner = p / R;
-        if (owner == rank) {
-            double* rp = M + (size_t)(p - r0) * L;
-            for (int j = tid; j < L; j += NT) {
-                const double v = (j == k) ? inv : rp[j] * inv;
-                prow[j] = v;
-                rp[j] = v;
-            }
-        }
         for (int r = tid; r < nrows; r += NT)
             if (r0 + r != p) fcol[r] = M[(size_t)r * L + k];
-        cluster.sync();  // the scaled pivot row is published; fcol is complete
-        const double* rprow = cluster.map_shared_rank(prow, owner);
+        __syncthreads();  // every multiplier is stashed before column k is overwritten
+        // the owner's raw pivot row: its shared memory (through the cluster
+        // window), or the L2-resident work rows when they live in global memory
+        const double* rprow = ROWS_IN_SMEM ? cluster.map_shared_rank(M, owner) + (size_t)(p - owner * R) * L
+                                           : gwork + (size_t)p * L;
         for (int j = tid; j < L; j += NT) {
-            const double pj = rprow[j];
+            const double pj = (j == k) ? inv : rprow[j] * inv;
             for (int r = 0; r < nrows; r++) {
                 if (r0 + r == p) continue;
                 const double f = fcol[r];
@@ -200,10 +205,17 @@ leaf_gj_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__
         }
         __syncthreads();
         local_candidate(M, L, nrows, r0, lpos, k + 1, &cand[0], warp_scratch);
+        prev_p = p;
+        prev_inv = inv;
         steps_done = k + 1;
     }
-    cluster.sync();  // no CTA still reads a peer's pivot row
+    cluster.sync();  // no CTA still reads a peer's rows
     if (steps_done < L) return;  // failure already recorded; X is undefined
+    if (prev_p >= 0 && prev_p / R == rank) {  // the last pivot row is still unscaled
+        double* rp = M + (size_t)(prev_p - r0) * L;
+        for (int j = tid; j < L; j += NT) rp[j] = (j == L - 1) ? prev_inv : rp[j] * prev_inv;
+    }
+    __syncthreads();
 
     if (tid == 0) {
         for (int q = 0; q < L; q++) sigma[q] = q;
@@ -225,6 +237,25 @@ leaf_gj_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__
         }
     }
     if (__syncthreads_or(nonfinite) && tid == 0) record_failure(info, SPIN_ERR_SINGULAR, leaf_index, L);
+}
+
+template <bool ROWS_IN_SMEM>
+__global__ void __launch_bounds__(NT, 1)
+leaf_gj_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__ dst, int64_t ldd,
+               double* __restrict__ gwork, int L, int R, int32_t* info, int leaf_index) {
+    leaf_gj_body<ROWS_IN_SMEM>(src, lds, dst, ldd, gwork, L, R, info, leaf_index);
+}
+
+// Batched form: cluster blockIdx.y inverts problem z = blockIdx.y.
+template <bool ROWS_IN_SMEM>
+__global__ void __launch_bounds__(NT, 1)
+leaf_gj_batched_kernel(BatchView src, BatchView dst, double* __restrict__ gwork, int64_t gwork_stride, int L, int R,
+                       int32_t* info, int leaf_index) {
+    const int z = blockIdx.y;
+    const int64_t lds = src.ld_of(z), ldd = dst.ld_of(z);
+    leaf_gj_body<ROWS_IN_SMEM>(src.ptr(z, lds), lds, const_cast<double*>(dst.ptr(z, ldd)), ldd,
+                               ROWS_IN_SMEM ? nullptr : gwork + (int64_t)z * gwork_stride, L, R,
+                               info + (int64_t)z * INFO_WORDS, leaf_index);
 }
 
 struct LeafConfig {
@@ -303,7 +334,45 @@ int launch_leaf_impl(const double* A, int64_t lda, double* X, int64_t ldx, const
     return SPIN_OK;
 }
 
+template <bool S>
+int launch_leaf_batched_impl(const BatchView& src, const BatchView& dst, const LeafConfig& c, int64_t L,
+                             double* scratch, int64_t stride, int32_t* info, int leaf_index, int count,
+                             cudaStream_t s) {
+    static bool attr_done[2] = {false, false};
+    auto kern = leaf_gj_batched_kernel<S>;
+    if (!attr_done[S ? 1 : 0]) {
+        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
+        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        attr_done[S ? 1 : 0] = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)c.C, (unsigned)count, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = c.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)c.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SPIN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, src, dst, scratch, stride, (int)L, c.R, info, leaf_index));
+    return SPIN_OK;
+}
+
 }  // namespace
+
+int launch_leaf_gj_batched(const BatchView& src, const BatchView& dst, int64_t L, double* scratch_base,
+                           int64_t scratch_stride, int32_t* info, int leaf_index, int count, cudaStream_t s) {
+    if (L <= 0 || count <= 0) return SPIN_OK;
+    if (L > kMaxLeaf || count > 65535) return SPIN_ERR_INVALID_ARG;
+    const LeafConfig c = leaf_config(L, scratch_base != nullptr);
+    if (c.smem > kSmemBudget) return SPIN_ERR_INVALID_ARG;
+    if (c.smem_rows)
+        return launch_leaf_batched_impl<true>(src, dst, c, L, nullptr, 0, info, leaf_index, count, s);
+    return launch_leaf_batched_impl<false>(src, dst, c, L, scratch_base, scratch_stride, info, leaf_index, count, s);
+}
 
 // Leaves above 256 may not fit shared memory on every cluster shape, so
 // they always get an L x L scratch slab (used only when the rows spill).

@@ -1,0 +1,294 @@
+// Serving: inversion requests admitted continuously by device-memory
+// footprint and run concurrently on a pool of CUDA streams.
+//
+// A request (A, n, precision, tol) waits in a FIFO queue until a slot is
+// free and its footprint (device copy of A when A is in host memory, the
+// result X, and the inversion workspace) fits the server's HBM budget; it
+// then runs on that slot's stream while other requests run on theirs, so
+// requests that arrive while others are on the GPU overlap with them.  Its
+// result stays in device memory (counted against the budget) until the
+// client polls it.  Memory comes from a stream-ordered pool
+// (cudaMallocAsync), so admission does not synchronise the device.
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+namespace spin {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Request {
+    uint64_t ticket;
+    const double* A;
+    int64_t lda, n;
+    bool a_on_device;
+    int precision;
+    double tol;
+    size_t footprint_run;   // released when the run ends (staged A + workspace)
+    size_t footprint_keep;  // released when the client polls (X)
+    Clock::time_point t_submit, t_start, t_end;
+    double* X = nullptr;    // device, n x n, owned by the server until polled
+    spin_info info{};
+    int status = SPIN_ERR_BUSY;
+    bool done = false;
+};
+
+}  // namespace
+}  // namespace spin
+
+struct spin_server {
+    spin_serve_cfg cfg;
+    int device = 0;
+    cudaMemPool_t pool = nullptr;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<std::shared_ptr<spin::Request>> queue;
+    std::map<uint64_t, std::shared_ptr<spin::Request>> table;
+    size_t in_use = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;
+    cudaStream_t copy_stream = nullptr;
+    // counters
+    uint64_t submitted = 0, completed = 0, rejected = 0;
+    int running = 0, peak_running = 0;
+};
+
+namespace spin {
+namespace {
+
+size_t request_workspace(int64_t n, int precision, double tol) {
+    spin_opts o = spin_opts_default();
+    o.precision = precision;
+    o.tol = tol;
+    return spin_workspace_bytes(n, &o);
+}
+
+void worker_loop(spin_server* sv, int slot) {
+    cudaSetDevice(sv->device);
+    cudaStream_t s = sv->streams[slot];
+    while (true) {
+        std::shared_ptr<Request> rq;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv.wait(lk, [&] {
+                if (sv->stop) return true;
+                if (sv->queue.empty()) return false;
+                const auto& h = sv->queue.front();
+                return sv->in_use + h->footprint_run + h->footprint_keep <= sv->cfg.hbm_budget_bytes;
+            });
+            if (sv->stop) return;
+            rq = sv->queue.front();
+            sv->queue.pop_front();
+            sv->in_use += rq->footprint_run + rq->footprint_keep;
+            sv->running++;
+            if (sv->running > sv->peak_running) sv->peak_running = sv->running;
+        }
+        rq->t_start = Clock::now();
+        const int64_t n = rq->n;
+        const size_t nn = (size_t)n * (size_t)n * sizeof(double);
+        const size_t ws_bytes = request_workspace(n, rq->precision, rq->tol);
+        double* Ad = nullptr;
+        void* ws = nullptr;
+        int rc = SPIN_OK;
+        if (cudaMallocFromPoolAsync((void**)&rq->X, nn, sv->pool, s) != cudaSuccess) rc = SPIN_ERR_OOM;
+        if (rc == SPIN_OK && ws_bytes && cudaMallocFromPoolAsync(&ws, ws_bytes, sv->pool, s) != cudaSuccess)
+            rc = SPIN_ERR_OOM;
+        const double* Ause = rq->A;
+        int64_t lda = rq->lda;
+        if (rc == SPIN_OK && !rq->a_on_device) {
+            if (cudaMallocFromPoolAsync((void**)&Ad, nn, sv->pool, s) != cudaSuccess) rc = SPIN_ERR_OOM;
+            if (rc == SPIN_OK &&
+                cudaMemcpy2DAsync(Ad, n * sizeof(double), rq->A, rq->lda * sizeof(double), n * sizeof(double), n,
+                                  cudaMemcpyHostToDevice, s) != cudaSuccess)
+                rc = SPIN_ERR_CUDA;
+            Ause = Ad;
+            lda = n;
+        }
+        if (rc == SPIN_OK) {
+            spin_opts o = spin_opts_default();
+            o.precision = rq->precision;
+            o.tol = rq->tol;
+            o.blocking = 1;
+            o.workspace = ws;
+            o.workspace_bytes = ws_bytes;
+            rc = spin_invert_ex(Ause, lda, rq->X, n, n, &o, &rq->info, (spin_stream_t)s);
+            if (rc == SPIN_OK || rc == SPIN_ERR_SINGULAR || rc == SPIN_ERR_NOT_CONVERGED) rc = rq->info.status;
+        }
+        if (Ad) cudaFreeAsync(Ad, s);
+        if (ws) cudaFreeAsync(ws, s);
+        cudaStreamSynchronize(s);
+        rq->t_end = Clock::now();
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            rq->status = rc;
+            rq->done = true;
+            sv->in_use -= rq->footprint_run;
+            sv->running--;
+            sv->completed++;
+        }
+        sv->cv.notify_all();
+    }
+}
+
+}  // namespace
+}  // namespace spin
+
+using namespace spin;
+
+extern "C" int spin_serve_create(const spin_serve_cfg* cfg, spin_server** out) {
+    if (cfg == nullptr || out == nullptr || cfg->max_slots < 1 || cfg->max_slots > 64 || cfg->hbm_budget_bytes == 0)
+        return SPIN_ERR_INVALID_ARG;
+    auto* sv = new spin_server();
+    sv->cfg = *cfg;
+    if (cudaGetDevice(&sv->device) != cudaSuccess) {
+        delete sv;
+        return SPIN_ERR_CUDA;
+    }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = sv->device;
+    if (cudaMemPoolCreate(&sv->pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        delete sv;
+        return SPIN_ERR_CUDA;
+    }
+    uint64_t keep = cfg->hbm_budget_bytes;  // keep freed blocks for reuse up to the budget
+    cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    sv->streams.resize(cfg->max_slots);
+    for (auto& st : sv->streams) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&sv->copy_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < cfg->max_slots; i++) sv->workers.emplace_back(worker_loop, sv, i);
+    *out = sv;
+    return SPIN_OK;
+}
+
+extern "C" int spin_serve_submit(spin_server* sv, const double* A, int64_t lda, int64_t n, int precision, double tol,
+                                 uint64_t* ticket) {
+    if (sv == nullptr || A == nullptr || ticket == nullptr || n < 1 || lda < n) return SPIN_ERR_INVALID_ARG;
+    if (precision < SPIN_FP64 || precision > SPIN_MIXED_BF16X3 || !(tol > 0.0)) return SPIN_ERR_INVALID_ARG;
+    cudaPointerAttributes at;
+    bool on_dev = false;
+    if (cudaPointerGetAttributes(&at, A) == cudaSuccess)
+        on_dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    else
+        cudaGetLastError();
+    auto rq = std::make_shared<Request>();
+    rq->A = A;
+    rq->lda = lda;
+    rq->n = n;
+    rq->a_on_device = on_dev;
+    rq->precision = precision;
+    rq->tol = tol;
+    const size_t nn = (size_t)n * (size_t)n * sizeof(double);
+    rq->footprint_keep = nn;
+    rq->footprint_run = request_workspace(n, precision, tol) + (on_dev ? 0 : nn);
+    rq->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (rq->footprint_run + rq->footprint_keep > sv->cfg.hbm_budget_bytes) {
+            sv->rejected++;
+            return SPIN_ERR_OOM;  // can never fit the budget
+        }
+        rq->ticket = sv->next_ticket++;
+        sv->table[rq->ticket] = rq;
+        sv->queue.push_back(rq);
+        sv->submitted++;
+    }
+    sv->cv.notify_all();
+    *ticket = rq->ticket;
+    return SPIN_OK;
+}
+
+extern "C" int spin_serve_poll(spin_server* sv, uint64_t ticket, double* X, int64_t ldx, spin_result* r) {
+    if (sv == nullptr) return SPIN_ERR_INVALID_ARG;
+    std::shared_ptr<Request> rq;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->table.find(ticket);
+        if (it == sv->table.end()) return SPIN_ERR_INVALID_ARG;
+        rq = it->second;
+        if (!rq->done) return SPIN_ERR_BUSY;
+        sv->table.erase(it);
+    }
+    const int64_t n = rq->n;
+    int rc = SPIN_OK;
+    if (X != nullptr && rq->X != nullptr) {
+        if (ldx < n) {
+            rc = SPIN_ERR_INVALID_ARG;
+        } else if (cudaMemcpy2DAsync(X, ldx * sizeof(double), rq->X, n * sizeof(double), n * sizeof(double), n,
+                                     cudaMemcpyDefault, sv->copy_stream) != cudaSuccess ||
+                   cudaStreamSynchronize(sv->copy_stream) != cudaSuccess) {
+            rc = SPIN_ERR_CUDA;
+        }
+    }
+    if (rq->X) {
+        cudaFreeAsync(rq->X, sv->copy_stream);
+        cudaStreamSynchronize(sv->copy_stream);
+        rq->X = nullptr;
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->in_use -= rq->footprint_keep;
+    }
+    sv->cv.notify_all();
+    if (r) {
+        r->status = rq->status;
+        r->refine_iters = rq->info.refine_iters;
+        r->precision = rq->precision;
+        r->reserved = 0;
+        r->rel_residual = rq->info.rel_residual;
+        r->queue_ms = ms_between(rq->t_submit, rq->t_start);
+        r->run_ms = ms_between(rq->t_start, rq->t_end);
+        r->latency_ms = ms_between(rq->t_submit, rq->t_end);
+    }
+    return rc;
+}
+
+extern "C" int spin_serve_stats(spin_server* sv, spin_serve_stats_t* st) {
+    if (sv == nullptr || st == nullptr) return SPIN_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    st->submitted = sv->submitted;
+    st->completed = sv->completed;
+    st->rejected = sv->rejected;
+    st->queued = sv->queue.size();
+    st->running = sv->running;
+    st->peak_running = sv->peak_running;
+    st->bytes_in_use = sv->in_use;
+    return SPIN_OK;
+}
+
+extern "C" int spin_serve_destroy(spin_server* sv) {
+    if (sv == nullptr) return SPIN_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_all();
+    for (auto& t : sv->workers) t.join();
+    for (auto& kv : sv->table)
+        if (kv.second->X) cudaFreeAsync(kv.second->X, sv->copy_stream);
+    cudaStreamSynchronize(sv->copy_stream);
+    for (auto& st : sv->streams) cudaStreamDestroy(st);
+    cudaStreamDestroy(sv->copy_stream);
+    cudaMemPoolDestroy(sv->pool);
+    delete sv;
+    return SPIN_OK;
+}

@@ -19,15 +19,15 @@
 //       FP64 output: the result is exact up to the truncation of the digit
 //       expansion, i.e. FP64-class for 5-7 slices.
 //
-// Kernel: one CTA per 128 x BN output tile (BN = 256 in float mode, 128 in
-// exact mode so that the int32 run sums, BN/2 per epilogue thread, stay in
-// registers), 320 threads:
-//   warp 0      TMA producer (one lane): ring of (A 128x64, B BNx64) BF16
-//               tiles, 128-byte swizzled, mbarrier complete_tx.
-//   warp 1      TMEM owner (2*BN columns = two 128 x BN FP32 accumulators)
+// Kernel: one CTA per 128 x 256 output tile:
+//   warp 0      TMA producer (one lane): 4-stage ring of (A 128x64, B 256x64)
+//               BF16 tiles, 128-byte swizzled, mbarrier complete_tx.
+//   warp 1      TMEM owner (512 columns = two 128 x 256 FP32 accumulators)
 //               and MMA issuer (one lane): 4 tcgen05.mma (K = 16) per stage.
-//   warps 2-9   epilogue: warp w reads TMEM lanes 32*(w%4).., columns
-//               (BN/2)*((w-2)/4).. with tcgen05.ld, so 8 warps cover the tile.
+//   warps 2..   epilogue: warp w reads TMEM lanes 32*(w%4).. with tcgen05.ld.
+//               Float mode uses 8 epilogue warps (128 columns each, no state);
+//               exact mode uses 16 (64 columns each), so that the int32 run
+//               sums of a thread (64) stay in registers.
 // The two accumulators alternate between runs so that draining one overlaps
 // the MMAs of the next.  Every wait is bounded (%globaltimer); on a timeout
 // the kernel records SPIN_ERR_TIMEOUT, stops issuing, waits (bounded) for
@@ -47,7 +47,12 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128, BK = 64;
-constexpr int NTHREADS = 320;
+#ifndef SPIN_EXACT_BN
+#define SPIN_EXACT_BN 128
+#define SPIN_EXACT_EPI_WARPS 8
+#endif
+constexpr int kExactBN = SPIN_EXACT_BN;             // exact-mode tile width
+constexpr int kExactEpiWarps = SPIN_EXACT_EPI_WARPS;  // exact-mode epilogue warps
 constexpr uint32_t A_TILE_BYTES = BM * BK * 2;  // 16 KB
 constexpr int FLUSH_LIMIT = 96;  // exact runs summed in int32 before an FP64 flush (96 * 2^23 < 2^31)
 constexpr uint64_t WAIT_LIMIT_NS = 10ull * 1000 * 1000 * 1000;
@@ -56,8 +61,8 @@ template <int BN>
 struct Cfg {
     static constexpr uint32_t B_TILE_BYTES = BN * BK * 2;
     static constexpr uint32_t STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
-    static constexpr int STAGES = BN == 256 ? 4 : 6;
-    static constexpr uint32_t TMEM_COLS = 2 * BN;
+    static constexpr int STAGES = (196608 / STAGE_BYTES) > 6 ? 6 : (196608 / STAGE_BYTES);  // ~192 KB ring
+    static constexpr uint32_t TMEM_COLS = 2 * BN <= 256 ? 256 : 512;  // power of two >= 2 BN
     static constexpr size_t SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256 /*barriers etc.*/;
 };
 constexpr int STAGES_MAX = 6;
@@ -72,20 +77,30 @@ struct SmemCtl {
     int abort;
 };
 
+// 2^e for -1022 <= e <= 1023, built from the exponent bits (exact).
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
 __device__ __forceinline__ void raise_timeout(SmemCtl* ctl, int* err) {
     ctl->abort = 1;
     if (err) atomicCAS(err, 0, SPIN_ERR_TIMEOUT);
 }
 
-template <int BN, bool EXACT>
-__global__ void __launch_bounds__(NTHREADS, 1)
+template <int EPI_WARPS>
+struct Epi {
+    static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+    static constexpr int MAXREG = (65536 / THREADS) / 8 * 8 > 255 ? 248 : (65536 / THREADS) / 8 * 8;
+};
+
+template <int BN, bool EXACT, int EPI_WARPS>
+__global__ void __maxnreg__(Epi<EPI_WARPS>::MAXREG)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const TcGemmParams p) {
     constexpr int STAGES = Cfg<BN>::STAGES;
     constexpr uint32_t B_TILE_BYTES = Cfg<BN>::B_TILE_BYTES;
     constexpr uint32_t STAGE_BYTES = Cfg<BN>::STAGE_BYTES;
     constexpr uint32_t TMEM_COLS = Cfg<BN>::TMEM_COLS;
-    constexpr int HALF = BN / 2;  // columns per epilogue warp
+    constexpr int HALF = BN / (EPI_WARPS / 4);  // columns per epilogue warp
+    static_assert(EPI_WARPS % 4 == 0 && BN % (EPI_WARPS / 4) == 0 && HALF % 16 == 0, "epilogue split");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* smA = base;
@@ -105,7 +120,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(&ctl->tfull[b], 1);
-            mbar_init(&ctl->tempty[b], 8);
+            mbar_init(&ctl->tempty[b], EPI_WARPS);
         }
         mbar_init(&ctl->final_bar, 1);
         ctl->abort = 0;
@@ -215,9 +230,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         __syncwarp();
     } else {
         // ------------------------------------------------------ epilogue --
-        const int e = warp - 2;         // 0..7
+        const int e = warp - 2;         // 0 .. EPI_WARPS-1
         const int quarter = warp & 3;   // TMEM lane quarter this warp may access
-        const int half = e >> 2;        // column half of the tile
+        const int half = e >> 2;        // column group of the tile
         const int row = quarter * 32 + lane;
         const int grow = m0 + row;
         const bool row_ok = grow < p.M;
@@ -231,15 +246,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             tc_fence_after();
             if (ok) {
 #pragma unroll 1
-                for (int cc = 0; cc < HALF; cc += 32) {
-                    uint32_t v[32];
-                    tmem_ld_32x32b_x32(lane_addr + (uint32_t)(half * HALF + cc), v);
+                for (int cc = 0; cc < HALF; cc += 16) {
+                    uint32_t v[16];
+                    tmem_ld_32x32b_x16(lane_addr + (uint32_t)(half * HALF + cc), v);
                     tmem_ld_wait();
                     if (row_ok) {
                         const double* crow = p.C ? p.C + (int64_t)grow * p.ldc : nullptr;
                         double* drow = p.D + (int64_t)grow * p.ldd;
 #pragma unroll
-                        for (int j = 0; j < 32; j++) {
+                        for (int j = 0; j < 16; j++) {
                             const int gcol = col0 + cc + j;
                             if (gcol < p.N) {
                                 double val = p.alpha * (double)__uint_as_float(v[j]);
@@ -273,12 +288,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     }
                     tc_fence_after();
 #pragma unroll
-                    for (int cc = 0; cc < HALF; cc += 32) {
-                        uint32_t v[32];
-                        tmem_ld_32x32b_x32(lane_addr + (uint32_t)(buf * BN + half * HALF + cc), v);
+                    for (int cc = 0; cc < HALF; cc += 16) {
+                        uint32_t v[16];
+                        tmem_ld_32x32b_x16(lane_addr + (uint32_t)(buf * BN + half * HALF + cc), v);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 32; j++) acc[cc + j] += __float2int_rn(__uint_as_float(v[j]));
+                        for (int j = 0; j < 16; j++) acc[cc + j] += __float2int_rn(__uint_as_float(v[j]));
                     }
                     tc_fence_before();
                     __syncwarp();
@@ -290,25 +305,37 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     const bool last = (c == nchunks_per_pair - 1) && (q == p.num_pairs - 1);
                     if (group_end || since_flush >= FLUSH_LIMIT) {
                         if (row_ok) {
-                            const int shift = p.group_shift[(int)p.pg[q]];
+                            // exact powers of two: 2^(e_row + shift) * 2^(e_col) * integer
+                            const int er = erow + p.group_shift[(int)p.pg[q]];
+                            const bool fast = er >= -1000 && er <= 1000;
+                            const double srow = fast ? pow2(er) : 0.0;
                             double* drow = p.D + (int64_t)grow * p.ldd;
                             const double* crow = p.C ? p.C + (int64_t)grow * p.ldc : nullptr;
 #pragma unroll
-                            for (int j = 0; j < HALF; j++) {
-                                const int gcol = col0 + j;
-                                if (gcol < p.N) {
-                                    const int ex = erow + (p.col_exp ? p.col_exp[gcol] : 0) + shift;
-                                    double val = p.alpha * ldexp((double)acc[j], ex);
-                                    if (first_flush) {
-                                        if (p.beta != 0.0) val = fma(p.beta, crow[gcol], val);
-                                        if (p.add_identity && gcol == grow) val += 1.0;
-                                    } else {
-                                        val += drow[gcol];
+                            for (int jj = 0; jj < HALF; jj += 16) {
+                                // keep the compiler from hoisting every column's loads at once
+                                asm volatile("" ::: "memory");
+#pragma unroll
+                                for (int j = jj; j < jj + 16; j++) {
+                                    const int gcol = col0 + j;
+                                    if (gcol < p.N) {
+                                        const int ec = p.col_exp ? p.col_exp[gcol] : 0;
+                                        double val;
+                                        if (fast && ec >= -1000 && ec <= 1000)
+                                            val = p.alpha * ((double)acc[j] * srow) * pow2(ec);
+                                        else
+                                            val = p.alpha * ldexp((double)acc[j], er + ec);
+                                        if (first_flush) {
+                                            if (p.beta != 0.0) val = fma(p.beta, crow[gcol], val);
+                                            if (p.add_identity && gcol == grow) val += 1.0;
+                                        } else {
+                                            val += drow[gcol];
+                                        }
+                                        drow[gcol] = val;
+                                        if (last) sumsq = fma(val, val, sumsq);
                                     }
-                                    drow[gcol] = val;
-                                    if (last) sumsq = fma(val, val, sumsq);
+                                    acc[j] = 0;
                                 }
-                                acc[j] = 0;
                             }
                         } else {
 #pragma unroll
@@ -524,7 +551,7 @@ int make_map(CUtensorMap* m, const uint16_t* base, int64_t inner, int64_t outer,
     return r == CUDA_SUCCESS ? SPIN_OK : SPIN_ERR_CUDA;
 }
 
-template <int BN, bool EXACT>
+template <int BN, bool EXACT, int EPI_WARPS>
 int launch_impl(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, cudaStream_t s) {
     CUtensorMap ta, tb;
     int rc = make_map(&ta, a.base, p.K, (int64_t)a.rows * a.slices, a.ld, BM);
@@ -532,13 +559,13 @@ int launch_impl(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, c
     rc = make_map(&tb, b.base, p.K, (int64_t)b.rows * b.slices, b.ld, BN);
     if (rc) return rc;
     static bool attr = false;
-    auto kern = tc_gemm_kernel<BN, EXACT>;
+    auto kern = tc_gemm_kernel<BN, EXACT, EPI_WARPS>;
     if (!attr) {
         SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<BN>::SMEM_BYTES));
         attr = true;
     }
     dim3 grid((unsigned)((p.N + BN - 1) / BN), (unsigned)((p.M + BM - 1) / BM));
-    kern<<<grid, NTHREADS, Cfg<BN>::SMEM_BYTES, s>>>(ta, tb, p);
+    kern<<<grid, Epi<EPI_WARPS>::THREADS, Cfg<BN>::SMEM_BYTES, s>>>(ta, tb, p);
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
 }
@@ -554,8 +581,8 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& p
     TcGemmParams p = prm;
     p.a_rows = a.rows;
     p.b_rows = b.rows;
-    if (prm.exact) return launch_impl<128, true>(a, b, p, s);
-    return launch_impl<256, false>(a, b, p, s);
+    if (prm.exact) return launch_impl<kExactBN, true, kExactEpiWarps>(a, b, p, s);
+    return launch_impl<256, false, 8>(a, b, p, s);
 }
 
 int launch_split_bf16x2(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,

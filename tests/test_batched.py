@@ -1,0 +1,82 @@
+"""spin_invert_batched against the oracle: a batch of matrices of uneven
+orders (log-uniform, multiples of 32, as in the batching workload), each
+result compared with the oracle's Algorithm 1 at the same leaf size."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1801_04723_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def spin():
+    import paper_1801_04723_gb300 as s
+
+    s.build()
+    s.lib()
+    return s
+
+
+def leaf_rule(n, leaf=0):
+    return min(leaf if leaf > 0 else (n if n <= 128 else 64), n)
+
+
+def check(A, X, leaf):
+    ref, _ = oracle.strassen_inv(A, leaf)
+    n = A.shape[0]
+    tol = 64 * n * np.linalg.cond(A) * U
+    assert np.linalg.norm(X - ref) / np.linalg.norm(ref) <= tol
+    assert oracle.residual(A, X)[0] <= 1e-13
+
+
+def test_batch_uneven_orders(spin):
+    orders = inputs.batch_orders(48, seed=inputs.SEED_BASE + 3)
+    orders = np.concatenate([orders, [32, 32, 1024, 96, 1, 5, 130]])
+    mats = [inputs.sdd(int(n), seed=1000 + i) for i, n in enumerate(orders)]
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    Xs, info = spin.invert_batched(As)
+    torch.cuda.synchronize()
+    assert int(info.abs().sum()) == 0
+    for i in range(0, len(mats), 5):  # oracle on a sample of the batch
+        check(mats[i], Xs[i].cpu().numpy(), leaf_rule(len(mats[i])))
+
+
+def test_batch_replay_strided_and_singular(spin):
+    big = torch.zeros((700, 900), dtype=torch.float64, device="cuda:0")
+    a0 = inputs.spd_gram(300, seed=5)
+    big[10:310, 20:320] = torch.from_numpy(a0).cuda()
+    sing = torch.tensor([[0.0, 1.0], [1.0, 0.0]], dtype=torch.float64, device="cuda:0")
+    a2 = torch.from_numpy(inputs.sdd(64, seed=6)).cuda()
+    As = [big[10:310, 20:320], sing, a2]
+    Xs, info = spin.invert_batched(As)
+    torch.cuda.synchronize()
+    st = info.cpu().tolist()
+    assert st[0] == 0 and st[2] == 0
+    # order 2 with leaf 2 (n <= 128: the whole matrix is the leaf) pivots: not singular
+    assert st[1] == 0
+    np.testing.assert_array_equal(Xs[1].cpu().numpy(), sing.cpu().numpy())
+    check(a0, Xs[0].cpu().numpy(), 64)
+    first = [x.clone() for x in Xs]
+    Xs2, info2 = spin.invert_batched(As, outs=Xs)  # same arguments: graph replay
+    torch.cuda.synchronize()
+    for a, b in zip(first, Xs2):
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    # leaf 1 on the 2x2 permutation: A11 = 0 is singular
+    Xs3, info3 = spin.invert_batched([sing, a2], leaf=1)
+    torch.cuda.synchronize()
+    assert info3.cpu().tolist()[0] == 2 and info3.cpu().tolist()[1] == 0
+
+
+def test_batch_matches_single_calls(spin):
+    mats = [inputs.spd_gram(n, seed=n) for n in (256, 256, 512, 320)]
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    Xs, info = spin.invert_batched(As, leaf=64)
+    for a, x in zip(As, Xs):
+        xs, _ = spin.invert(a, leaf=64)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(x.cpu().numpy(), xs.cpu().numpy())

@@ -1,0 +1,82 @@
+"""Serving: requests of mixed orders and precisions submitted while others
+run; every result must equal the same request run alone (bit for bit on the
+plain path, whose kernels are deterministic; within the requested residual
+on the mixed path), and admission must respect the memory budget."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1801_04723_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def spin():
+    import paper_1801_04723_gb300 as s
+
+    s.build()
+    s.lib()
+    return s
+
+
+def test_serve_mix_equals_alone(spin):
+    trace = inputs.serve_trace(inputs.SEED_BASE + 4004, rate=400.0, duration=0.08, lo=64, hi=1024)
+    assert len(trace) >= 20
+    srv = spin.Server(hbm_budget_bytes=16 << 30, max_slots=4)
+    reqs = []
+    t0 = time.perf_counter()
+    for j, (t_arr, n, alpha, mixed) in enumerate(trace):
+        A = inputs.spd_gram(n, seed=inputs.SEED_BASE + 4000 + j, alpha=alpha)
+        src = torch.from_numpy(A).cuda() if j % 3 else A  # device and host submissions
+        prec, tol = ("bf16x3", 1e-10) if mixed else ("fp64", 1e-13)
+        while time.perf_counter() - t0 < t_arr:
+            time.sleep(0.001)
+        reqs.append((srv.submit(src, precision=prec, tol=tol), A, prec, tol))
+    results = {}
+    deadline = time.time() + 300
+    while len(results) < len(reqs) and time.time() < deadline:
+        for t, A, prec, tol in reqs:
+            if t in results:
+                continue
+            got = srv.poll(t)
+            if got is not None:
+                results[t] = got
+        time.sleep(0.002)
+    st = srv.stats()
+    srv.close()
+    assert len(results) == len(reqs)
+    assert st["completed"] == st["submitted"] == len(reqs) and st["rejected"] == 0
+    for t, A, prec, tol in reqs:
+        X, r = results[t]
+        assert r["status"] == 0, r
+        alone, info = spin.invert(torch.from_numpy(A).cuda(), precision=prec, tol=tol)
+        alone = alone.cpu().numpy()
+        if prec == "fp64":
+            np.testing.assert_array_equal(X, alone)
+            assert oracle.residual(A, X)[0] <= 1e-13
+        else:
+            assert r["rel_residual"] <= tol and oracle.residual(A, X)[0] <= tol
+            assert np.linalg.norm(X - alone) / np.linalg.norm(alone) <= np.linalg.cond(A) * 10 * tol
+        assert r["latency_ms"] >= r["run_ms"] > 0
+
+
+def test_serve_budget_and_errors(spin):
+    srv = spin.Server(hbm_budget_bytes=16 << 20, max_slots=2)
+    A = torch.from_numpy(inputs.sdd(2048, seed=1)).cuda()  # X alone is 32 MB > 16 MB
+    with pytest.raises(spin.SpinError):
+        srv.submit(A, precision="fp64")
+    assert srv.stats()["rejected"] == 1
+    small = inputs.sdd(200, seed=2)  # ~0.7 MB: fits
+    t = srv.submit(small, precision="fp64")
+    while (got := srv.poll(t)) is None:
+        time.sleep(0.001)
+    X, r = got
+    assert r["status"] == 0
+    assert oracle.residual(small, X)[0] <= 1e-13
+    with pytest.raises(spin.SpinError):
+        srv.poll(t)  # already collected
+    srv.close()
