@@ -49,6 +49,10 @@ WORKLOADS = {
     "batched_fp64": dict(n=1024, leaf=0, precision="fp64", family="batch_sdd", seed=SEED_BASE + 3,
                          desc="4096 independent FP64 matrices, orders log-uniform in [32, 1024] rounded to "
                               "multiples of 32, each U(-1,1) + n I; one spin_invert_batched call (CUDA graph)"),
+    "serve": dict(n=8192, leaf=0, precision="mixed", family="serve", seed=SEED_BASE + 4,
+                  desc="serving: Poisson arrivals at 200 req/s, n log-uniform in [64, 8192], A = G G^T/n + alpha I "
+                       "(alpha uniform in [0.1, 1]); half the requests ask for residual <= 1e-13, half for "
+                       "<= 1e-10; admission by device-memory footprint under a 150 GB budget, 8 slots"),
     "mixed_bf16x3": dict(n=32768, leaf=128, precision="bf16x3", family="householder", seed=SEED_BASE + 2,
                          desc="mixed precision, one SPD matrix A = Q diag(d) Q^T (64 Householder reflectors, "
                               "d log-uniform in [1, 1e3]), n = 32768: BF16x3 tensor-core level products, FP64 "
@@ -80,6 +84,13 @@ def parse():
     ap.add_argument("--probes", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-json", default="", help="write per-launch records here")
+    ap.add_argument("--leaf-sweep", default="", help="comma-separated orders: time every candidate leaf "
+                    "(the U-shaped block-size sweep) with spin_autotune_leaf and print one JSON line")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: arrival window (s)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: Poisson arrival rate (req/s)")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-fp64-path", default="mixed", choices=["mixed", "plain"],
+                    help="path for the 1e-13 requests: mixed precision refined to 1e-13, or the plain FP64 method")
     return ap.parse_args()
 
 
@@ -192,7 +203,7 @@ def freivalds_rel(A, X, k: int, seed: int) -> float:
 def host_sample(w: dict, n_s: int):
     from paper_1801_04723_gb300 import inputs
 
-    if w["family"] == "spd_gram":
+    if w["family"] in ("spd_gram", "serve"):
         return inputs.spd_gram(n_s, seed=w["seed"])
     if w["family"] == "householder":
         return inputs.householder_spd(n_s, seed=w["seed"], reflectors=64, cond=1e3)[0]
@@ -225,6 +236,52 @@ def cpu_baseline(w: dict, seconds_hint: float = 15.0) -> dict:
                                         f"{dt:.1f} s on {oracle.num_threads()} threads"}
 
 
+def run_reference_serve(args, w: dict):
+    """The oracle serving the same request trace one request at a time on the
+    host's cores, on a bounded prefix of the trace (about 20 s of work)."""
+    import numpy as np
+
+    import oracle
+    from paper_1801_04723_gb300 import inputs
+
+    trace = inputs.serve_trace(w["seed"], rate=args.serve_rate, duration=args.serve_seconds, lo=64,
+                               hi=min(8192, w["n"]))
+    oracle.strassen_inv(np.eye(8), 2)
+    lat, flops, t_used, skipped = [], 0.0, 0.0, 0
+    rate = 5e9  # flop/s guess until the first requests are timed
+    for j, (t, n, alpha, mixed) in enumerate(trace):
+        if t_used > 20.0:
+            break
+        if t_used + 2.0 * float(n) ** 3 / rate > 30.0:  # keep the sample bounded
+            skipped += 1
+            continue
+        A = inputs.spd_gram(n, seed=w["seed"] + 7919 * (j + 1), alpha=alpha)
+        leaf = n if n <= 128 else 128
+        t0 = time.perf_counter()
+        oracle.strassen_inv(A, leaf)
+        dt = time.perf_counter() - t0
+        t_used += dt
+        lat.append(dt * 1e3)
+        flops += 2.0 * float(n) ** 3
+        rate = flops / t_used
+    val = len(lat) / t_used
+    lat.sort()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "req/s", "n_gpus": args.gpus, "steps": 1,
+        "warmup": 0, "ms_per_step": t_used * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serve", "rate_req_s": args.serve_rate, "requests_sampled": len(lat)},
+        "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+        "cpu_baseline": {"value": val, "unit": "req/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"first {len(lat)} requests of the trace ({skipped} predicted to overrun a 30 s "
+                                   f"budget skipped), served one at a time by the oracle "
+                                   f"({flops / t_used / 1e12:.4f} TFLOP/s)"},
+        "e2e": {"value": val, "unit": "req/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, w: dict, n: int, leaf: int):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -233,6 +290,9 @@ def run_reference(args, w: dict, n: int, leaf: int):
 
     import oracle
     from paper_1801_04723_gb300 import inputs
+
+    if w["family"] == "serve":
+        return run_reference_serve(args, w)
 
     n_s = min(n, 4096)
     leaf_s = sample_leaf(w, n_s)
@@ -280,6 +340,9 @@ class SingleWork:
     def step(self):
         self.spin.invert(self.A, leaf=self.leaf, precision=self.w["precision"], out=self.X, blocking=False)
 
+    def launches(self, recs, steps):
+        return len(recs)
+
     def finish(self):
         return self.spin.sync(check=False)
 
@@ -313,6 +376,9 @@ class BatchWork:
 
     def step(self):
         _, self.info = self.spin.invert_batched(self.As, leaf=self.leaf, outs=self.Xs, blocking=False)
+
+    def launches(self, recs, steps):
+        return self.spin.batched_stats()["kernels"] * steps
 
     def finish(self):
         import torch
@@ -419,6 +485,12 @@ def run_ours(args, w: dict, n: int, leaf: int):
     top = max(by_kind, key=lambda k: by_kind[k]["ms"]) if by_kind else None
     roof = None
     peaks = measured_peaks()
+    if isinstance(work, BatchWork):
+        # the batch replays one CUDA graph: no per-launch events; the whole
+        # graph is FP64-pipe bound (batched products and leaves)
+        roof = {"kernel": "batched graph (gemm_f64_batched_kernel + leaf_gj_batched_kernel)", "bound": "alu",
+                "achieved": value / world, "peak": peak_fp64, "unit": "TFLOP/s", "frac": value / world / peak_fp64,
+                "traffic": None, "peak_source": "FP64 FMA rate measured live by spin_probe_fp64_peak on this GPU"}
     if top is not None:
         d = by_kind[top]
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
@@ -460,7 +532,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
         "e2e": {"value": flops / e2e_t / 1e12 if e2e_t else None, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": work.h2d, "d2h_bytes_per_step": work.d2h,
                 "how": "host buffers (pinned), copies inside the timed call, warm-up steps 2..W, host wall clock"},
-        "gpu_launches": len(recs),
+        "gpu_launches": work.launches(recs, args.steps),
         "roofline": roof,
         "status": info["status"],
         "refine_iters": info.get("refine_iters"),
@@ -486,14 +558,149 @@ def run_ours(args, w: dict, n: int, leaf: int):
     return 0
 
 
+def run_serve(args, w: dict):
+    """Serving benchmark: replay a Poisson arrival trace against spin_serve_*."""
+    import queue
+    import threading
+
+    import torch
+
+    import paper_1801_04723_gb300 as spin
+    from paper_1801_04723_gb300 import inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    spin.build()
+    spin.lib()
+    trace = inputs.serve_trace(w["seed"] + 1000 * rank, rate=args.serve_rate, duration=args.serve_seconds,
+                               lo=64, hi=min(8192, w["n"]))
+    gen_stream = torch.cuda.Stream(device)
+
+    def make(j, n, alpha):
+        with torch.cuda.stream(gen_stream):
+            G = inputs.normal_torch(w["seed"] + 7919 * (j + 1), n, n, 0, device, torch.float32)
+            A = (G @ G.T).double() / float(n)
+            A = 0.5 * (A + A.T)
+            A.diagonal().add_(alpha)
+            ev = torch.cuda.Event()
+            ev.record(gen_stream)
+        return A, ev
+
+    ready = queue.Queue(maxsize=64)  # bounded look-ahead of generated inputs
+
+    def producer():
+        for j, (t, n, alpha, mixed) in enumerate(trace):
+            A, ev = make(j, n, alpha)
+            ready.put((j, t, n, mixed, A, ev))
+        ready.put(None)
+
+    srv = spin.Server(hbm_budget_bytes=150 << 30, max_slots=args.serve_slots)
+    pending = {}
+    done = []
+    lock = threading.Lock()
+    # warm the kernels once (both paths) outside the measured window
+    for prec, tol in (("bf16x3", 1e-10), ("fp64", 1e-13)):
+        Aw, ev = make(10 ** 6, 256, 0.5)
+        ev.synchronize()
+        spin.invert(Aw, precision=prec, tol=tol)
+    th = threading.Thread(target=producer, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    flops_done = 0.0
+    with ClockSampler(local) as clk:
+        while True:
+            item = ready.get()
+            if item is None:
+                break
+            j, t_arr, n, mixed, A, ev = item
+            while time.perf_counter() - t0 < t_arr:
+                # poll finished requests while waiting for the next arrival
+                for tk in list(pending):
+                    got = srv.poll(tk, discard=True)
+                    if got is not None:
+                        pending.pop(tk)
+                        done.append(got[1])
+                time.sleep(0.0005)
+            ev.synchronize()
+            if mixed:
+                tk = srv.submit(A, precision="bf16x3", tol=1e-10)
+            else:
+                prec = "bf16x3" if args.serve_fp64_path == "mixed" else "fp64"
+                tk = srv.submit(A, precision=prec, tol=1e-13)
+            pending[tk] = n
+            flops_done += 2.0 * float(n) ** 3
+        t_last_arrival = time.perf_counter() - t0
+        while pending:
+            for tk in list(pending):
+                got = srv.poll(tk, discard=True)
+                if got is not None:
+                    pending.pop(tk)
+                    done.append(got[1])
+            time.sleep(0.001)
+        makespan = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = sorted(r["latency_ms"] for r in done)
+    bad = sum(1 for r in done if r["status"] != 0)
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(q * len(lat)))] if lat else None
+
+    line = {
+        "metric": METRIC, "value": len(done) / makespan, "unit": "req/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
+        "config": {"workload": "serve", "rate_req_s": args.serve_rate, "arrival_window_s": args.serve_seconds,
+                   "requests": len(trace), "n_range": [64, min(8192, w["n"])], "slots": args.serve_slots,
+                   "hbm_budget_gb": 150, "fp64_class_path": args.serve_fp64_path, "desc": w["desc"]},
+        "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat[-1] if lat else None,
+        "offered_req_s": len(trace) / args.serve_seconds,
+        "offered_tflops": flops_done / args.serve_seconds / 1e12,
+        "served_tflops": flops_done / makespan / 1e12,
+        "drain_s_after_last_arrival": makespan - t_last_arrival,
+        "failed": bad, "peak_running": st["peak_running"],
+        "clocks": clk.summary(),
+        "e2e": {"value": len(done) / makespan, "unit": "req/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "how": "requests submitted from device memory; results left on the device"},
+        "gpu_launches": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_leaf_sweep(args):
+    import torch
+
+    import paper_1801_04723_gb300 as spin
+
+    spin.build()
+    prec = "fp64" if args.workload in ("plain_fp64", "small_fp64", "batched_fp64") else "bf16x3"
+    cands = (64, 128, 256, 512, 1024, 2048)
+    out = {"sweep": "leaf", "precision": prec, "candidates": list(cands), "results": []}
+    for n in [int(v) for v in args.leaf_sweep.split(",") if v]:
+        best, ms = spin.autotune_leaf(n, prec, cands)
+        out["results"].append({"n": n, "best_leaf": best,
+                               "ms": {str(k): v for k, v in ms.items()},
+                               "tflops": {str(k): 2.0 * n ** 3 / (v * 1e-3) / 1e12 for k, v in ms.items()}})
+    torch.cuda.synchronize()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.leaf_sweep:
+        return run_leaf_sweep(args)
     w = dict(WORKLOADS[args.workload])
     n = args.n if args.n > 0 else w["n"]
     leaf = args.leaf if args.leaf >= 0 else w["leaf"]
     w["n"], w["leaf"] = n, leaf
     if args.impl == "reference":
         return run_reference(args, w, n, leaf)
+    if w["family"] == "serve":
+        return run_serve(args, w)
     return run_ours(args, w, n, leaf)
 
 

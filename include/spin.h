@@ -142,6 +142,10 @@ int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t
 int spin_invert_batched(const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
                         int count, const spin_opts* opts, int* info_dev, spin_stream_t stream);
 
+/* Shape of the graph the latest spin_invert_batched on `stream` replays:
+ * kernel launches per call and order buckets.  SPIN_ERR_INVALID_ARG if none. */
+int spin_batched_stats(spin_stream_t stream, int* kernels, int* buckets);
+
 /* ---------------------------------------------------------------------
  * Serving: inversion requests admitted continuously by device-memory
  * footprint (the paper runs one job at a time; Sec. 5.1 sizes the Spark
@@ -208,8 +212,25 @@ int spin_sync(spin_stream_t stream, spin_info* info);
  * these options (the value to pass as opts->workspace_bytes). */
 size_t spin_workspace_bytes(int64_t n, const spin_opts* opts);
 
-/* The leaf order the library picks for n and a precision when leaf = 0. */
+/* The leaf order the library picks for n and a precision when leaf = 0:
+ * n itself for n <= 128, else the autotuned choice for n's size class
+ * (ceil(log2 n); a class above the largest tuned one reuses it), else a
+ * built-in default (plain: 512 for n >= 16384, else 256; mixed: 128). */
 int spin_default_leaf(int64_t n, int precision);
+
+/*
+ * spin_autotune_leaf: time one inversion (after a warm-up) per candidate
+ * leaf order on a synthetic strictly diagonally dominant matrix of order n,
+ * and record the fastest for n's size class and this precision; later calls
+ * with leaf = 0 use it.  This is the block-size trade-off the paper studies
+ * (Sec. 5.3, the U-shaped running time against the number of splits): many
+ * small leaves leave the level products small and inefficient, few large
+ * leaves make the serial leaf inversions dominate.  candidates: host array
+ * of ncand orders (orders >= n are skipped); ms_out (optional, host, ncand)
+ * receives each time (-1 if skipped).  Allocates two n x n matrices.
+ */
+int spin_autotune_leaf(int64_t n, int precision, const int* candidates, int ncand, int* leaf_out, double* ms_out,
+                       spin_stream_t stream);
 
 /*
  * spin_invert_host: X_host = A_host^-1 with both matrices in host memory

@@ -15,6 +15,7 @@ from .binding import (  # noqa: F401
     Info,
     Opts,
     default_leaf,
+    autotune_leaf,
     gemm_f64,
     gemm_bf16x3,
     gemm_ozaki,
@@ -22,6 +23,7 @@ from .binding import (  # noqa: F401
     invert,
     invert_host,
     invert_batched,
+    batched_stats,
     leaf_inverse,
     lib,
     status_string,

@@ -173,6 +173,10 @@ def lib():
         L.spin_serve_stats.restype = ctypes.c_int
         L.spin_serve_destroy.argtypes = [vp]
         L.spin_serve_destroy.restype = ctypes.c_int
+        L.spin_batched_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.spin_batched_stats.restype = ctypes.c_int
+        L.spin_autotune_leaf.argtypes = [i64, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp, vp]
+        L.spin_autotune_leaf.restype = ctypes.c_int
         L.spin_take_device_error.argtypes = [vp]
         L.spin_take_device_error.restype = ctypes.c_int
         _lib = L
@@ -401,6 +405,15 @@ def take_device_error(stream=None) -> int:
     return int(lib().spin_take_device_error(_stream(stream)))
 
 
+def batched_stats(stream=None) -> dict:
+    """Kernel launches per call and buckets of the latest batched graph on the stream."""
+    k, b = ctypes.c_int(0), ctypes.c_int(0)
+    rc = lib().spin_batched_stats(_stream(stream), ctypes.byref(k), ctypes.byref(b))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_batched_stats")
+    return {"kernels": k.value, "buckets": b.value}
+
+
 def invert_batched(As, *, leaf: int = 0, outs=None, stream=None, blocking: bool = True):
     """X_i = A_i^-1 for a list of square float64 CUDA tensors of any orders
     (spin_invert_batched).  Returns (list of X, int32 CUDA tensor of statuses)."""
@@ -459,19 +472,24 @@ class Server:
         self._keep[t.value] = A
         return t.value
 
-    def poll(self, ticket: int, out=None):
+    def poll(self, ticket: int, out=None, discard: bool = False):
         """None while busy; else (X, result dict).  X is a numpy array unless
-        ``out`` (numpy array or CUDA tensor) is given."""
+        ``out`` (numpy array or CUDA tensor) is given; with ``discard`` the
+        result is dropped on the device and X is None."""
         import numpy as np
 
         A = self._keep.get(ticket)
         n = A.shape[0] if A is not None else 0
-        if out is None:
-            out = np.empty((n, n), dtype=np.float64)
-        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
-        ld = out.stride(0) if hasattr(out, "data_ptr") else out.shape[1]
+        if discard:
+            out, ptr, ld = None, None, n
+        else:
+            if out is None:
+                out = np.empty((n, n), dtype=np.float64)
+            ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+            ld = out.stride(0) if hasattr(out, "data_ptr") else out.shape[1]
         r = Result()
-        rc = lib().spin_serve_poll(self._h, ctypes.c_uint64(ticket), ctypes.c_void_p(ptr), ld, ctypes.byref(r))
+        rc = lib().spin_serve_poll(self._h, ctypes.c_uint64(ticket), ctypes.c_void_p(ptr) if ptr else None, ld,
+                                   ctypes.byref(r))
         if rc == SPIN_ERR_BUSY:
             return None
         if rc != SPIN_OK:
@@ -495,3 +513,17 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def autotune_leaf(n: int, precision="fp64", candidates=(64, 128, 256, 512, 1024, 2048), stream=None):
+    """Time the candidate leaf orders at order n (spin_autotune_leaf); returns
+    (best leaf, {leaf: ms})."""
+    cand = [int(c) for c in candidates]
+    arr = (ctypes.c_int * len(cand))(*cand)
+    ms = (ctypes.c_double * len(cand))()
+    best = ctypes.c_int(0)
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    rc = lib().spin_autotune_leaf(int(n), p, arr, len(cand), ctypes.byref(best), ms, _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_autotune_leaf")
+    return best.value, {c: ms[i] for i, c in enumerate(cand) if ms[i] >= 0}

@@ -443,7 +443,46 @@ int enqueue(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, con
     return SPIN_OK;
 }
 
+// ---- leaf autotuning ----
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tuned;  // (precision, ceil log2 n) -> leaf
+
+int size_class(int64_t n) {
+    int c = 0;
+    while (((int64_t)1 << c) < n) c++;
+    return c;
+}
+
+__global__ void synth_sdd_kernel(double* A, int64_t n, uint64_t seed) {
+    const int64_t total = n * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;  // splitmix64 of the position
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        double v = 2.0 * (double)(z >> 11) * 0x1.0p-53 - 1.0;
+        if (i / n == i % n) v += (double)n;
+        A[i] = v;
+    }
+}
+
 }  // namespace
+
+int tuned_leaf(int64_t n, int precision) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(std::make_pair(precision, size_class(n)));
+    if (it == g_tuned.end()) {
+        // a size class above the largest tuned one reuses that class's choice
+        int best_c = -1, leaf = 0;
+        for (auto& kv : g_tuned)
+            if (kv.first.first == precision && kv.first.second <= size_class(n) && kv.first.second > best_c) {
+                best_c = kv.first.second;
+                leaf = kv.second;
+            }
+        return leaf;
+    }
+    return it->second;
+}
 
 // Internal entry for other translation units: the FP64 recursion over a
 // caller-supplied workspace W (fp64_workspace_elems(n, leaf) doubles) and
@@ -476,9 +515,70 @@ spin_opts spin_opts_default(void) {
 }
 
 int spin_default_leaf(int64_t n, int precision) {
-    (void)precision;
     if (n <= 128) return (int)(n < 1 ? 1 : n);
+    const int t = tuned_leaf(n, precision);
+    if (t > 0) return (int)std::min<int64_t>(t, n);
+    // untuned: leaves large enough that the FP64 leaf kernel keeps its
+    // cluster busy, small enough that leaf work stays a few percent
+    if (precision == SPIN_FP64) return n >= 16384 ? 512 : 256;
     return 128;
+}
+
+int spin_autotune_leaf(int64_t n, int precision, const int* candidates, int ncand, int* leaf_out, double* ms_out,
+                       spin_stream_t stream) {
+    if (n < 2 || ncand < 1 || candidates == nullptr || leaf_out == nullptr) return SPIN_ERR_INVALID_ARG;
+    if (precision < SPIN_FP64 || precision > SPIN_MIXED_BF16X3) return SPIN_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    StreamState* st = nullptr;
+    RET(get_state(s, &st));
+    double* A = nullptr;
+    double* X = nullptr;
+    const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
+    if (cudaMalloc(&A, bytes) != cudaSuccess || cudaMalloc(&X, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(A);
+        return SPIN_ERR_OOM;
+    }
+    synth_sdd_kernel<<<1024, 256, 0, s>>>(A, n, 0x5EED5EEDull);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = -1, rc = SPIN_OK;
+    float best_ms = 1e30f;
+    for (int i = 0; i < ncand && rc == SPIN_OK; i++) {
+        const int L = candidates[i];
+        if (ms_out) ms_out[i] = -1.0;
+        if (L < 1 || L > kMaxLeaf || L >= n) continue;
+        spin_opts o = spin_opts_default();
+        o.precision = precision;
+        o.leaf = L;
+        spin_info info;
+        rc = spin_invert_ex(A, n, X, n, n, &o, &info, stream);  // warm (workspace, modules)
+        if (rc != SPIN_OK) break;
+        cudaEventRecord(e0, s);
+        rc = spin_invert_ex(A, n, X, n, n, &o, &info, stream);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_out) ms_out[i] = ms;
+        if (rc == SPIN_OK && info.status == SPIN_OK && ms < best_ms) {
+            best_ms = ms;
+            best = L;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(A);
+    cudaFree(X);
+    if (rc != SPIN_OK) return rc;
+    if (best < 0) return SPIN_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[std::make_pair(precision, size_class(n))] = best;
+    }
+    *leaf_out = best;
+    return SPIN_OK;
 }
 
 size_t spin_workspace_bytes(int64_t n, const spin_opts* opts) {

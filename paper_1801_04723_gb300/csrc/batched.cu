@@ -47,6 +47,7 @@ struct BatchPlan {
     double* ws = nullptr;
     size_t ws_bytes = 0;
     int count = 0;
+    int kernels = 0;  // kernel launches in the captured graph
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;  // private stream the launch sequence is captured on
     cudaStream_t streams[kStreams] = {};
@@ -81,6 +82,7 @@ __global__ void scatter_status_kernel(const int32_t* records, const int* user_in
 }
 
 struct BRun {
+    int* kernels;  // launch counter
     cudaStream_t s;
     int32_t* records;  // bucket's first record
     int leaf_counter;
@@ -107,8 +109,10 @@ BatchView sub(BatchView v, int64_t dr, int64_t dc) {
 int binv(BRun& r, BatchView A, BatchView X, const double* const* wbase, int64_t woff, int64_t n) {
     if (n <= r.leaf) {
         double* scratch = leaf_scratch_elems(n) ? r.ws_block + woff : nullptr;
+        (*r.kernels)++;
         return launch_leaf_gj_batched(A, X, n, scratch, r.ws_stride, r.records, r.leaf_counter++, r.count, r.s);
     }
+    *r.kernels += 6;
     const int64_t n1 = split_order(n), n2 = n - n1;
     BatchView A11 = A, A12 = sub(A, 0, n1), A21 = sub(A, n1, 0), A22 = sub(A, n1, n1);
     BatchView X11 = X, X12 = sub(X, 0, n1), X21 = sub(X, n1, 0), X22 = sub(X, n1, n1);
@@ -137,6 +141,7 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
                int count, int leaf_opt, int* info_dev, cudaStream_t s) {
     free_plan(p);
     p.count = count;
+    p.kernels = 0;
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] < n[b]; });
@@ -219,7 +224,7 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
         const Bucket& b = p.buckets[bi];
         const int si = (int)(std::min_element(load.begin(), load.end()) - load.begin());
         load[si] += (double)b.count * b.n * b.n * b.n;
-        BRun r{p.streams[si], p.records + (int64_t)b.first * INFO_WORDS, 0, b.leaf, b.count,
+        BRun r{&p.kernels, p.streams[si], p.records + (int64_t)b.first * INFO_WORDS, 0, b.leaf, b.count,
                p.ws + b.ws_offset, (int64_t)b.ws_elems};
         BatchView Av{p.a_base + b.first, p.a_ld + b.first, 0, 0, 0};
         BatchView Xv{(const double* const*)(p.x_base + b.first), nullptr, b.n, 0, 0};
@@ -234,6 +239,7 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
         }
     }
     if (rc == SPIN_OK && info_dev != nullptr) {
+        p.kernels++;
         scatter_status_kernel<<<(count + 255) / 256, 256, 0, s>>>(p.records, p.user_index, count, info_dev);
         cudaError_t e3 = cudaGetLastError();
         if (e3 != cudaSuccess) {
@@ -304,5 +310,14 @@ extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, d
     }
     SPIN_CUDA_TRY(cudaGraphLaunch(p.exec, s));
     if (o.blocking) SPIN_CUDA_TRY(cudaStreamSynchronize(s));
+    return SPIN_OK;
+}
+
+extern "C" int spin_batched_stats(spin_stream_t stream, int* kernels, int* buckets) {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    auto it = g_plans.find((cudaStream_t)stream);
+    if (it == g_plans.end() || it->second.exec == nullptr) return SPIN_ERR_INVALID_ARG;
+    if (kernels) *kernels = it->second.kernels;
+    if (buckets) *buckets = (int)it->second.buckets.size();
     return SPIN_OK;
 }

@@ -88,7 +88,9 @@ __device__ __forceinline__ void raise_timeout(SmemCtl* ctl, int* err) {
 template <int EPI_WARPS>
 struct Epi {
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;
-    static constexpr int MAXREG = (65536 / THREADS) / 8 * 8 > 255 ? 248 : (65536 / THREADS) / 8 * 8;
+    // registers are granted per group of four warps: budget for the rounded-up count
+    static constexpr int ALLOC_THREADS = (THREADS + 127) / 128 * 128;
+    static constexpr int MAXREG = (65536 / ALLOC_THREADS) / 8 * 8 > 255 ? 248 : (65536 / ALLOC_THREADS) / 8 * 8;
 };
 
 template <int BN, bool EXACT, int EPI_WARPS>

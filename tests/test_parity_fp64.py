@@ -249,3 +249,15 @@ def test_householder_known_inverse(spin):
     ref = inputs.householder_apply(V, 1.0 / d, np.eye(1024))
     assert rel(X, ref) < 1e-11
     assert oracle.residual(A, X)[0] <= 1e-13
+
+
+def test_autotune_leaf_records_choice(spin):
+    best, ms = spin.autotune_leaf(1024, "fp64", candidates=(64, 128, 256, 2048))
+    assert best in (64, 128, 256) and set(ms) == {64, 128, 256}  # 2048 >= n is skipped
+    assert best == min(ms, key=ms.get)
+    assert spin.default_leaf(1024) == best
+    assert spin.default_leaf(1500) == best  # a larger size class reuses the largest tuned one
+    A = inputs.sdd(1024, seed=77)
+    X, info = spin.invert(dev(A))  # leaf 0 -> the tuned leaf
+    ref, _ = oracle.strassen_inv(A, best)
+    assert rel(host(X), ref) <= tol(A)
