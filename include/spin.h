@@ -204,6 +204,27 @@ int spin_serve_stats(spin_server* sv, spin_serve_stats_t* st);
 /* Stop the slots (running requests finish), free everything. */
 int spin_serve_destroy(spin_server* sv);
 
+/*
+ * spin_invert_noalloc: spin_invert for callers that must not allocate device
+ * memory (the paper has no counterpart; it is a deployment variant).  A
+ * process whose device memory is reserved up front by another allocator, or
+ * code that cannot pay for the device-wide synchronisation of cudaMalloc /
+ * cudaFree, can call this instead: it calls neither, and no allocating
+ * library routine either.  Its workspace and status record live in one
+ * fixed 8 MB array in device global memory that every GPU loading the
+ * library keeps until exit, so the order is limited to problems whose
+ * workspace fits it (n <= 1024 at any leaf <= 512; larger n, or a leaf whose
+ * scratch does not fit, returns SPIN_ERR_INVALID_ARG before any work).
+ *   A, X, n, lda, leaf, stream: as spin_invert (X has leading dimension n).
+ * Blocking: returns the numerical status after the stream has finished.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the one array:
+ * calls that may overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller.
+ */
+int spin_invert_noalloc(const double* A, double* X, int64_t n, int64_t lda, int leaf, spin_stream_t stream);
+
 /* Synchronise the stream and fill *info with the status of the latest
  * non-blocking spin_invert_ex enqueued on it by this thread. */
 int spin_sync(spin_stream_t stream, spin_info* info);

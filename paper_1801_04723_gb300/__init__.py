@@ -22,6 +22,7 @@ from .binding import (  # noqa: F401
     take_device_error,
     invert,
     invert_host,
+    invert_noalloc,
     invert_batched,
     batched_stats,
     leaf_inverse,

@@ -179,6 +179,8 @@ def lib():
         L.spin_autotune_leaf.restype = ctypes.c_int
         L.spin_take_device_error.argtypes = [vp]
         L.spin_take_device_error.restype = ctypes.c_int
+        L.spin_invert_noalloc.argtypes = [vp, vp, i64, i64, ctypes.c_int, vp]
+        L.spin_invert_noalloc.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -403,6 +405,21 @@ def gemm_ozaki(A, B, *, slices=7, alpha=1.0, beta=0.0, C=None, out=None, add_ide
 
 def take_device_error(stream=None) -> int:
     return int(lib().spin_take_device_error(_stream(stream)))
+
+
+def invert_noalloc(A, *, leaf: int = 0, out=None, stream=None):
+    """X = A^-1 through spin_invert_noalloc (no device allocation by the
+    library; fixed 8 MB workspace per device).  Returns (X, status)."""
+    import torch
+
+    _check_matrix(A, "A")
+    n = A.shape[0]
+    X = out if out is not None else torch.empty((n, n), dtype=torch.float64, device=A.device)
+    if X.stride(0) != n:
+        raise ValueError("X must be contiguous (leading dimension n)")
+    rc = lib().spin_invert_noalloc(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(X.data_ptr()), n, A.stride(0),
+                                   int(leaf), _stream(stream))
+    return X, int(rc)
 
 
 def batched_stats(stream=None) -> dict:
