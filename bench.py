@@ -53,6 +53,9 @@ WORKLOADS = {
                   desc="serving: Poisson arrivals at 200 req/s, n log-uniform in [64, 8192], A = G G^T/n + alpha I "
                        "(alpha uniform in [0.1, 1]); half the requests ask for residual <= 1e-13, half for "
                        "<= 1e-10; admission by device-memory footprint under a 150 GB budget, 8 slots"),
+    "mixed_digits": dict(n=32768, leaf=128, precision="digits", family="householder", seed=SEED_BASE + 2,
+                         desc="as mixed_bf16x3 but the level products are 4-slice BF16 digit products with exact "
+                              "FP32 runs (~2^-30), so the first residual usually certifies the result"),
     "mixed_bf16x3": dict(n=32768, leaf=128, precision="bf16x3", family="householder", seed=SEED_BASE + 2,
                          desc="mixed precision, one SPD matrix A = Q diag(d) Q^T (64 Householder reflectors, "
                               "d log-uniform in [1, 1e3]), n = 32768: BF16x3 tensor-core level products, FP64 "
@@ -86,6 +89,8 @@ def parse():
     ap.add_argument("--profile-json", default="", help="write per-launch records here")
     ap.add_argument("--leaf-sweep", default="", help="comma-separated orders: time every candidate leaf "
                     "(the U-shaped block-size sweep) with spin_autotune_leaf and print one JSON line")
+    ap.add_argument("--gemm-probe", type=int, default=0, help="time one digit-slice (6 slices) and one bf16x3 "
+                    "tensor-core product of this order and print one JSON line")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: arrival window (s)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: Poisson arrival rate (req/s)")
     ap.add_argument("--serve-slots", type=int, default=8)
@@ -526,7 +531,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if w["precision"] == "fp64" else "bf16x3+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if w["precision"] == "fp64" else ("bf16x3+f64" if w["precision"] == "bf16x3" else "bf16-digits+f64"), "data": "synthetic",
         "config": config,
         "clocks": clk.summary(),
         "e2e": {"value": flops / e2e_t / 1e12 if e2e_t else None, "unit": "TFLOP/s",
@@ -670,6 +675,34 @@ def run_serve(args, w: dict):
     return 0
 
 
+def run_gemm_probe(args):
+    import torch
+
+    import paper_1801_04723_gb300 as spin
+    from paper_1801_04723_gb300 import inputs
+
+    spin.build()
+    n = args.gemm_probe
+    A = inputs.sdd_device(n, SEED_BASE + 11, "cuda")
+    B = inputs.sdd_device(n, SEED_BASE + 12, "cuda")
+    D = torch.empty_like(A)
+    out = {"probe": "tensor-core products", "n": n}
+    for name, fn, pairs in (("ozaki6", lambda: spin.gemm_ozaki(A, B, slices=6, out=D), 21),
+                            ("bf16x3", lambda: spin.gemm_bf16x3(A, B, out=D), 3)):
+        fn()  # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"ms_with_splits": ms, "bf16_tflops_incl_splits": pairs * 2.0 * n ** 3 / (ms * 1e-3) / 1e12}
+    out["device_error"] = spin.take_device_error()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_leaf_sweep(args):
     import torch
 
@@ -693,6 +726,8 @@ def main():
     args = parse()
     if args.leaf_sweep:
         return run_leaf_sweep(args)
+    if args.gemm_probe:
+        return run_gemm_probe(args)
     w = dict(WORKLOADS[args.workload])
     n = args.n if args.n > 0 else w["n"]
     leaf = args.leaf if args.leaf >= 0 else w["leaf"]

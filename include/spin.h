@@ -63,7 +63,11 @@ typedef enum {
     SPIN_FP64 = 0,         /* every product in FP64 (plain method)                           */
     SPIN_MIXED_BF16X3 = 1, /* products on BF16 tensor cores with 3-term splits, FP32 accumulate,
                               then Newton-Schulz refinement to opts.tol                       */
-    SPIN_MIXED_TF32 = 2    /* as above with TF32 operands                                     */
+    SPIN_MIXED_TF32 = 2,   /* reserved: TF32 operands (returns SPIN_ERR_NOT_IMPLEMENTED)      */
+    SPIN_MIXED_DIGITS = 3  /* products on BF16 tensor cores as 4-slice fixed-point digit
+                              products with exact FP32 runs (~2^-30 relative), then the same
+                              refinement -- which usually stops at its first, certifying
+                              residual                                                    */
 } spin_precision;
 
 /* Options of spin_invert_ex.  Zero-initialise and set what you need;

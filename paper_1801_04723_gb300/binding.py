@@ -22,8 +22,9 @@ SPIN_ERR_NOT_IMPLEMENTED = 8
 SPIN_FP64 = 0
 SPIN_MIXED_BF16X3 = 1
 SPIN_MIXED_TF32 = 2
+SPIN_MIXED_DIGITS = 3
 
-PRECISIONS = {"fp64": SPIN_FP64, "bf16x3": SPIN_MIXED_BF16X3, "tf32": SPIN_MIXED_TF32}
+PRECISIONS = {"fp64": SPIN_FP64, "bf16x3": SPIN_MIXED_BF16X3, "tf32": SPIN_MIXED_TF32, "digits": SPIN_MIXED_DIGITS}
 
 
 class Opts(ctypes.Structure):

@@ -22,6 +22,7 @@
 // ws(n) = max(ws(n1), n1 n2 + n2^2 + ws(n2)) elements (2n^2/3 for n = 2^p).
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -149,6 +150,7 @@ struct Run {
 
 constexpr int kTcMin = 128;     // products smaller than this in m or n stay in FP64
 constexpr int kSchurSlices = 7; // digit slices of the FP64-class Schur complements
+constexpr int kLevelSlices = 4; // digit slices of the level products in SPIN_MIXED_DIGITS
 
 // Bracket one launch with events when the stream's profiler is on.
 struct ProfScope {
@@ -203,19 +205,21 @@ int level_gemm(Run& r, int depth, bool schur, int64_t m, int64_t n, int64_t k, d
     const double f = 2.0 * (double)m * (double)n * (double)k;
     SplitPlan sp;
     int rc;
-    if (schur && depth < r.fp64_levels) {
-        RET(plan_ozaki(m, n, k, kSchurSlices, r.scratch, r.scratch_bytes, &sp));
+    const bool fp64_schur = schur && depth < r.fp64_levels;
+    if (fp64_schur || r.precision == SPIN_MIXED_DIGITS) {
+        const int sl = fp64_schur ? kSchurSlices : kLevelSlices;
+        RET(plan_ozaki(m, n, k, sl, r.scratch, r.scratch_bytes, &sp));
         {
-            ProfScope ps(r.prof, r.s, SPIN_KERNEL_SPLIT, depth, m, k, 0, 0.0, 8.0 * m * k + 2.0 * kSchurSlices * m * k);
+            ProfScope ps(r.prof, r.s, SPIN_KERNEL_SPLIT, depth, m, k, 0, 0.0, 8.0 * m * k + 2.0 * sl * m * k);
             RET(split_a_ozaki(sp, A, lda, m, k, nullptr, r.s));
         }
         {
-            ProfScope ps(r.prof, r.s, SPIN_KERNEL_SPLIT, depth, k, n, 0, 0.0, 8.0 * k * n + 2.0 * kSchurSlices * k * n);
+            ProfScope ps(r.prof, r.s, SPIN_KERNEL_SPLIT, depth, k, n, 0, 0.0, 8.0 * k * n + 2.0 * sl * k * n);
             RET(split_b_ozaki(sp, B, ldb, k, n, nullptr, r.s));
         }
-        const int pairs = kSchurSlices * (kSchurSlices + 1) / 2;
+        const int pairs = sl * (sl + 1) / 2;
         ProfScope ps(r.prof, r.s, SPIN_KERNEL_GEMM_TC, depth, m, n, k, pairs * f,
-                     2.0 * kSchurSlices * (m * k + k * n) + 8.0 * m * n * (beta != 0.0 ? 2 : 1));
+                     2.0 * sl * (m * k + k * n) + 8.0 * m * n * (beta != 0.0 ? 2 : 1));
         rc = product_ozaki(sp, m, n, k, alpha, beta, C, ldc, D, ldd, 0, nullptr, r.err, r.s);
         return rc;
     }
@@ -323,9 +327,10 @@ MixLayout mix_layout(int64_t n, int64_t leaf, const spin_opts& o) {
         const int64_t n1 = split_order(n);
         sc = bf16x3_scratch_bytes(n1, n1, n1);
         if (o.fp64_levels > 0) sc = std::max(sc, ozaki_scratch_bytes(n1, n1, n1, kSchurSlices));
+        if (o.precision == SPIN_MIXED_DIGITS) sc = std::max(sc, ozaki_scratch_bytes(n1, n1, n1, kLevelSlices));
     }
     sc = std::max(sc, ozaki_scratch_bytes(0, n, n, L.sr));
-    sc = std::max(sc, bf16x3_scratch_bytes(n, n, n));
+    sc = std::max(sc, bf16x6_scratch_bytes(n, n, n));
     L.scratch = round256(sc);
     L.apl = round256((size_t)L.sr * (size_t)n * (size_t)tc_ld(n) * 2 + (size_t)n * 4 + 512);
     L.off_scratch = L.region0;
@@ -341,9 +346,12 @@ size_t workspace_bytes_for(int64_t n, int64_t leaf, const spin_opts& o) {
 }
 
 // Newton-Schulz refinement X <- X + X (I - A X) (Bailey-style stabilisation
-// of Strassen's inversion, cited in Sec. 2.1): the residual is FP64-class
-// (digit slices of A, cached, and of X), the correction X R is bf16x3.
-// Stops when ||AX - I||_F / (||A||_F ||X||_F) <= tol.
+// of Strassen's inversion, cited in Sec. 2.1): every residual R = I - A X is
+// FP64-class (digit slices of A, split once and cached, and of X), the
+// correction X R is a six-product BF16 form.  Every residual is recomputed
+// in full: after a step the true residual is dominated by the previous
+// residual's own rounding error, which an update of the form R - A (dX)
+// cannot see.  Stops when ||AX - I||_F / (||A||_F ||X||_F) <= tol.
 int refine(Run& r, StreamState* st, const double* A, int64_t lda, double* X, int64_t ldx, int64_t n,
            const spin_opts& o, const MixLayout& L, unsigned char* ws) {
     cudaStream_t s = r.s;
@@ -358,28 +366,31 @@ int refine(Run& r, StreamState* st, const double* A, int64_t lda, double* X, int
         RET(ozaki_split_a(A, lda, n, n, L.sr, &ca, &norms[0], s));
     }
     const double f = 2.0 * (double)n * n * n;
-    const int pairs = L.sr * (L.sr + 1) / 2;
     st->last_refine_iters = 0;
     st->last_rel = -1.0;
+    const bool verbose = getenv("SPIN_VERBOSE") != nullptr;
     for (int it = 0;; it++) {
+        const int sr = L.sr;
+        const int pairs = sr * (sr + 1) / 2;
         SPIN_CUDA_TRY(cudaMemsetAsync(norms + 1, 0, 2 * sizeof(double), s));
         SplitPlan sp;
-        RET(plan_ozaki(0, n, n, L.sr, scratch, L.scratch, &sp));
+        RET(plan_ozaki(0, n, n, sr, scratch, L.scratch, &sp));
         sp.a = ca.planes;
         sp.ea = ca.exps;
         {
-            ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 8.0 * n * n + 2.0 * L.sr * n * n);
+            ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 8.0 * n * n + 2.0 * sr * n * n);
             RET(split_b_ozaki(sp, X, ldx, n, n, &norms[1], s));
         }
         {
             ProfScope ps(r.prof, s, SPIN_KERNEL_RESIDUAL, -1, n, n, n, pairs * f,
-                         2.0 * L.sr * 2.0 * n * n + 8.0 * n * n);
+                         2.0 * sr * 2.0 * n * n + 8.0 * n * n);
             RET(product_ozaki(sp, n, n, n, -1.0, 0.0, nullptr, 0, R, n, 1, &norms[2], r.err, s));
         }
         SPIN_CUDA_TRY(cudaMemcpyAsync(st->norms_host, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
         SPIN_CUDA_TRY(cudaStreamSynchronize(s));
         const double* h = st->norms_host;
         const double rel = std::sqrt(h[2]) / (std::sqrt(h[0]) * std::sqrt(h[1]));
+        if (verbose) fprintf(stderr, "[spin] refine it=%d slices=%d rel=%.3e\n", it, sr, rel);
         st->last_rel = rel;
         st->last_refine_iters = it;
         if (rel <= o.tol) return SPIN_OK;
@@ -387,15 +398,18 @@ int refine(Run& r, StreamState* st, const double* A, int64_t lda, double* X, int
             st->last_host_status = SPIN_ERR_NOT_CONVERGED;
             return SPIN_OK;
         }
+        // X <- X + X R with three-plane BF16 splits and six products (~2^-22
+        // relative): the correction's own error enters the next residual
+        // amplified by ~kappa * rel, so it needs more than bf16x3's ~2^-16.
         SplitPlan up;
-        RET(plan_bf16x3(n, n, n, scratch, L.scratch, &up));
+        RET(plan_bf16x6(n, n, n, scratch, L.scratch, &up));
         {
-            ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 24.0 * n * n);
-            RET(split_a_bf16x3(up, X, ldx, n, n, s));
-            RET(split_b_bf16x3(up, R, n, n, n, s));
+            ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 28.0 * n * n);
+            RET(split_a_bf16x6(up, X, ldx, n, n, s));
+            RET(split_b_bf16x6(up, R, n, n, n, s));
         }
-        ProfScope ps(r.prof, s, SPIN_KERNEL_UPDATE, -1, n, n, n, 3.0 * f, 8.0 * n * n + 16.0 * n * n);
-        RET(product_bf16x3(up, n, n, n, 1.0, 1.0, X, ldx, X, ldx, r.err, s));
+        ProfScope ps(r.prof, s, SPIN_KERNEL_UPDATE, -1, n, n, n, 6.0 * f, 12.0 * n * n + 16.0 * n * n);
+        RET(product_bf16x6(up, n, n, n, 1.0, 1.0, X, ldx, X, ldx, r.err, s));
     }
 }
 
@@ -527,7 +541,8 @@ int spin_default_leaf(int64_t n, int precision) {
 int spin_autotune_leaf(int64_t n, int precision, const int* candidates, int ncand, int* leaf_out, double* ms_out,
                        spin_stream_t stream) {
     if (n < 2 || ncand < 1 || candidates == nullptr || leaf_out == nullptr) return SPIN_ERR_INVALID_ARG;
-    if (precision < SPIN_FP64 || precision > SPIN_MIXED_BF16X3) return SPIN_ERR_INVALID_ARG;
+    if (precision < SPIN_FP64 || precision > SPIN_MIXED_DIGITS || precision == SPIN_MIXED_TF32)
+        return SPIN_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     StreamState* st = nullptr;
     RET(get_state(s, &st));
@@ -593,7 +608,7 @@ int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t
                    spin_info* info, spin_stream_t stream) {
     cudaStream_t s = (cudaStream_t)stream;
     spin_opts o = opts ? *opts : spin_opts_default();
-    if (o.precision < SPIN_FP64 || o.precision > SPIN_MIXED_TF32) return SPIN_ERR_INVALID_ARG;
+    if (o.precision < SPIN_FP64 || o.precision > SPIN_MIXED_DIGITS) return SPIN_ERR_INVALID_ARG;
     RET(check_common(A, lda, X, ldx, n, n >= 1 ? resolve_leaf(n, o.leaf, o.precision) : 1));
     StreamState* st = nullptr;
     RET(get_state(s, &st));

@@ -15,12 +15,13 @@
 // shared memory when they fit (global memory, L2-resident, otherwise).  Row interchanges
 // are bookkeeping only (position <-> physical row tables replicated in every
 // CTA), so no data moves between CTAs except the pivot row, read through
-// distributed shared memory.  Per step: local argmax -> cluster barrier ->
-// every CTA reduces the C candidates identically -> the pivot row's owner
-// scales it -> cluster barrier -> all CTAs eliminate their rows.  Cluster
-// barriers are hardware barriers: there is no spin-wait anywhere.  Per step
-// there is a single cluster barrier: the pivot row is read raw by every CTA
-// through distributed shared memory and scaled on the fly.
+// distributed shared memory.  Per step: cluster barrier -> every CTA reduces
+// the C published candidates identically -> all CTAs eliminate their rows
+// with the pivot row read raw from its owner through distributed shared
+// memory and scaled on the fly -> each CTA publishes its candidate for the
+// next column.  One cluster barrier per step (a hardware barrier: no
+// spin-wait anywhere); the owner scales the pivot row in place after the
+// next barrier.
 #include <cooperative_groups.h>
 #include <limits.h>
 
@@ -142,7 +143,11 @@ __device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int
     // One cluster barrier per step.  The pivot row of step k is read raw by
     // every CTA (and scaled on the fly); its owner scales it in place at the
     // start of step k+1, after the barrier, when nobody reads it any more and
-    // before it is eliminated like every other row.
+    // before it is eliminated like every other row.  The candidates
+    // alternate between two slots (step k reads slot k & 1): a CTA writes
+    // step k+1's candidate before the next barrier, while others may still
+    // be reading step k's; the slot it overwrites was last read in step k-1,
+    // which every CTA finished before the barrier that opened step k.
     int steps_done = 0;
     int prev_p = -1;
     double prev_inv = 0.0;
@@ -154,7 +159,7 @@ __device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int
         }
         if (tid < 32) {
             Cand c{-1.0, 0.0, INT_MAX, -1};
-            if (tid < C) c = *cluster.map_shared_rank(&cand[0], tid);
+            if (tid < C) c = *cluster.map_shared_rank(&cand[k & 1], tid);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 const double ok = __shfl_down_sync(0xffffffffu, c.key, off);
@@ -204,7 +209,9 @@ __device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int
             }
         }
         __syncthreads();
-        local_candidate(M, L, nrows, r0, lpos, k + 1, &cand[0], warp_scratch);
+        // next step's candidate goes to the other slot: a slower CTA may
+        // still be reading this step's slot through the cluster window
+        local_candidate(M, L, nrows, r0, lpos, k + 1, &cand[(k + 1) & 1], warp_scratch);
         prev_p = p;
         prev_inv = inv;
         steps_done = k + 1;
@@ -295,12 +302,21 @@ int max_cluster_size() {
     return cached;
 }
 
-LeafConfig leaf_config(int64_t L, bool have_scratch) {
+// Cluster shape.  A pivot step costs a few microseconds of latency
+// (barrier, DSMEM reads) plus R*L FMAs on each CTA at ~2 FP64 FMA/clock:
+// measured per-step times at L = 128 are 17.4 / 10.6 / 7.2 / 5.6 / 5.0 us for
+// 1 / 2 / 4 / 8 / 16 CTAs.  A single inversion waits on its leaves, so it
+// takes the widest cluster (latency); a batch runs many leaves side by side,
+// so it takes the narrowest that fits shared memory (SM time).
+LeafConfig leaf_config(int64_t L, bool have_scratch, bool batched = false) {
     LeafConfig c;
     const int cmax = max_cluster_size();
-    int need = (int)((L + 31) / 32);
     c.C = 1;
-    while (c.C < need && c.C < cmax) c.C <<= 1;
+    if (batched) {
+        while (c.C < cmax && leaf_layout((int)L, (int)((L + c.C - 1) / c.C), true).total > kSmemBudget) c.C <<= 1;
+    } else {
+        while (c.C < cmax && c.C < L) c.C <<= 1;
+    }
     c.R = (int)((L + c.C - 1) / c.C);
     c.smem_rows = leaf_layout((int)L, c.R, true).total <= kSmemBudget;
     if (!c.smem_rows && !have_scratch) c.smem_rows = true;  // rejected by the caller's size check
@@ -367,7 +383,7 @@ int launch_leaf_gj_batched(const BatchView& src, const BatchView& dst, int64_t L
                            int64_t scratch_stride, int32_t* info, int leaf_index, int count, cudaStream_t s) {
     if (L <= 0 || count <= 0) return SPIN_OK;
     if (L > kMaxLeaf || count > 65535) return SPIN_ERR_INVALID_ARG;
-    const LeafConfig c = leaf_config(L, scratch_base != nullptr);
+    const LeafConfig c = leaf_config(L, scratch_base != nullptr, true);
     if (c.smem > kSmemBudget) return SPIN_ERR_INVALID_ARG;
     if (c.smem_rows)
         return launch_leaf_batched_impl<true>(src, dst, c, L, nullptr, 0, info, leaf_index, count, s);

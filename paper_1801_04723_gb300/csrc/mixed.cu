@@ -34,6 +34,11 @@ size_t bf16x3_scratch_bytes(int64_t m, int64_t n, int64_t k) {
     return (size_t)(2 * m * ld + 2 * n * ld) * 2 + 256;
 }
 
+size_t bf16x6_scratch_bytes(int64_t m, int64_t n, int64_t k) {
+    const int64_t ld = tc_ld(k);
+    return (size_t)(3 * m * ld + 3 * n * ld) * 2 + 256;
+}
+
 size_t ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices) {
     const int64_t ld = tc_ld(k);
     return (size_t)(slices * m * ld + slices * n * ld) * 2 + (size_t)(m + n) * 4 + 1024;
@@ -103,6 +108,49 @@ int product_bf16x3(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double 
     return launch_tc_gemm(oa, ob, p, s);
 }
 
+int plan_bf16x6(int64_t m, int64_t n, int64_t k, void* scratch, size_t bytes, SplitPlan* sp) {
+    if (bytes < bf16x6_scratch_bytes(m, n, k)) return SPIN_ERR_INVALID_ARG;
+    sp->ld = tc_ld(k);
+    sp->a = (uint16_t*)align_up((uintptr_t)scratch, 256);
+    sp->b = sp->a + 3 * m * sp->ld;
+    sp->ea = sp->eb = nullptr;
+    sp->slices = 3;
+    return SPIN_OK;
+}
+
+int split_a_bf16x6(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, int64_t k, cudaStream_t s) {
+    return launch_split_bf16x3p(A, lda, (int)m, (int)k, false, sp.a, sp.ld, s);
+}
+int split_b_bf16x6(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, cudaStream_t s) {
+    return launch_split_bf16x3p(B, ldb, (int)k, (int)n, true, sp.b, sp.ld, s);
+}
+
+int product_bf16x6(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
+                   int64_t ldc, double* D, int64_t ldd, int* err, cudaStream_t s) {
+    TcGemmParams p = {};
+    p.M = (int)m;
+    p.N = (int)n;
+    p.K = (int)k;
+    // planes 0 = hi, 1 = mid, 2 = lo: pairs of combined weight >= 2^-16
+    const int8_t pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+    p.num_pairs = 6;
+    for (int i = 0; i < 6; i++) {
+        p.pa[i] = pa[i];
+        p.pb[i] = pb[i];
+        p.pg[i] = 0;
+    }
+    p.exact = 0;
+    p.alpha = alpha;
+    p.beta = beta;
+    p.C = C;
+    p.ldc = ldc;
+    p.D = D;
+    p.ldd = ldd;
+    p.err = err;
+    TcOperand oa{sp.a, (int)m, 3, sp.ld}, ob{sp.b, (int)n, 3, sp.ld};
+    return launch_tc_gemm(oa, ob, p, s);
+}
+
 int product_ozaki(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
                   int64_t ldc, double* D, int64_t ldd, int add_identity, double* sumsq, int* err, cudaStream_t s) {
     const int slices = sp.slices;
@@ -121,7 +169,7 @@ int product_ozaki(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double a
     p.num_pairs = q;
     for (int w = 0; w < slices; w++) p.group_shift[w] = -14 - 8 * w;
     p.exact = 1;
-    p.chunk_kb = 8;  // runs of 512: |sum| <= 512 * 2^14 = 2^23, exact in FP32
+    p.chunk_kb = 16;  // runs of 1024: every partial sum is an integer of magnitude <= 2^24, exact in FP32
     p.alpha = alpha;
     p.beta = beta;
     p.C = C;

@@ -21,6 +21,7 @@ struct OzakiCachedA {
 };
 
 size_t bf16x3_scratch_bytes(int64_t m, int64_t n, int64_t k);
+size_t bf16x6_scratch_bytes(int64_t m, int64_t n, int64_t k);
 size_t ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices);
 
 int gemm_bf16x3(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda, const double* B,
@@ -50,6 +51,12 @@ int split_a_ozaki(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, 
 int split_b_ozaki(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, double* sumsq,
                   cudaStream_t s);
 int product_bf16x3(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
+                   int64_t ldc, double* D, int64_t ldd, int* err, cudaStream_t s);
+// Three-plane form (hi, mid, lo) with the six products of weight <= 2^-16.
+int plan_bf16x6(int64_t m, int64_t n, int64_t k, void* scratch, size_t bytes, SplitPlan* sp);
+int split_a_bf16x6(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, int64_t k, cudaStream_t s);
+int split_b_bf16x6(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, cudaStream_t s);
+int product_bf16x6(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
                    int64_t ldc, double* D, int64_t ldd, int* err, cudaStream_t s);
 int product_ozaki(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
                   int64_t ldc, double* D, int64_t ldd, int add_identity, double* sumsq, int* err, cudaStream_t s);

@@ -12,28 +12,36 @@
 //       A is scaled by a power of two 2^e_i so that |a_ik| < 2^e_i, and the
 //       scaled row is written as digits d_1 + 2^-8 d_2 + ... (|d| <= 128,
 //       each an exact BF16 integer); likewise every column of B.  A product
-//       of two digits is an integer of at most 2^14, so a run of 512 of them
-//       sums exactly in the FP32 accumulator.  Each run is drained into int32
+//       of two digits is an integer of at most 2^14, so a run of 1024 of them
+//       sums exactly in the FP32 accumulator (every partial sum is an integer
+//       of magnitude <= 2^24).  Each run is drained into int32
 //       registers, and each group of slice pairs of equal weight
 //       (t + u = const) is scaled by 2^(e_i + f_j + shift) and added into the
 //       FP64 output: the result is exact up to the truncation of the digit
 //       expansion, i.e. FP64-class for 5-7 slices.
 //
-// Kernel: one CTA per 128 x 256 output tile:
-//   warp 0      TMA producer (one lane): 4-stage ring of (A 128x64, B 256x64)
-//               BF16 tiles, 128-byte swizzled, mbarrier complete_tx.
-//   warp 1      TMEM owner (512 columns = two 128 x 256 FP32 accumulators)
-//               and MMA issuer (one lane): 4 tcgen05.mma (K = 16) per stage.
-//   warps 2..   epilogue: warp w reads TMEM lanes 32*(w%4).. with tcgen05.ld.
-//               Float mode uses 8 epilogue warps (128 columns each, no state);
-//               exact mode uses 16 (64 columns each), so that the int32 run
-//               sums of a thread (64) stay in registers.
-// The two accumulators alternate between runs so that draining one overlaps
-// the MMAs of the next.  Every wait is bounded (%globaltimer); on a timeout
-// the kernel records SPIN_ERR_TIMEOUT, stops issuing, waits (bounded) for
-// its own copies and MMAs, frees TMEM and returns.
+// Kernel (tc_gemm_kernel): one CTA per output tile, warp-specialised:
+//   warp 0      TMA producer (one lane): a ~192 KB ring of BF16 operand
+//               stages, 128-byte swizzled, mbarrier complete_tx.  Float mode:
+//               128 x 256 tiles, 4 stages of one 64-wide k-block; exact mode:
+//               128 x 128 tiles, 3 stages of two k-blocks.
+//   warp 1      TMEM owner and MMA issuer (one lane): tcgen05.mma kind::f16,
+//               K = 16 per instruction, one commit per stage.
+//   warps 2..9  epilogue: warp w reads TMEM lanes 32*(w%4).. (tcgen05.ld);
+//               the two column halves of the tile go to warps 2-5 and 6-9.
+// TMEM holds two FP32 accumulators that alternate between runs, so draining
+// one overlaps the MMAs of the next; in exact mode it also holds each
+// output's FP64 running sum (two 32-bit columns), so the slice-pair groups
+// are summed without global-memory traffic and D is written once.  Every
+// wait is bounded (%globaltimer); on a timeout the kernel records
+// SPIN_ERR_TIMEOUT, stops issuing, waits (bounded) for its own copies and
+// MMAs, frees TMEM and returns.  tc_gemm_pair_kernel is the exact mode on
+// CTA pairs (tcgen05 cta_group::2, 256 x 128 tiles), selected by
+// SPIN_TC_PAIR=1.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
+
+#include <stdlib.h>
 
 #include <algorithm>
 
@@ -47,25 +55,43 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128, BK = 64;
+constexpr int GROUP_M = 8;  // row blocks per rasterisation band
 #ifndef SPIN_EXACT_BN
 #define SPIN_EXACT_BN 128
 #define SPIN_EXACT_EPI_WARPS 8
 #endif
+#ifndef SPIN_FLOAT_BN
+#define SPIN_FLOAT_BN 256
+#endif
+#ifndef SPIN_KSUB_EXACT
+#define SPIN_KSUB_EXACT 2
+#endif
+#ifndef SPIN_KSUB_FLOAT
+#define SPIN_KSUB_FLOAT 1
+#endif
+constexpr int kFloatBN = SPIN_FLOAT_BN;             // float-mode tile width
 constexpr int kExactBN = SPIN_EXACT_BN;             // exact-mode tile width
 constexpr int kExactEpiWarps = SPIN_EXACT_EPI_WARPS;  // exact-mode epilogue warps
 constexpr uint32_t A_TILE_BYTES = BM * BK * 2;  // 16 KB
-constexpr int FLUSH_LIMIT = 96;  // exact runs summed in int32 before an FP64 flush (96 * 2^23 < 2^31)
+// 64-wide k-blocks per pipeline stage.  The MMA issuer's fixed cost per
+// stage (barrier wait, commit) is spread over 4 * KSUB MMAs: two k-blocks
+// for the 128-wide exact tiles (measured 1140 vs 970 TFLOP/s at n = 8192),
+// one for the 256-wide float tiles, whose stages are already twice as long
+// and which need the deeper ring (4 stages rather than 2).
+constexpr int KSUB_EXACT = SPIN_KSUB_EXACT;
+constexpr int KSUB_FLOAT = SPIN_KSUB_FLOAT;
+constexpr int FLUSH_LIMIT = 96;  // exact runs summed in int32 before an FP64 flush (96 * 2^24 < 2^31)
 constexpr uint64_t WAIT_LIMIT_NS = 10ull * 1000 * 1000 * 1000;
 
-template <int BN>
+template <int BN, int KS>
 struct Cfg {
     static constexpr uint32_t B_TILE_BYTES = BN * BK * 2;
-    static constexpr uint32_t STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
+    static constexpr uint32_t STAGE_BYTES = KS * (A_TILE_BYTES + B_TILE_BYTES);
     static constexpr int STAGES = (196608 / STAGE_BYTES) > 6 ? 6 : (196608 / STAGE_BYTES);  // ~192 KB ring
     static constexpr uint32_t TMEM_COLS = 2 * BN <= 256 ? 256 : 512;  // power of two >= 2 BN
     static constexpr size_t SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256 /*barriers etc.*/;
 };
-constexpr int STAGES_MAX = 6;
+constexpr int STAGES_MAX = 8;
 
 struct SmemCtl {
     uint64_t full[STAGES_MAX];
@@ -75,14 +101,39 @@ struct SmemCtl {
     uint64_t final_bar;
     uint32_t tmem_base;
     int abort;
+    int issued;  // pair kernel: stage uses this CTA's producer issued
 };
 
-// 2^e for -1022 <= e <= 1023, built from the exponent bits (exact).
-__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+// x * 2^E exactly, for |x| < 2^31, from the bits: the leading one of |x|
+// becomes the implicit bit and the rest the fraction.  Integer operations
+// only (GB300's FP64 pipe is ~2 operations per clock per SM); ldexp when
+// the result would not be a normal double.
+__device__ __forceinline__ double scaled_int(int x, int E) {
+    if (x == 0) return 0.0;
+    const unsigned u = x < 0 ? 0u - (unsigned)x : (unsigned)x;
+    const int lz = __clz(u);     // leading one at bit 31 - lz
+    const int e = 31 - lz + E;   // exponent of the result
+    if (e < -1022 || e > 1023) return ldexp((double)x, E);
+    const unsigned long long frac = ((unsigned long long)u << (21 + lz)) & 0xFFFFFFFFFFFFFull;
+    const unsigned long long bits =
+        ((unsigned long long)(x < 0) << 63) | ((unsigned long long)(e + 1023) << 52) | frac;
+    return __longlong_as_double((long long)bits);
+}
+
+static_assert(sizeof(SmemCtl) <= 256, "control block");
 
 __device__ __forceinline__ void raise_timeout(SmemCtl* ctl, int* err) {
     ctl->abort = 1;
     if (err) atomicCAS(err, 0, SPIN_ERR_TIMEOUT);
+}
+// CTA pair: stop both CTAs (the peer's waits read its own abort flag).
+__device__ __forceinline__ void raise_pair_error(SmemCtl* ctl, int* err, int code) {
+    ctl->abort = 1;
+    st_cluster_u32(mapa_u32(smem_u32(&ctl->abort), cluster_ctarank() ^ 1u), 1u);
+    if (err) atomicCAS(err, 0, code);
+}
+__device__ __forceinline__ void raise_timeout_pair(SmemCtl* ctl, int* err) {
+    raise_pair_error(ctl, err, SPIN_ERR_TIMEOUT);
 }
 
 template <int EPI_WARPS>
@@ -93,24 +144,159 @@ struct Epi {
     static constexpr int MAXREG = (65536 / ALLOC_THREADS) / 8 * 8 > 255 ? 248 : (65536 / ALLOC_THREADS) / 8 * 8;
 };
 
+// Exact-mode epilogue of one warp (HALF columns of one TMEM lane quarter):
+// drains every exact run from TMEM into int32 sums and, at the end of each
+// group of equal-weight slice pairs (or every FLUSH_LIMIT runs), adds the
+// group's 2^(e_row + e_col + shift)-scaled sums into the FP64 output.
+// Returns this thread's sum of squares of its final outputs.  PAIR: the
+// accumulators belong to a CTA pair whose MMA issuer waits on the even
+// CTA's tempty barriers (cluster addresses tempty_c0 / tempty_c1); the
+// tfull barriers are this CTA's own (the issuer multicasts its commits).
+template <int BN, int HALF, bool PAIR>
+__device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl* ctl, volatile int* abort,
+                                                 uint32_t lane_addr, int half, int grow, int col0,
+                                                 int nchunks_per_pair, int lane, uint32_t tempty_c0,
+                                                 uint32_t tempty_c1) {
+    const bool row_ok = grow < p.M;
+    double sumsq = 0.0;
+    // alpha = +-1 (every product of the method) is a sign flip of the integer
+    // sums (|sum| < 2^31, no overflow); anything else costs one FP64 multiply
+    const int alpha_sign = p.alpha == -1.0 ? -1 : 1;
+    const bool alpha_general = p.alpha != 1.0 && p.alpha != -1.0;
+    int acc[HALF];
+#pragma unroll
+    for (int j = 0; j < HALF; j++) acc[j] = 0;
+    int chunk = 0, since_flush = 0;
+    bool first_flush = true, ok = true;
+    const int erow = (p.row_exp && row_ok) ? p.row_exp[grow] : 0;
+    for (int q = 0; q < p.num_pairs && ok; q++) {
+        for (int c = 0; c < nchunks_per_pair && ok; c++) {
+            const int buf = chunk & 1;
+            const uint32_t use = (uint32_t)(chunk >> 1);
+            ok = PAIR ? mbar_wait_cluster(&ctl->tfull[buf], use & 1u, abort, WAIT_LIMIT_NS)
+                      : mbar_wait(&ctl->tfull[buf], use & 1u, abort, WAIT_LIMIT_NS);
+            if (!ok) {
+                if (PAIR)
+                    raise_timeout_pair(ctl, p.err);
+                else
+                    raise_timeout(ctl, p.err);
+                break;
+            }
+            tc_fence_after();
+            {
+                // 32 columns per wait: two loads in flight, 32 registers
+#pragma unroll
+                for (int c0 = 0; c0 < HALF; c0 += 32) {
+                    uint32_t v[32];
+                    tmem_ld_32x32b_x16(lane_addr + (uint32_t)(buf * BN + half * HALF + c0),
+                                       *reinterpret_cast<uint32_t(*)[16]>(&v[0]));
+                    tmem_ld_32x32b_x16(lane_addr + (uint32_t)(buf * BN + half * HALF + c0 + 16),
+                                       *reinterpret_cast<uint32_t(*)[16]>(&v[16]));
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; j++) acc[c0 + j] += __float2int_rn(__uint_as_float(v[j]));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (PAIR)
+                    mbar_arrive_cluster(buf ? tempty_c1 : tempty_c0);
+                else
+                    mbar_arrive(&ctl->tempty[buf]);
+            }
+            chunk++;
+            since_flush++;
+            const bool group_end =
+                (c == nchunks_per_pair - 1) && (q == p.num_pairs - 1 || p.pg[q + 1] != p.pg[q]);
+            const bool last = (c == nchunks_per_pair - 1) && (q == p.num_pairs - 1);
+            if (group_end || since_flush >= FLUSH_LIMIT) {
+                // acc * 2^(e_row + e_col + shift) is built from the integer's
+                // bits (exact, no FP64 arithmetic); the running FP64 sum of
+                // this thread's columns stays in TMEM until the last flush,
+                // which writes D once.
+                const int er = erow + p.group_shift[(int)p.pg[q]];
+                double* drow = p.D + (int64_t)grow * p.ldd;
+                const double* crow = p.C ? p.C + (int64_t)grow * p.ldc : nullptr;
+                const uint32_t sum_addr = lane_addr + (uint32_t)(2 * BN + half * 2 * HALF);
+#pragma unroll
+                for (int jj = 0; jj < HALF; jj += 8) {
+                    uint32_t w[16];  // 8 FP64 running sums as (lo, hi) words
+                    if (!first_flush) {
+                        tmem_ld_32x32b_x16(sum_addr + (uint32_t)(2 * jj), w);
+                        tmem_ld_wait();
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        const int gcol = col0 + jj + j;
+                        const bool ok_ij = row_ok && gcol < p.N;
+                        const int ec = (p.col_exp && ok_ij) ? p.col_exp[gcol] : 0;
+                        double val = scaled_int(alpha_sign * acc[jj + j], er + ec);
+                        if (alpha_general) val *= p.alpha;
+                        if (first_flush) {
+                            if (p.beta != 0.0 && ok_ij) val = fma(p.beta, crow[gcol], val);
+                            if (p.add_identity && gcol == grow) val += 1.0;
+                        } else {
+                            val += __hiloint2double((int)w[2 * j + 1], (int)w[2 * j]);
+                        }
+                        if (last) {
+                            if (ok_ij) {
+                                drow[gcol] = val;
+                                sumsq = fma(val, val, sumsq);
+                            }
+                        } else {
+                            w[2 * j] = (uint32_t)__double2loint(val);
+                            w[2 * j + 1] = (uint32_t)__double2hiint(val);
+                        }
+                        acc[jj + j] = 0;
+                    }
+                    if (!last) tmem_st_32x32b_x16(sum_addr + (uint32_t)(2 * jj), w);
+                }
+                if (!last) tmem_st_wait();
+                first_flush = false;
+                since_flush = 0;
+            }
+        }
+    }
+    return sumsq;
+}
+
 template <int BN, bool EXACT, int EPI_WARPS>
 __global__ void __maxnreg__(Epi<EPI_WARPS>::MAXREG)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const TcGemmParams p) {
-    constexpr int STAGES = Cfg<BN>::STAGES;
-    constexpr uint32_t B_TILE_BYTES = Cfg<BN>::B_TILE_BYTES;
-    constexpr uint32_t STAGE_BYTES = Cfg<BN>::STAGE_BYTES;
-    constexpr uint32_t TMEM_COLS = Cfg<BN>::TMEM_COLS;
+    constexpr int KS = EXACT ? KSUB_EXACT : KSUB_FLOAT;  // k-blocks per stage
+    using C = Cfg<BN, KS>;
+    constexpr int STAGES = C::STAGES;
+    constexpr uint32_t B_TILE_BYTES = C::B_TILE_BYTES;
+    constexpr uint32_t STAGE_BYTES = C::STAGE_BYTES;
+    // exact mode: two FP32 accumulators + the FP64 running sums (2 columns each)
+    constexpr uint32_t TMEM_COLS = EXACT ? 4 * BN : C::TMEM_COLS;
+    static_assert(TMEM_COLS <= 512, "TMEM");
     constexpr int HALF = BN / (EPI_WARPS / 4);  // columns per epilogue warp
-    static_assert(EPI_WARPS % 4 == 0 && BN % (EPI_WARPS / 4) == 0 && HALF % 16 == 0, "epilogue split");
+    static_assert(EPI_WARPS % 4 == 0 && BN % (EPI_WARPS / 4) == 0 && HALF % 32 == 0, "epilogue split");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* smA = base;
-    unsigned char* smB = base + STAGES * A_TILE_BYTES;
+    unsigned char* smA = base;                              // [stage][sub] A tiles
+    unsigned char* smB = base + STAGES * KS * A_TILE_BYTES;  // [stage][sub] B tiles
     SmemCtl* ctl = reinterpret_cast<SmemCtl*>(base + STAGES * STAGE_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    // Grouped rasterisation: consecutive CTAs sweep a band of GROUP_M row
+    // blocks column by column, so the CTAs resident at one time share a few
+    // B column blocks and a few A row blocks (L2 reuse) instead of streaming
+    // every B block once per row block.
+    int m0, n0;
+    {
+        const int num_m = (p.M + BM - 1) / BM, num_n = (p.N + BN - 1) / BN;
+        const int pid = blockIdx.x;
+        const int per_group = GROUP_M * num_n;
+        const int first_m = (pid / per_group) * GROUP_M;
+        const int gsize = min(num_m - first_m, GROUP_M);
+        const int in_group = pid % per_group;
+        m0 = (first_m + in_group % gsize) * BM;
+        n0 = (in_group / gsize) * BN;
+    }
     const int KB = (p.K + BK - 1) / BK;
     const int chunk_kb = EXACT ? p.chunk_kb : KB;
     const int nchunks_per_pair = (KB + chunk_kb - 1) / chunk_kb;
@@ -145,24 +331,30 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (lane == 0) {
             int it = 0;
             bool ok = true;
+            // one stage = k-blocks kb .. kb + KS - 1 of one slice pair (past K: zero fill)
             auto issue = [&](int pair, int kb) -> bool {
                 const int s = it % STAGES;
                 const uint32_t ph = (uint32_t)((it / STAGES) & 1);
                 if (!mbar_wait(&ctl->empty[s], ph ^ 1u, abort, WAIT_LIMIT_NS)) return false;
                 mbar_arrive_expect_tx(&ctl->full[s], STAGE_BYTES);
-                tma_load_2d(smA + s * A_TILE_BYTES, &tmA, kb * BK, p.pa[pair] * p.a_rows + m0, &ctl->full[s]);
-                tma_load_2d(smB + s * B_TILE_BYTES, &tmB, kb * BK, p.pb[pair] * p.b_rows + n0, &ctl->full[s]);
+#pragma unroll
+                for (int u = 0; u < KS; u++) {
+                    tma_load_2d(smA + (s * KS + u) * A_TILE_BYTES, &tmA, (kb + u) * BK,
+                                p.pa[pair] * p.a_rows + m0, &ctl->full[s]);
+                    tma_load_2d(smB + (s * KS + u) * B_TILE_BYTES, &tmB, (kb + u) * BK,
+                                p.pb[pair] * p.b_rows + n0, &ctl->full[s]);
+                }
                 it++;
                 return true;
             };
             if (!EXACT) {
-                for (int kb = 0; kb < KB && ok; kb++)
+                for (int kb = 0; kb < KB && ok; kb += KS)
                     for (int q = 0; q < p.num_pairs && ok; q++) ok = issue(q, kb);
             } else {
                 for (int q = 0; q < p.num_pairs && ok; q++)
                     for (int c = 0; c < nchunks_per_pair && ok; c++) {
                         const int kb1 = min(KB, (c + 1) * chunk_kb);
-                        for (int kb = c * chunk_kb; kb < kb1 && ok; kb++) ok = issue(q, kb);
+                        for (int kb = c * chunk_kb; kb < kb1 && ok; kb += KS) ok = issue(q, kb);
                     }
             }
             if (!ok) raise_timeout(ctl, p.err);
@@ -179,18 +371,23 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const uint32_t idesc = idesc_bf16_f32(BM, BN);
             int it = 0, chunk = 0;
             bool ok = true;
-            auto consume = [&](uint32_t d_tmem, bool first_in_chunk) -> bool {
+            // nsub valid k-blocks in this stage; descriptors advance by 32 B per K = 16
+            auto consume = [&](uint32_t d_tmem, bool first_in_chunk, int nsub) -> bool {
                 const int s = it % STAGES;
                 const uint32_t ph = (uint32_t)((it / STAGES) & 1);
                 if (!mbar_wait(&ctl->full[s], ph, abort, WAIT_LIMIT_NS)) return false;
                 tc_fence_after();
-                const uint32_t a_addr = smem_u32(smA + s * A_TILE_BYTES);
-                const uint32_t b_addr = smem_u32(smB + s * B_TILE_BYTES);
+                const uint64_t ad0 = sdesc_kmajor_sw128(smem_u32(smA + s * KS * A_TILE_BYTES));
+                const uint64_t bd0 = sdesc_kmajor_sw128(smem_u32(smB + s * KS * B_TILE_BYTES));
 #pragma unroll
-                for (int k = 0; k < BK / 16; k++) {
-                    const uint64_t ad = sdesc_kmajor_sw128(a_addr + k * 32);
-                    const uint64_t bd = sdesc_kmajor_sw128(b_addr + k * 32);
-                    mma_bf16(d_tmem, ad, bd, idesc, (first_in_chunk && k == 0) ? 0u : 1u);
+                for (int u = 0; u < KS; u++) {
+                    if (u < nsub) {
+#pragma unroll
+                        for (int k = 0; k < BK / 16; k++)
+                            mma_bf16(d_tmem, ad0 + ((u * A_TILE_BYTES + k * 32) >> 4),
+                                     bd0 + ((u * B_TILE_BYTES + k * 32) >> 4), idesc,
+                                     (first_in_chunk && u == 0 && k == 0) ? 0u : 1u);
+                    }
                 }
                 mma_commit(&ctl->empty[s]);  // frees the stage once these MMAs have read it
                 it++;
@@ -207,8 +404,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 int buf = 0;
                 ok = begin_chunk(buf);
                 const uint32_t d = tmem_base + (uint32_t)(buf * BN);
-                for (int kb = 0; kb < KB && ok; kb++)
-                    for (int q = 0; q < p.num_pairs && ok; q++) ok = consume(d, kb == 0 && q == 0);
+                for (int kb = 0; kb < KB && ok; kb += KS)
+                    for (int q = 0; q < p.num_pairs && ok; q++) ok = consume(d, kb == 0 && q == 0, min(KS, KB - kb));
                 if (ok) mma_commit(&ctl->tfull[buf]);
                 chunk++;
             } else {
@@ -218,7 +415,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         ok = begin_chunk(buf);
                         const uint32_t d = tmem_base + (uint32_t)(buf * BN);
                         const int kb0 = c * chunk_kb, kb1 = min(KB, (c + 1) * chunk_kb);
-                        for (int kb = kb0; kb < kb1 && ok; kb++) ok = consume(d, kb == kb0);
+                        for (int kb = kb0; kb < kb1 && ok; kb += KS) ok = consume(d, kb == kb0, min(KS, kb1 - kb));
                         if (ok) mma_commit(&ctl->tfull[buf]);
                         chunk++;
                     }
@@ -273,81 +470,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->tempty[0]);
         } else {
-            int acc[HALF];
-#pragma unroll
-            for (int j = 0; j < HALF; j++) acc[j] = 0;
-            int chunk = 0, since_flush = 0;
-            bool first_flush = true, ok = true;
-            const int erow = (p.row_exp && row_ok) ? p.row_exp[grow] : 0;
-            for (int q = 0; q < p.num_pairs && ok; q++) {
-                for (int c = 0; c < nchunks_per_pair && ok; c++) {
-                    const int buf = chunk & 1;
-                    const uint32_t use = (uint32_t)(chunk >> 1);
-                    ok = mbar_wait(&ctl->tfull[buf], use & 1u, abort, WAIT_LIMIT_NS);
-                    if (!ok) {
-                        raise_timeout(ctl, p.err);
-                        break;
-                    }
-                    tc_fence_after();
-#pragma unroll
-                    for (int cc = 0; cc < HALF; cc += 16) {
-                        uint32_t v[16];
-                        tmem_ld_32x32b_x16(lane_addr + (uint32_t)(buf * BN + half * HALF + cc), v);
-                        tmem_ld_wait();
-#pragma unroll
-                        for (int j = 0; j < 16; j++) acc[cc + j] += __float2int_rn(__uint_as_float(v[j]));
-                    }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&ctl->tempty[buf]);
-                    chunk++;
-                    since_flush++;
-                    const bool group_end =
-                        (c == nchunks_per_pair - 1) && (q == p.num_pairs - 1 || p.pg[q + 1] != p.pg[q]);
-                    const bool last = (c == nchunks_per_pair - 1) && (q == p.num_pairs - 1);
-                    if (group_end || since_flush >= FLUSH_LIMIT) {
-                        if (row_ok) {
-                            // exact powers of two: 2^(e_row + shift) * 2^(e_col) * integer
-                            const int er = erow + p.group_shift[(int)p.pg[q]];
-                            const bool fast = er >= -1000 && er <= 1000;
-                            const double srow = fast ? pow2(er) : 0.0;
-                            double* drow = p.D + (int64_t)grow * p.ldd;
-                            const double* crow = p.C ? p.C + (int64_t)grow * p.ldc : nullptr;
-#pragma unroll
-                            for (int jj = 0; jj < HALF; jj += 16) {
-                                // keep the compiler from hoisting every column's loads at once
-                                asm volatile("" ::: "memory");
-#pragma unroll
-                                for (int j = jj; j < jj + 16; j++) {
-                                    const int gcol = col0 + j;
-                                    if (gcol < p.N) {
-                                        const int ec = p.col_exp ? p.col_exp[gcol] : 0;
-                                        double val;
-                                        if (fast && ec >= -1000 && ec <= 1000)
-                                            val = p.alpha * ((double)acc[j] * srow) * pow2(ec);
-                                        else
-                                            val = p.alpha * ldexp((double)acc[j], er + ec);
-                                        if (first_flush) {
-                                            if (p.beta != 0.0) val = fma(p.beta, crow[gcol], val);
-                                            if (p.add_identity && gcol == grow) val += 1.0;
-                                        } else {
-                                            val += drow[gcol];
-                                        }
-                                        drow[gcol] = val;
-                                        if (last) sumsq = fma(val, val, sumsq);
-                                    }
-                                    acc[j] = 0;
-                                }
-                            }
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < HALF; j++) acc[j] = 0;
-                        }
-                        first_flush = false;
-                        since_flush = 0;
-                    }
-                }
-            }
+            sumsq = exact_epilogue<BN, HALF, false>(p, ctl, abort, lane_addr, half, grow, col0, nchunks_per_pair,
+                                                    lane, 0u, 0u);
         }
         if (p.sumsq) {
 #pragma unroll
@@ -364,20 +488,268 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
 }
 
+// ------------------------------------------------ exact mode on CTA pairs --
+// The two CTAs of a cluster share one 256 x 128 output tile through
+// tcgen05.mma.cta_group::2 (M = 256).  Each CTA loads its own 128 rows of A
+// and its own 64 rows of B (half of the tile's 128 columns) into an 8-stage
+// ring, so per K-step of 16 a CTA's shared memory supplies 6 KB per MMA
+// instead of the 8 KB of the single-CTA 128 x 128 form, and the deeper ring
+// covers more copy latency.  Both CTAs' copies of a stage complete on the
+// even CTA's full barrier (armed by the even CTA for the pair's bytes); lane
+// 0 of warp 1 of the even CTA issues the pair's MMAs and multicasts its
+// commits to both CTAs' empty / tfull barriers; each CTA drains its own 128
+// TMEM lanes with the exact epilogue, whose tempty arrivals go to the even
+// CTA.  At exit the even CTA accounts for every copy either CTA issued
+// (arming or cancelling the expected bytes of uses that only one CTA
+// issued) and waits for them, so no copy is in flight when the pair leaves.
+constexpr int PAIR_BN = 128, PAIR_BNH = PAIR_BN / 2;
+constexpr uint32_t PAIR_B_BYTES = PAIR_BNH * BK * 2;                         // 8 KB
+constexpr uint32_t PAIR_STAGE_BYTES = KSUB_EXACT * (A_TILE_BYTES + PAIR_B_BYTES);  // per CTA
+constexpr int PAIR_STAGES = (196608 / PAIR_STAGE_BYTES) > 8 ? 8 : (196608 / PAIR_STAGE_BYTES);
+constexpr uint32_t PAIR_TMEM_COLS = 4 * PAIR_BN;  // two accumulators + FP64 running sums
+constexpr size_t PAIR_SMEM_BYTES = 1024 + PAIR_STAGES * PAIR_STAGE_BYTES + 256;
+static_assert(PAIR_STAGES <= STAGES_MAX, "ring");
+
+template <int EPI_WARPS>
+__global__ void __cluster_dims__(2, 1, 1) __maxnreg__(Epi<EPI_WARPS>::MAXREG)
+tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const TcGemmParams p) {
+    constexpr int HALF = PAIR_BN / (EPI_WARPS / 4);
+    static_assert(EPI_WARPS % 4 == 0 && PAIR_BN % (EPI_WARPS / 4) == 0 && HALF % 32 == 0, "epilogue split");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* smA = base;                                    // [stage][sub] A tiles
+    unsigned char* smB = base + PAIR_STAGES * KSUB_EXACT * A_TILE_BYTES;  // [stage][sub] B tiles
+    SmemCtl* ctl = reinterpret_cast<SmemCtl*>(base + PAIR_STAGES * PAIR_STAGE_BYTES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();  // 0 issues the pair's MMAs
+    int m0, n0;  // the pair's tile; grouped rasterisation as in tc_gemm_kernel
+    {
+        const int num_m = (p.M + 2 * BM - 1) / (2 * BM), num_n = (p.N + PAIR_BN - 1) / PAIR_BN;
+        const int pid = (int)(blockIdx.x >> 1);
+        const int per_group = GROUP_M * num_n;
+        const int first_m = (pid / per_group) * GROUP_M;
+        const int gsize = min(num_m - first_m, GROUP_M);
+        const int in_group = pid % per_group;
+        m0 = (first_m + in_group % gsize) * 2 * BM;
+        n0 = (in_group / gsize) * PAIR_BN;
+    }
+    const int my_m0 = m0 + (int)rank * BM;        // this CTA's A rows = its TMEM lanes
+    const int my_n0 = n0 + (int)rank * PAIR_BNH;  // this CTA's B rows
+    const int KB = (p.K + BK - 1) / BK;
+    const int chunk_kb = p.chunk_kb;
+    const int nchunks_per_pair = (KB + chunk_kb - 1) / chunk_kb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PAIR_STAGES; s++) {
+            mbar_init(&ctl->full[s], 1);
+            mbar_init(&ctl->empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&ctl->tfull[b], 1);
+            mbar_init(&ctl->tempty[b], 2 * EPI_WARPS);
+        }
+        mbar_init(&ctl->final_bar, 1);
+        ctl->abort = 0;
+        ctl->issued = 0;
+        fence_mbar_init();
+        prefetch_tensormap(&tmA);
+        prefetch_tensormap(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(&ctl->tmem_base, PAIR_TMEM_COLS);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    cluster_sync_all();  // barriers initialised and TMEM allocated in both CTAs
+    tc_fence_after();
+    const uint32_t tmem_base = ctl->tmem_base;
+    volatile int* abort = &ctl->abort;
+
+    if (warp == 0) {
+        // ------------------------------------------ producer (both CTAs) --
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            const uint32_t full0 = mapa_u32(smem_u32(&ctl->full[0]), 0u);  // even CTA's barriers
+            for (int q = 0; q < p.num_pairs && ok; q++)
+                for (int c = 0; c < nchunks_per_pair && ok; c++) {
+                    const int kb1 = min(KB, (c + 1) * chunk_kb);
+                    for (int kb = c * chunk_kb; kb < kb1; kb += KSUB_EXACT) {
+                        const int s = it % PAIR_STAGES;
+                        const uint32_t ph = (uint32_t)((it / PAIR_STAGES) & 1);
+                        ok = mbar_wait_cluster(&ctl->empty[s], ph ^ 1u, abort, WAIT_LIMIT_NS) && !*abort;
+                        if (!ok) break;
+                        if (rank == 0) mbar_arrive_expect_tx(&ctl->full[s], 2 * PAIR_STAGE_BYTES);
+                        const uint32_t bar = full0 + (uint32_t)(s * sizeof(uint64_t));
+#pragma unroll
+                        for (int u = 0; u < KSUB_EXACT; u++) {
+                            tma_load_2d_pair(smA + (s * KSUB_EXACT + u) * A_TILE_BYTES, &tmA, (kb + u) * BK,
+                                             p.pa[q] * p.a_rows + my_m0, bar);
+                            tma_load_2d_pair(smB + (s * KSUB_EXACT + u) * PAIR_B_BYTES, &tmB, (kb + u) * BK,
+                                             p.pb[q] * p.b_rows + my_n0, bar);
+                        }
+                        it++;
+                    }
+                }
+            if (!ok) raise_timeout_pair(ctl, p.err);
+            ctl->issued = it;
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // --------------------------------- MMA issuer (even CTA), M = 256
+            bool ok = ld_cluster_u32(mapa_u32(smem_u32(&ctl->tmem_base), 1u)) == tmem_base;
+            if (!ok) raise_pair_error(ctl, p.err, SPIN_ERR_CUDA);  // both CTAs must hold the same columns
+            const uint32_t idesc = idesc_bf16_f32(2 * BM, PAIR_BN);
+            int it = 0, chunk = 0;
+            for (int q = 0; q < p.num_pairs && ok; q++)
+                for (int c = 0; c < nchunks_per_pair && ok; c++) {
+                    const int buf = chunk & 1;
+                    const uint32_t use = (uint32_t)(chunk >> 1);
+                    ok = mbar_wait_cluster(&ctl->tempty[buf], (use & 1u) ^ 1u, abort, WAIT_LIMIT_NS);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + (uint32_t)(buf * PAIR_BN);
+                    const int kb0 = c * chunk_kb, kb1 = min(KB, (c + 1) * chunk_kb);
+                    for (int kb = kb0; kb < kb1 && ok; kb += KSUB_EXACT) {
+                        const int s = it % PAIR_STAGES;
+                        ok = mbar_wait_cluster(&ctl->full[s], (uint32_t)((it / PAIR_STAGES) & 1), abort,
+                                               WAIT_LIMIT_NS);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint64_t ad0 = sdesc_kmajor_sw128(smem_u32(smA + s * KSUB_EXACT * A_TILE_BYTES));
+                        const uint64_t bd0 = sdesc_kmajor_sw128(smem_u32(smB + s * KSUB_EXACT * PAIR_B_BYTES));
+                        const int nsub = min(KSUB_EXACT, kb1 - kb);
+#pragma unroll
+                        for (int u = 0; u < KSUB_EXACT; u++) {
+                            if (u < nsub) {
+#pragma unroll
+                                for (int k = 0; k < BK / 16; k++)
+                                    mma_bf16_pair(d, ad0 + ((u * A_TILE_BYTES + k * 32) >> 4),
+                                                  bd0 + ((u * PAIR_B_BYTES + k * 32) >> 4), idesc,
+                                                  (kb == kb0 && u == 0 && k == 0) ? 0u : 1u);
+                            }
+                        }
+                        mma_commit_pair(&ctl->empty[s], (uint16_t)3);  // frees stage s in both CTAs
+                        it++;
+                    }
+                    if (ok) mma_commit_pair(&ctl->tfull[buf], (uint16_t)3);
+                    chunk++;
+                }
+            if (!ok) raise_timeout_pair(ctl, p.err);
+            // every MMA issued so far has completed once final_bar flips
+            mma_commit_pair(&ctl->final_bar, (uint16_t)1);
+            volatile int never = 0;
+            mbar_wait_cluster(&ctl->final_bar, 0u, &never, WAIT_LIMIT_NS);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------ epilogue (both CTAs) --
+        const int e = warp - 2;
+        const int quarter = warp & 3;
+        const int half = e >> 2;
+        const int grow = my_m0 + quarter * 32 + lane;
+        const uint32_t lane_addr = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        double sumsq = exact_epilogue<PAIR_BN, HALF, true>(
+            p, ctl, abort, lane_addr, half, grow, n0 + half * HALF, nchunks_per_pair, lane,
+            mapa_u32(smem_u32(&ctl->tempty[0]), 0u), mapa_u32(smem_u32(&ctl->tempty[1]), 0u));
+        if (p.sumsq) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) sumsq += __shfl_down_sync(0xffffffffu, sumsq, off);
+            if (lane == 0 && sumsq != 0.0) atomicAdd(p.sumsq, sumsq);
+        }
+    }
+
+    tc_fence_before();
+    cluster_sync_all();  // both producers have stopped; no MMA of the pair is in flight
+    if (rank == 0 && threadIdx.x == 0) {
+        // Copies still in flight can only belong to the last PAIR_STAGES uses
+        // (a use is issued after the use PAIR_STAGES earlier was consumed).
+        const int own = ctl->issued;
+        const int peer = (int)ld_cluster_u32(mapa_u32(smem_u32(&ctl->issued), 1u));
+        const int hi = max(own, peer);
+        for (int j = max(0, hi - PAIR_STAGES); j < hi; j++) {
+            uint64_t* bar = &ctl->full[j % PAIR_STAGES];
+            if (j >= own)
+                mbar_arrive_expect_tx(bar, PAIR_STAGE_BYTES);  // only the odd CTA issued this use
+            else if (j >= peer)
+                mbar_complete_tx(bar, PAIR_STAGE_BYTES);  // the odd CTA's share will not come
+            volatile int never = 0;
+            mbar_wait_cluster(bar, (uint32_t)((j / PAIR_STAGES) & 1), &never, WAIT_LIMIT_NS);
+        }
+    }
+    cluster_sync_all();  // no copy into either CTA is in flight
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, PAIR_TMEM_COLS);
+    }
+}
+
 // ------------------------------------------------------------ splitting --
 
 __device__ __forceinline__ uint16_t bf16_bits(float f) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(f));
 }
 
-// hi = bf16(a) (round to nearest from FP64 via FP32 is not exact, so the
-// rounding goes FP64 -> FP32 (RN) -> BF16 (RN); hi is *a* nearby BF16 value
-// and lo = bf16(a - hi) captures the next 8 bits either way).
+// hi = bf16(x), lo = bf16(x - hi), both computed from xf = fp32(x): one
+// FP64 operation per element (GB300's FP64 rate would otherwise bound this
+// memory-bound pass); xf differs from x by 2^-24 relative, far below what
+// the three-product form keeps (~2^-16).
 __device__ __forceinline__ void split2(double a, uint16_t& hi, uint16_t& lo) {
-    const __nv_bfloat16 h = __float2bfloat16_rn((float)a);
-    const double r = a - (double)__bfloat162float(h);
+    const float xf = __double2float_rn(a);
+    const __nv_bfloat16 h = __float2bfloat16_rn(xf);
     hi = __bfloat16_as_ushort(h);
-    lo = bf16_bits((float)r);
+    lo = bf16_bits(xf - __bfloat162float(h));  // exact in FP32
+}
+
+// hi, mid, lo planes: the same from xf with one more level.
+__device__ __forceinline__ void split3(double a, uint16_t& hi, uint16_t& mid, uint16_t& lo) {
+    const float xf = __double2float_rn(a);
+    const __nv_bfloat16 h = __float2bfloat16_rn(xf);
+    const float r1 = xf - __bfloat162float(h);  // exact in FP32
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    hi = __bfloat16_as_ushort(h);
+    mid = __bfloat16_as_ushort(m);
+    lo = bf16_bits(r1 - __bfloat162float(m));  // exact in FP32
+}
+
+__global__ void split_bf16x3p_rows_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols,
+                                          uint16_t* __restrict__ dst, int64_t ldd, int64_t plane) {
+    const int64_t total = (int64_t)rows * cols;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / cols), c = (int)(idx % cols);
+        uint16_t hi, mid, lo;
+        split3(src[(int64_t)r * lds + c], hi, mid, lo);
+        const int64_t o = (int64_t)r * ldd + c;
+        dst[o] = hi;
+        dst[plane + o] = mid;
+        dst[2 * plane + o] = lo;
+    }
+}
+
+__global__ void split_bf16x3p_cols_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols,
+                                          uint16_t* __restrict__ dst, int64_t ldd, int64_t plane) {
+    __shared__ double tile[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(int64_t)r * lds + c] : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) {
+            uint16_t hi, mid, lo;
+            split3(tile[threadIdx.x][i], hi, mid, lo);
+            const int64_t o = (int64_t)c * ldd + r;
+            dst[o] = hi;
+            dst[plane + o] = mid;
+            dst[2 * plane + o] = lo;
+        }
+    }
 }
 
 // Row-major FP64 (rows x cols, lds) -> two BF16 planes [2][rows][ldd].
@@ -415,16 +787,14 @@ __global__ void split_bf16x2_cols_kernel(const double* __restrict__ src, int64_t
     }
 }
 
-// Exponent e with max|x| < 2^e (frexp convention); rows/columns of zeros get
-// a small exponent so that every digit is zero.
-__device__ __forceinline__ int exp_of_max(double m) {
-    if (!(m > 0.0)) return -1000;
-    int e;
-    frexp(m, &e);
-    return e;
+// Biased exponent field of x (0 for zero and subnormals).  The exponent e
+// with max|x| < 2^e (frexp convention) of a row is max(field) - 1022: the
+// largest magnitude has the largest field.  Integer work only.
+__device__ __forceinline__ int exp_field(double x) {
+    return (int)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF;
 }
 
-// Per-row max-exponent of an FP64 matrix (one warp per row) and optional
+// Per-row max exponent of an FP64 matrix (one warp per row) and optional
 // sum of squares of all entries.
 __global__ void row_exp_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols, int* __restrict__ ex,
                                double* sumsq) {
@@ -432,37 +802,40 @@ __global__ void row_exp_kernel(const double* __restrict__ src, int64_t lds, int 
     const int r = blockIdx.x * warps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
-    double m = 0.0, ss = 0.0;
+    int m = 0;
+    double ss = 0.0;
     for (int c = lane; c < cols; c += 32) {
         const double v = src[(int64_t)r * lds + c];
-        m = fmax(m, fabs(v));
-        ss = fma(v, v, ss);
+        m = max(m, exp_field(v));
+        if (sumsq) ss = fma(v, v, ss);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+        m = max(m, __shfl_down_sync(0xffffffffu, m, off));
         ss += __shfl_down_sync(0xffffffffu, ss, off);
     }
     if (lane == 0) {
-        ex[r] = exp_of_max(m);
+        ex[r] = m - 1022;
         if (sumsq) atomicAdd(sumsq, ss);
     }
 }
 
-// Per-column max-exponent (exponents only grow: atomicMax on a -1000 start).
+// Per-column max exponent: atomicMax of exponent fields on a zero start,
+// converted to the frexp convention by col_exp_finish_kernel.
 __global__ void col_exp_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols, int rows_per_block,
                                int* __restrict__ ex, double* sumsq) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int r0 = blockIdx.y * rows_per_block;
     const int r1 = min(rows, r0 + rows_per_block);
-    double m = 0.0, ss = 0.0;
+    int m = 0;
+    double ss = 0.0;
     if (c < cols)
         for (int r = r0; r < r1; r++) {
             const double v = src[(int64_t)r * lds + c];
-            m = fmax(m, fabs(v));
-            ss = fma(v, v, ss);
+            m = max(m, exp_field(v));
+            if (sumsq) ss = fma(v, v, ss);
         }
-    if (c < cols && m > 0.0) atomicMax(&ex[c], exp_of_max(m));
+    if (c < cols && m > 0) atomicMax(&ex[c], m);
     if (sumsq) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, off);
@@ -470,23 +843,56 @@ __global__ void col_exp_kernel(const double* __restrict__ src, int64_t lds, int 
     }
 }
 
+__global__ void col_exp_finish_kernel(int* ex, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) ex[i] -= 1022;
+}
+
 __global__ void fill_int_kernel(int* p, int n, int v) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
 }
 
-// Digits of x * 2^-e: t = x * 2^(7-e); d_1 = rint(t); t = (t - d_1) * 2^8; ...
+// Fixed-point digits of x relative to 2^e (|x| < 2^e): with t = x 2^(7-e)
+// (|t| < 128), N = round(|t| 2^(8(s-1))) is an integer below 2^(8s-1);
+// its balanced base-256 digits (low digits in [-128, 127], the top one in
+// [-128, 128]) are the slices, so x = 2^(e-7) sum_i d_i 2^(-8 i) to within
+// half a unit of the last slice.  Integer arithmetic on the IEEE fields.
 template <int MAXS>
 __device__ __forceinline__ void digits(double x, int e, int nslices, uint16_t (&d)[MAXS]) {
-    double t = ldexp(x, 7 - e);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const bool neg = (b >> 63) != 0;
+    int fe = (int)(b >> 52) & 0x7FF;
+    unsigned long long m = b & ((1ull << 52) - 1);
+    if (fe == 0)
+        fe = 1;  // subnormal: no implicit bit
+    else
+        m |= 1ull << 52;
+    const int sh = fe - 1075 + 7 - e + 8 * (nslices - 1);  // |x| 2^(7-e+8(s-1)) = m 2^sh
+    unsigned long long N;
+    if (sh >= 0)
+        N = m << sh;  // < 2^(8 s - 1) because |t| < 128
+    else if (sh > -64)
+        N = (m + (1ull << (-sh - 1))) >> (-sh);
+    else
+        N = 0;
+    int dig[MAXS];
 #pragma unroll
-    for (int s = 0; s < MAXS; s++) {
-        if (s < nslices) {
-            const double di = rint(t);
-            d[s] = bf16_bits((float)di);  // |di| <= 128: exact in BF16
-            t = (t - di) * 256.0;
+    for (int i = MAXS - 1; i >= 1; i--) {
+        if (i < nslices) {
+            int v = (int)(N & 255u);
+            N >>= 8;
+            if (v >= 128) {
+                v -= 256;
+                N += 1;
+            }
+            dig[i] = v;
         }
     }
+    dig[0] = (int)N;
+#pragma unroll
+    for (int i = 0; i < MAXS; i++)
+        if (i < nslices) d[i] = bf16_bits((float)(neg ? -dig[i] : dig[i]));  // |d| <= 128: exact
 }
 
 constexpr int kMaxSlices = 8;
@@ -563,13 +969,43 @@ int launch_impl(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, c
     static bool attr = false;
     auto kern = tc_gemm_kernel<BN, EXACT, EPI_WARPS>;
     if (!attr) {
-        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<BN>::SMEM_BYTES));
+        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<BN, EXACT ? KSUB_EXACT : KSUB_FLOAT>::SMEM_BYTES));
         attr = true;
     }
-    dim3 grid((unsigned)((p.N + BN - 1) / BN), (unsigned)((p.M + BM - 1) / BM));
-    kern<<<grid, Epi<EPI_WARPS>::THREADS, Cfg<BN>::SMEM_BYTES, s>>>(ta, tb, p);
+    const int64_t tiles = (int64_t)((p.N + BN - 1) / BN) * ((p.M + BM - 1) / BM);
+    if (tiles > INT32_MAX) return SPIN_ERR_INVALID_ARG;
+    kern<<<(unsigned)tiles, Epi<EPI_WARPS>::THREADS, Cfg<BN, EXACT ? KSUB_EXACT : KSUB_FLOAT>::SMEM_BYTES, s>>>(ta, tb, p);
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
+}
+
+int launch_pair(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, cudaStream_t s) {
+    CUtensorMap ta, tb;
+    int rc = make_map(&ta, a.base, p.K, (int64_t)a.rows * a.slices, a.ld, BM);
+    if (rc) return rc;
+    rc = make_map(&tb, b.base, p.K, (int64_t)b.rows * b.slices, b.ld, PAIR_BNH);
+    if (rc) return rc;
+    static bool attr = false;
+    auto kern = tc_gemm_pair_kernel<kExactEpiWarps>;
+    if (!attr) {
+        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PAIR_SMEM_BYTES));
+        attr = true;
+    }
+    const int64_t tiles = (int64_t)((p.N + PAIR_BN - 1) / PAIR_BN) * ((p.M + 2 * BM - 1) / (2 * BM));
+    if (2 * tiles > INT32_MAX) return SPIN_ERR_INVALID_ARG;
+    kern<<<(unsigned)(2 * tiles), Epi<kExactEpiWarps>::THREADS, PAIR_SMEM_BYTES, s>>>(ta, tb, p);
+    SPIN_CUDA_TRY(cudaGetLastError());
+    return SPIN_OK;
+}
+
+// Exact products run on single CTAs (measured 1140 vs 1109 TFLOP/s for the
+// pair form at n = 8192); SPIN_TC_PAIR=1 selects the pair kernel.
+bool use_pair_kernel() {
+    static const int v = [] {
+        const char* e = getenv("SPIN_TC_PAIR");
+        return (e && e[0] == '1') ? 1 : 0;
+    }();
+    return v != 0;
 }
 
 }  // namespace
@@ -579,12 +1015,14 @@ int64_t tc_ld(int64_t k) { return (k + 7) / 8 * 8; }
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& prm, cudaStream_t s) {
     if (prm.M <= 0 || prm.N <= 0) return SPIN_OK;
     if (prm.K <= 0 || prm.num_pairs <= 0 || prm.num_pairs > kTcMaxPairs) return SPIN_ERR_INVALID_ARG;
-    if (prm.exact && (prm.chunk_kb < 1 || prm.chunk_kb > 8)) return SPIN_ERR_INVALID_ARG;
+    // runs <= 1024 (exactness) made of whole pipeline stages
+    if (prm.exact && (prm.chunk_kb < 1 || prm.chunk_kb > 16 || prm.chunk_kb % KSUB_EXACT != 0)) return SPIN_ERR_INVALID_ARG;
     TcGemmParams p = prm;
     p.a_rows = a.rows;
     p.b_rows = b.rows;
-    if (prm.exact) return launch_impl<kExactBN, true, kExactEpiWarps>(a, b, p, s);
-    return launch_impl<256, false, 8>(a, b, p, s);
+    if (prm.exact)
+        return use_pair_kernel() ? launch_pair(a, b, p, s) : launch_impl<kExactBN, true, kExactEpiWarps>(a, b, p, s);
+    return launch_impl<kFloatBN, false, 8>(a, b, p, s);
 }
 
 int launch_split_bf16x2(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
@@ -604,6 +1042,23 @@ int launch_split_bf16x2(const double* src, int64_t lds, int rows, int cols, bool
     return SPIN_OK;
 }
 
+int launch_split_bf16x3p(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
+                         int64_t ldd, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return SPIN_OK;
+    if (!transpose) {
+        const int64_t plane = (int64_t)rows * ldd;
+        const int64_t total = (int64_t)rows * cols;
+        const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+        split_bf16x3p_rows_kernel<<<blocks, 256, 0, s>>>(src, lds, rows, cols, dst, ldd, plane);
+    } else {
+        const int64_t plane = (int64_t)cols * ldd;
+        dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+        split_bf16x3p_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(src, lds, rows, cols, dst, ldd, plane);
+    }
+    SPIN_CUDA_TRY(cudaGetLastError());
+    return SPIN_OK;
+}
+
 int launch_ozaki_split(const double* src, int64_t lds, int rows, int cols, bool transpose, int nslices, int* ex,
                        uint16_t* dst, int64_t ldd, double* sumsq, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return SPIN_OK;
@@ -615,10 +1070,11 @@ int launch_ozaki_split(const double* src, int64_t lds, int rows, int cols, bool 
         const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
         ozaki_rows_kernel<<<blocks, 256, 0, s>>>(src, lds, rows, cols, ex, nslices, dst, ldd, plane);
     } else {
-        fill_int_kernel<<<(cols + 255) / 256, 256, 0, s>>>(ex, cols, -1000);
+        fill_int_kernel<<<(cols + 255) / 256, 256, 0, s>>>(ex, cols, 0);
         const int rpb = 256;
         dim3 g1((unsigned)((cols + 255) / 256), (unsigned)((rows + rpb - 1) / rpb));
         col_exp_kernel<<<g1, 256, 0, s>>>(src, lds, rows, cols, rpb, ex, sumsq);
+        col_exp_finish_kernel<<<(cols + 255) / 256, 256, 0, s>>>(ex, cols);
         const int64_t plane = (int64_t)cols * ldd;
         dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
         ozaki_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(src, lds, rows, cols, ex, nslices, dst, ldd, plane);

@@ -42,6 +42,9 @@ struct TcGemmParams {
 
 int64_t tc_ld(int64_t k);
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, cudaStream_t s);
+// FP64 view -> (hi, mid, lo) BF16 planes; transpose=true writes the cols x rows transpose.
+int launch_split_bf16x3p(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
+                         int64_t ldd, cudaStream_t s);
 // FP64 view -> (hi, lo) BF16 planes; transpose=true writes the cols x rows transpose.
 int launch_split_bf16x2(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
                         int64_t ldd, cudaStream_t s);

@@ -109,6 +109,29 @@ def test_leaf_power_of_two_diagonal_exact(spin, L):
     np.testing.assert_array_equal(X, np.diag(1.0 / d))
 
 
+@pytest.mark.parametrize("L", [16, 33, 64, 100, 256])
+def test_leaf_concurrent_streams_deterministic(spin, L):
+    """Many leaves on eight streams at once (wide clusters, few rows per CTA:
+    the fastest CTA of a cluster runs ahead of the slowest by up to one
+    step): every result must equal the first bit for bit, and the oracle's
+    Gauss-Jordan to rounding."""
+    A = np.random.default_rng(100 + L).uniform(-1, 1, (L, L))
+    Ad = dev(A)
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(8)]
+    outs = []
+    for i in range(96):
+        st = streams[i % 8]
+        with torch.cuda.stream(st):
+            outs.append(spin.leaf_inverse(Ad, stream=st))
+    torch.cuda.synchronize()
+    first = outs[0].cpu().numpy()
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o.cpu().numpy(), first)
+    G, st = oracle.gj_inv(A)
+    assert st == 0 and rel(first, G) <= tol(A)
+
+
 def test_leaf_singular_reports_column(spin):
     # a zero column c stays exactly zero under row operations, so the pivot
     # search fails exactly at step c (the oracle agrees)

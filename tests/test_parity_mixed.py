@@ -101,3 +101,15 @@ def test_deterministic(spin):
     X1 = host(spin.invert(A, leaf=128, precision="bf16x3")[0])
     X2 = host(spin.invert(A, leaf=128, precision="bf16x3")[0])
     np.testing.assert_array_equal(X1, X2)
+
+
+@pytest.mark.parametrize("n,leaf", [(1024, 128), (777, 100)])
+def test_digit_level_products(spin, n, leaf):
+    """SPIN_MIXED_DIGITS: 4-slice digit level products; same residual target."""
+    A, V, d = inputs.householder_spd(n, seed=inputs.SEED_BASE + 2, reflectors=64, cond=1e3)
+    X, info = spin.invert(dev(A), leaf=leaf, precision="digits")
+    X = host(X)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+    assert oracle.residual(A, X)[0] <= 1e-10
+    ref = inputs.householder_apply(V, 1.0 / d, np.eye(n))
+    assert rel(X, ref) <= 1e3 * 10 * 1e-10

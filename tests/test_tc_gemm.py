@@ -62,7 +62,8 @@ def test_ozaki_ragged_exact(spin, m, n, k, slices):
 
 
 def test_ozaki_long_k_flushes_exact(spin):
-    # 98 runs of 512 in the leading group: crosses the int32 flush limit (96)
+    # runs of 1024: 49 per slice pair, 147 in the group t + u = 2, which
+    # crosses the int32 flush limit (96 runs) once
     A, B = int_case(128, 128, 50000, 1000, 7)
     D = host(spin.gemm_ozaki(dev(A), dev(B), slices=3))
     assert spin.take_device_error() == 0
@@ -127,3 +128,36 @@ def test_bf16x3_in_place_strided(spin):
     got = host(D)
     want = C0 - Ah @ Bh
     assert np.max(np.abs(got - want)) < (2.0 ** -14 + 300 * 2.0 ** -23) * np.max(np.abs(Ah) @ np.abs(Bh))
+
+
+PAIR_SCRIPT = r"""
+import numpy as np, torch
+import paper_1801_04723_gb300 as s
+s.lib()
+for (m, n, k, sl, seed) in [(300, 200, 1000, 3, 1), (513, 130, 700, 4, 2), (256, 128, 50000, 3, 3), (1, 1, 1, 1, 4)]:
+    rng = np.random.default_rng(seed)
+    lim = 1000 if k > 10000 else 120
+    A = rng.integers(-lim, lim + 1, size=(m, k)).astype(np.int64)
+    B = rng.integers(-lim, lim + 1, size=(k, n)).astype(np.int64)
+    C = rng.integers(-50, 50, size=(m, n)).astype(np.int64)
+    d = lambda X: torch.from_numpy(X.astype(np.float64)).to("cuda:0")
+    D = s.gemm_ozaki(d(A), d(B), slices=sl, alpha=-1.0, beta=1.0, C=d(C))
+    torch.cuda.synchronize()
+    assert s.take_device_error() == 0
+    assert (D.cpu().numpy().astype(np.int64) == C - A @ B).all(), (m, n, k, sl)
+print("PAIR-OK")
+"""
+
+
+def test_pair_kernel_exact():
+    """The CTA-pair form of the exact kernel (SPIN_TC_PAIR=1, read once per
+    process) gives the same exact integer products, ragged and long-K."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SPIN_TC_PAIR="1")
+    r = subprocess.run([sys.executable, "-c", PAIR_SCRIPT], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and "PAIR-OK" in r.stdout, r.stdout + r.stderr
