@@ -164,6 +164,11 @@ typedef struct spin_serve_cfg {
     size_t hbm_budget_bytes;  /* device memory the server may hold for requests       */
     int32_t max_slots;        /* requests running at once (one stream and thread each) */
     int32_t reserved;
+    size_t max_queued_bytes;  /* load shedding: 0 = unbounded queue; else a submit whose
+                                 A (n*n*8 bytes) would take the bytes of A held by
+                                 queued, not yet admitted, requests above this is
+                                 refused with SPIN_ERR_BUSY and counted as shed (an
+                                 empty queue accepts any request)                    */
 } spin_serve_cfg;
 
 typedef struct spin_result {
@@ -181,6 +186,7 @@ typedef struct spin_serve_stats_t {
     uint64_t submitted, completed, rejected, queued;
     int32_t running, peak_running;
     size_t bytes_in_use;
+    uint64_t shed;            /* submits refused by max_queued_bytes                   */
 } spin_serve_stats_t;
 
 typedef struct spin_server spin_server;
@@ -191,8 +197,10 @@ int spin_serve_create(const spin_serve_cfg* cfg, spin_server** out);
 
 /* Queue X = A^-1.  A (host or device memory, n x n, leading dimension lda)
  * must stay valid and unchanged until the request is polled.  precision:
- * SPIN_FP64 or SPIN_MIXED_BF16X3 (tol applies to the latter).  Returns a
- * ticket; SPIN_ERR_OOM if the request alone exceeds the budget. */
+ * SPIN_FP64, SPIN_MIXED_BF16X3 or SPIN_MIXED_DIGITS (tol applies to the
+ * mixed modes).  Returns a ticket; SPIN_ERR_OOM if the request alone
+ * exceeds the budget; SPIN_ERR_BUSY (nothing queued, A may be released) if
+ * cfg.max_queued_bytes would be exceeded. */
 int spin_serve_submit(spin_server* sv, const double* A, int64_t lda, int64_t n, int precision, double tol,
                       uint64_t* ticket);
 
@@ -202,7 +210,8 @@ int spin_serve_submit(spin_server* sv, const double* A, int64_t lda, int64_t n, 
  * numerical status is r->status). */
 int spin_serve_poll(spin_server* sv, uint64_t ticket, double* X, int64_t ldx, spin_result* r);
 
-/* Counters: submitted, completed, rejected, queued, running, peak running, bytes held. */
+/* Counters: submitted, completed, rejected, queued, running, peak running,
+ * bytes held, shed. */
 int spin_serve_stats(spin_server* sv, spin_serve_stats_t* st);
 
 /* Stop the slots (running requests finish), free everything. */

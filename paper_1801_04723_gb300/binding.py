@@ -71,7 +71,8 @@ KERNEL_KINDS = {0: "leaf_gj", 1: "gemm_f64", 2: "gemm_tc", 3: "split", 4: "resid
 
 
 class ServeCfg(ctypes.Structure):
-    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_queued_bytes", ctypes.c_size_t)]
 
 
 class Result(ctypes.Structure):
@@ -99,6 +100,7 @@ class ServeStats(ctypes.Structure):
         ("running", ctypes.c_int32),
         ("peak_running", ctypes.c_int32),
         ("bytes_in_use", ctypes.c_size_t),
+        ("shed", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -463,10 +465,12 @@ SPIN_ERR_BUSY = 7
 
 class Server:
     """Request server (spin_serve_*): submit matrices (host numpy arrays or
-    CUDA tensors, kept alive by the caller until polled), poll results."""
+    CUDA tensors, kept alive by the caller until polled), poll results.
+    With ``max_queued_bytes`` a submit that would overfill the queue is shed:
+    ``submit`` returns None."""
 
-    def __init__(self, hbm_budget_bytes: int, max_slots: int = 4):
-        cfg = ServeCfg(int(hbm_budget_bytes), int(max_slots), 0)
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 4, max_queued_bytes: int = 0):
+        cfg = ServeCfg(int(hbm_budget_bytes), int(max_slots), 0, int(max_queued_bytes))
         h = ctypes.c_void_p()
         rc = lib().spin_serve_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != SPIN_OK:
@@ -474,7 +478,7 @@ class Server:
         self._h = h
         self._keep = {}
 
-    def submit(self, A, precision="bf16x3", tol: float = 1e-10) -> int:
+    def submit(self, A, precision="bf16x3", tol: float = 1e-10):
         import numpy as np
 
         if hasattr(A, "data_ptr"):
@@ -485,6 +489,8 @@ class Server:
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         t = ctypes.c_uint64(0)
         rc = lib().spin_serve_submit(self._h, ctypes.c_void_p(ptr), lda, n, p, float(tol), ctypes.byref(t))
+        if rc == SPIN_ERR_BUSY:
+            return None  # shed: the queue is full
         if rc != SPIN_OK:
             raise SpinError(rc, "spin_serve_submit")
         self._keep[t.value] = A

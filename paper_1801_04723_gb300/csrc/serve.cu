@@ -60,13 +60,14 @@ struct spin_server {
     std::deque<std::shared_ptr<spin::Request>> queue;
     std::map<uint64_t, std::shared_ptr<spin::Request>> table;
     size_t in_use = 0;
+    size_t queued_a_bytes = 0;  // n*n*8 of every queued (not yet admitted) request
     uint64_t next_ticket = 1;
     bool stop = false;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
     cudaStream_t copy_stream = nullptr;
     // counters
-    uint64_t submitted = 0, completed = 0, rejected = 0;
+    uint64_t submitted = 0, completed = 0, rejected = 0, shed = 0;
     int running = 0, peak_running = 0;
 };
 
@@ -96,6 +97,7 @@ void worker_loop(spin_server* sv, int slot) {
             if (sv->stop) return;
             rq = sv->queue.front();
             sv->queue.pop_front();
+            sv->queued_a_bytes -= (size_t)rq->n * (size_t)rq->n * sizeof(double);
             sv->in_use += rq->footprint_run + rq->footprint_keep;
             sv->running++;
             if (sv->running > sv->peak_running) sv->peak_running = sv->running;
@@ -208,6 +210,13 @@ extern "C" int spin_serve_submit(spin_server* sv, const double* A, int64_t lda, 
             sv->rejected++;
             return SPIN_ERR_OOM;  // can never fit the budget
         }
+        // an empty queue takes any request, so that none is refused for ever
+        if (sv->cfg.max_queued_bytes != 0 && sv->queued_a_bytes > 0 &&
+            sv->queued_a_bytes + nn > sv->cfg.max_queued_bytes) {
+            sv->shed++;
+            return SPIN_ERR_BUSY;  // load shedding: the queue is full
+        }
+        sv->queued_a_bytes += nn;
         rq->ticket = sv->next_ticket++;
         sv->table[rq->ticket] = rq;
         sv->queue.push_back(rq);
@@ -273,6 +282,7 @@ extern "C" int spin_serve_stats(spin_server* sv, spin_serve_stats_t* st) {
     st->running = sv->running;
     st->peak_running = sv->peak_running;
     st->bytes_in_use = sv->in_use;
+    st->shed = sv->shed;
     return SPIN_OK;
 }
 

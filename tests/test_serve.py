@@ -80,3 +80,31 @@ def test_serve_budget_and_errors(spin):
     with pytest.raises(spin.SpinError):
         srv.poll(t)  # already collected
     srv.close()
+
+
+def test_serve_load_shedding(spin):
+    """max_queued_bytes bounds the A bytes of queued (not yet admitted)
+    requests: with the only slot busy and room for two 256 x 256 requests,
+    the third and later submits are shed (None) and counted; the queued
+    ones still run and are right."""
+    nbytes = 256 * 256 * 8
+    srv = spin.Server(hbm_budget_bytes=1 << 30, max_slots=1, max_queued_bytes=2 * nbytes)
+    big = torch.from_numpy(inputs.sdd(2048, seed=3)).cuda()
+    tb = srv.submit(big, precision="fp64")
+    assert tb is not None
+    for _ in range(5000):  # the slot has taken the big request (bounded wait)
+        if srv.stats()["running"] == 1:
+            break
+        time.sleep(0.001)
+    assert srv.stats()["running"] == 1
+    smalls = [inputs.sdd(256, seed=10 + i) for i in range(5)]
+    tickets = [srv.submit(a, precision="fp64") for a in smalls]
+    assert [t is None for t in tickets] == [False, False, True, True, True]
+    assert srv.stats()["shed"] == 3
+    for a, t in zip(smalls[:2], tickets[:2]):
+        while (got := srv.poll(t)) is None:
+            time.sleep(0.001)
+        assert got[1]["status"] == 0 and oracle.residual(a, got[0])[0] <= 1e-13
+    while srv.poll(tb, discard=True) is None:
+        time.sleep(0.001)
+    srv.close()
