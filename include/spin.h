@@ -129,19 +129,27 @@ int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t
 /*
  * spin_invert_batched: X[i] = A[i]^-1 for `count` independent matrices of
  * any orders (the paper inverts one matrix at a time; the batch is this
- * library's form of its many-block parallelism, Sec. 3.3).  Plain FP64.
+ * library's form of its many-block parallelism, Sec. 3.3).
  *   A, X     host arrays of `count` device pointers (X[i] has leading
  *            dimension n[i]); lda, n: host arrays.  Matrices may not overlap.
- *   opts     NULL or spin_opts: leaf (0 = n for n <= 128, else 64) and
- *            blocking are used; precision must be SPIN_FP64.
+ *   opts     NULL or spin_opts: precision SPIN_FP64 (plain method) or
+ *            SPIN_MIXED_BF16X3 (tensor-core level products, FP64 leaves,
+ *            FP64-class Schur complements at the top fp64_levels levels,
+ *            Newton-Schulz refinement of every matrix to tol); leaf (0 = n
+ *            for n <= 128, else 64), blocking, and for the mixed form tol,
+ *            max_refine, fp64_levels and residual_slices are used.
  *   info_dev device int32[count] (may be NULL): status of each matrix
- *            (SPIN_OK or SPIN_ERR_SINGULAR), written when the work ends.
+ *            (SPIN_OK, SPIN_ERR_SINGULAR, or SPIN_ERR_NOT_CONVERGED for the
+ *            mixed form), written when the work ends.
  * Matrices of equal order form a bucket whose recursion runs in lockstep
  * (batched products, one leaf cluster per matrix); buckets run concurrently
  * on streams forked from `stream`.  The launch sequence is captured into a
  * CUDA graph on the first call and replayed while the arguments (pointers,
- * orders, leading dimensions, info_dev, leaf) stay the same; the workspace
- * is library-owned.  count <= 65535, n[i] <= 65536.
+ * orders, leading dimensions, info_dev, options) stay the same; the
+ * workspace is library-owned.  The mixed form reads residual norms on the
+ * host between refinement steps, so it returns when the batch is done (its
+ * refinement launches are not part of the graph).  count <= 65535,
+ * n[i] <= 65536.
  */
 int spin_invert_batched(const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
                         int count, const spin_opts* opts, int* info_dev, spin_stream_t stream);
@@ -149,6 +157,11 @@ int spin_invert_batched(const double* const* A, const int64_t* lda, double* cons
 /* Shape of the graph the latest spin_invert_batched on `stream` replays:
  * kernel launches per call and order buckets.  SPIN_ERR_INVALID_ARG if none. */
 int spin_batched_stats(spin_stream_t stream, int* kernels, int* buckets);
+
+/* Mixed-form refinement of the latest spin_invert_batched on `stream`:
+ * Newton-Schulz steps taken (the most over the buckets) and the largest
+ * ||A X - I||_F / (||A||_F ||X||_F) over the batch; -1 for a plain batch. */
+int spin_batched_refine_info(spin_stream_t stream, int* refine_iters, double* worst_rel);
 
 /* ---------------------------------------------------------------------
  * Serving: inversion requests admitted continuously by device-memory

@@ -25,6 +25,7 @@ from .binding import (  # noqa: F401
     invert_noalloc,
     invert_batched,
     batched_stats,
+    batched_refine_info,
     leaf_inverse,
     lib,
     status_string,

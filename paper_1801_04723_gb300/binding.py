@@ -178,6 +178,8 @@ def lib():
         L.spin_serve_destroy.restype = ctypes.c_int
         L.spin_batched_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.spin_batched_stats.restype = ctypes.c_int
+        L.spin_batched_refine_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        L.spin_batched_refine_info.restype = ctypes.c_int
         L.spin_autotune_leaf.argtypes = [i64, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp, vp]
         L.spin_autotune_leaf.restype = ctypes.c_int
         L.spin_take_device_error.argtypes = [vp]
@@ -434,9 +436,11 @@ def batched_stats(stream=None) -> dict:
     return {"kernels": k.value, "buckets": b.value}
 
 
-def invert_batched(As, *, leaf: int = 0, outs=None, stream=None, blocking: bool = True):
+def invert_batched(As, *, leaf: int = 0, outs=None, stream=None, blocking: bool = True, precision="fp64",
+                   tol: float = 1e-10, max_refine: int = 6, fp64_levels: int = 2):
     """X_i = A_i^-1 for a list of square float64 CUDA tensors of any orders
-    (spin_invert_batched).  Returns (list of X, int32 CUDA tensor of statuses)."""
+    (spin_invert_batched).  Returns (list of X, int32 CUDA tensor of statuses).
+    precision "bf16x3" runs the mixed form (returns when done)."""
     import torch
 
     count = len(As)
@@ -452,12 +456,22 @@ def invert_batched(As, *, leaf: int = 0, outs=None, stream=None, blocking: bool 
     lda = (ctypes.c_int64 * count)(*[a.stride(0) for a in As])
     ns = (ctypes.c_int64 * count)(*[a.shape[0] for a in As])
     info = torch.zeros(count, dtype=torch.int32, device=As[0].device)
-    o = make_opts("fp64", leaf, blocking=blocking)
+    o = make_opts(precision, leaf, blocking=blocking, tol=tol, max_refine=max_refine, fp64_levels=fp64_levels)
     rc = lib().spin_invert_batched(pa, lda, px, ns, count, ctypes.byref(o), ctypes.c_void_p(info.data_ptr()),
                                    _stream(stream))
     if rc != SPIN_OK:
         raise SpinError(rc, "spin_invert_batched")
     return outs, info
+
+
+def batched_refine_info(stream=None) -> dict:
+    """Refinement of the latest mixed batch on the stream: steps and worst residual."""
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    rc = lib().spin_batched_refine_info(_stream(stream), ctypes.byref(it), ctypes.byref(rel))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_batched_refine_info")
+    return {"refine_iters": it.value, "worst_rel_residual": rel.value}
 
 
 SPIN_ERR_BUSY = 7

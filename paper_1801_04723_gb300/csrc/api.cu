@@ -148,9 +148,6 @@ struct Run {
     int* err = nullptr;
 };
 
-constexpr int kTcMin = 128;     // products smaller than this in m or n stay in FP64
-constexpr int kSchurSlices = 7; // digit slices of the FP64-class Schur complements
-constexpr int kLevelSlices = 4; // digit slices of the level products in SPIN_MIXED_DIGITS
 
 // Bracket one launch with events when the stream's profiler is on.
 struct ProfScope {

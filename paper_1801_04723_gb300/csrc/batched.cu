@@ -10,6 +10,15 @@
 // The launch sequence (all buckets, fork and join) is captured once into a
 // CUDA graph and replayed while the caller passes the same arguments, so a
 // batch of thousands of matrices costs one graph launch on the host.
+//
+// Mixed precision (SPIN_MIXED_BF16X3): the same lockstep recursion with the
+// level products on the tensor cores, batched over the bucket (one launch
+// per split and per product; the digit or BF16 planes of every matrix of the
+// bucket sit in one arena, one problem after the other), FP64-class Schur
+// complements at the top fp64_levels levels, then Newton-Schulz refinement
+// of every matrix with FP64-class residuals (cached digit planes of A).
+// The refinement reads the residual norms on the host between iterations,
+// so a mixed call returns when the batch is done.
 #include <stdio.h>
 #include <string.h>
 
@@ -20,6 +29,8 @@
 #include <vector>
 
 #include "common.cuh"
+#include "mixed.h"
+#include "tc_gemm.h"
 
 namespace spin {
 namespace {
@@ -32,6 +43,11 @@ struct Bucket {
     int first;             // offset of the bucket in the sorted order
     size_t ws_elems;       // per matrix
     size_t ws_offset;      // elements into the workspace block
+    // mixed precision
+    size_t scratch_per;    // split-plane bytes per matrix (products, residual, update)
+    size_t cache_per;      // cached digit planes of A per matrix
+    size_t arena_offset;   // bytes into the plan's arena
+    int stream;            // pool stream the bucket runs on
 };
 
 struct BatchPlan {
@@ -47,7 +63,19 @@ struct BatchPlan {
     double* ws = nullptr;
     size_t ws_bytes = 0;
     int count = 0;
-    int kernels = 0;  // kernel launches in the captured graph
+    int kernels = 0;        // kernel launches of the latest call (graph + refinement)
+    int graph_kernels = 0;  // kernel launches in the captured graph
+    // mixed precision
+    int precision = SPIN_FP64;
+    int fp64_levels = 2, sr = 6, max_refine = 6;
+    double tol = 1e-10;
+    unsigned char* arena = nullptr;
+    size_t arena_bytes = 0;
+    double* norms = nullptr;       // device: [3][count] sums of squares of A, X, R (sorted order)
+    double* norms_host = nullptr;  // pinned copy
+    int* err = nullptr;            // device: SPIN_ERR_TIMEOUT from a bounded wait
+    int refine_iters = 0;
+    double worst_rel = -1.0;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;  // private stream the launch sequence is captured on
     cudaStream_t streams[kStreams] = {};
@@ -59,6 +87,15 @@ std::map<cudaStream_t, BatchPlan> g_plans;
 
 void free_plan(BatchPlan& p) {
     if (p.exec) cudaGraphExecDestroy(p.exec);
+    cudaFree(p.arena);
+    cudaFree(p.norms);
+    cudaFree(p.err);
+    if (p.norms_host) cudaFreeHost(p.norms_host);
+    p.arena = nullptr;
+    p.arena_bytes = 0;
+    p.norms = nullptr;
+    p.norms_host = nullptr;
+    p.err = nullptr;
     cudaFree((void*)p.a_base);
     cudaFree(p.a_ld);
     cudaFree(p.x_base);
@@ -132,16 +169,267 @@ int binv(BRun& r, BatchView A, BatchView X, const double* const* wbase, int64_t 
     return SPIN_OK;
 }
 
+// ---- mixed precision ----
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Split-plane bytes per matrix for a bucket of order n: the largest level
+// product (bf16x3 planes, or digit planes for the top Schur complements),
+// the residual's digit planes of X and the update's three planes of X and R.
+size_t mixed_scratch_per(int64_t n, int64_t leaf, int fp64_levels, int sr) {
+    size_t need = 0;
+    if (n > leaf) {
+        const int64_t n1 = split_order(n);
+        const size_t ld1 = (size_t)tc_ld(n1);
+        need = std::max(need, 2 * 2 * (size_t)n1 * ld1 * 2);  // bf16x3: 2 planes of m and n rows
+        if (fp64_levels > 0)
+            need = std::max(need, (size_t)kSchurSlices * 2 * (size_t)n1 * ld1 * 2 + 2 * (size_t)n1 * 4 + 512);
+    }
+    const size_t ld = (size_t)tc_ld(n);
+    need = std::max(need, (size_t)sr * (size_t)n * ld * 2 + (size_t)n * 4 + 512);  // residual: X digits
+    need = std::max(need, 3 * 2 * (size_t)n * ld * 2);                             // update: X and R planes
+    return align256(need);
+}
+
+size_t mixed_cache_per(int64_t n, int sr) {
+    return align256((size_t)sr * (size_t)n * (size_t)tc_ld(n) * 2 + (size_t)n * 4 + 512);
+}
+
+struct BMix {
+    unsigned char* scratch;  // bucket's split planes: count * scratch_per bytes
+    int count;
+    int fp64_levels;
+    int* err;
+    int* kernels;
+    cudaStream_t s;
+};
+
+template <class T>
+T* after(const void* p, size_t bytes) {
+    return (T*)(((uintptr_t)p + bytes + 255) & ~(uintptr_t)255);
+}
+
+// D(z) = beta C(z) + alpha A(z) B(z) for every matrix z of the bucket, in
+// the form the single-matrix mixed path uses for this product.
+int bproduct(BMix& x, int depth, bool schur, int64_t m, int64_t n, int64_t k, double alpha, const BatchView& A,
+             const BatchView& B, double beta, const BatchView& C, const BatchView& D) {
+    if (m < kTcMin || n < kTcMin || k < 64) {
+        (*x.kernels)++;
+        return launch_gemm_f64_batched(m, n, k, alpha, A, B, beta, C, D, x.count, x.s);
+    }
+    const int64_t ld = tc_ld(k);
+    const int64_t cnt = x.count;
+    TcGemmParams p = {};
+    p.M = (int)m;
+    p.N = (int)n;
+    p.K = (int)k;
+    p.alpha = alpha;
+    p.beta = beta;
+    p.err = x.err;
+    p.batch = x.count;
+    p.c_base = beta != 0.0 ? C.base : nullptr;
+    p.c_lds = C.lds;
+    p.c_ld = C.ld;
+    p.c_r0 = C.r0;
+    p.c_c0 = C.c0;
+    p.d_base = const_cast<double* const*>(D.base);
+    p.d_lds = D.lds;
+    p.d_ld = D.ld;
+    p.d_r0 = D.r0;
+    p.d_c0 = D.c0;
+    uint16_t* pa = (uint16_t*)x.scratch;
+    if (schur && depth < x.fp64_levels) {
+        const int sl = kSchurSlices;
+        uint16_t* pb = pa + cnt * sl * m * ld;
+        int* ea = after<int>(pb, (size_t)cnt * sl * n * ld * 2);
+        int* eb = ea + cnt * m;
+        *x.kernels += 2 * 3 + 1;
+        BRET(launch_ozaki_split_batched(A, (int)m, (int)k, false, sl, ea, pa, ld, nullptr, x.count, x.s));
+        BRET(launch_ozaki_split_batched(B, (int)k, (int)n, true, sl, eb, pb, ld, nullptr, x.count, x.s));
+        tc_pairs_ozaki(p, sl);
+        p.row_exp = ea;
+        p.col_exp = eb;
+        return launch_tc_gemm(TcOperand{pa, (int)m, sl, ld}, TcOperand{pb, (int)n, sl, ld}, p, x.s);
+    }
+    uint16_t* pb = pa + cnt * 2 * m * ld;
+    *x.kernels += 3;
+    BRET(launch_split_planes_batched(A, (int)m, (int)k, false, 2, pa, ld, x.count, x.s));
+    BRET(launch_split_planes_batched(B, (int)k, (int)n, true, 2, pb, ld, x.count, x.s));
+    tc_pairs_bf16x3(p);
+    return launch_tc_gemm(TcOperand{pa, (int)m, 2, ld}, TcOperand{pb, (int)n, 2, ld}, p, x.s);
+}
+
+// Lockstep recursion of a bucket with tensor-core level products (binv's
+// schedule; the Schur product is the one that forms S = -V).
+int binv_mixed(BRun& r, BMix& x, int depth, BatchView A, BatchView X, const double* const* wbase, int64_t woff,
+               int64_t n) {
+    if (n <= r.leaf) {
+        double* scratch = leaf_scratch_elems(n) ? r.ws_block + woff : nullptr;
+        (*r.kernels)++;
+        return launch_leaf_gj_batched(A, X, n, scratch, r.ws_stride, r.records, r.leaf_counter++, r.count, r.s);
+    }
+    const int64_t n1 = split_order(n), n2 = n - n1;
+    BatchView A12 = sub(A, 0, n1), A21 = sub(A, n1, 0), A22 = sub(A, n1, n1);
+    BatchView X11 = X, X12 = sub(X, 0, n1), X21 = sub(X, n1, 0), X22 = sub(X, n1, n1);
+    BatchView T{wbase, nullptr, n2, 0, woff};
+    BatchView S{wbase, nullptr, n2, 0, woff + n1 * n2};
+    BatchView T2{wbase, nullptr, n1, 0, woff};
+    const int64_t wsub = woff + n1 * n2 + n2 * n2;
+    BatchView none{wbase, nullptr, 1, 0, 0};
+    const int d = depth;
+    BRET(binv_mixed(r, x, d + 1, A, X11, wbase, woff, n1));
+    BRET(bproduct(x, d, false, n1, n2, n1, 1.0, X11, A12, 0.0, none, T));
+    BRET(bproduct(x, d, true, n2, n2, n1, -1.0, A21, T, 1.0, A22, S));
+    BRET(binv_mixed(r, x, d + 1, S, X22, wbase, wsub, n2));
+    BRET(bproduct(x, d, false, n1, n2, n2, -1.0, T, X22, 0.0, none, X12));
+    BRET(bproduct(x, d, false, n2, n1, n1, 1.0, A21, X11, 0.0, none, T2));
+    BRET(bproduct(x, d, false, n2, n1, n2, -1.0, X22, T2, 0.0, none, X21));
+    BRET(bproduct(x, d, false, n1, n1, n2, -1.0, X12, T2, 1.0, X11, X11));
+    return SPIN_OK;
+}
+
+// Refinement of every matrix: residuals R(z) = I - A(z) X(z) FP64-class
+// (digit planes, A's cached), X(z) <- X(z) + X(z) R(z) in the six-product
+// BF16 form, until every ||R||_F / (||A||_F ||X||_F) <= tol.  R lives in
+// each matrix's workspace.  Statuses go to the records (sorted order).
+int brefine(BatchPlan& p) {
+    const int count = p.count;
+    double* nA = p.norms;
+    double* nX = p.norms + count;
+    double* nR = p.norms + 2 * count;
+    const int sr = p.sr;
+    std::vector<int> active(p.buckets.size(), 1);
+    auto views = [&](const Bucket& b, BatchView& Av, BatchView& Xv, BatchView& Rv) {
+        Av = BatchView{p.a_base + b.first, p.a_ld + b.first, 0, 0, 0};
+        Xv = BatchView{(const double* const*)(p.x_base + b.first), nullptr, b.n, 0, 0};
+        Rv = BatchView{(const double* const*)(p.w_base + b.first), nullptr, b.n, 0, 0};
+    };
+    for (size_t bi = 0; bi < p.buckets.size(); bi++) {  // cached digit planes of A and ||A||
+        const Bucket& b = p.buckets[bi];
+        BatchView Av, Xv, Rv;
+        views(b, Av, Xv, Rv);
+        unsigned char* cache = p.arena + b.arena_offset + (size_t)b.count * b.scratch_per;
+        const int64_t ld = tc_ld(b.n);
+        uint16_t* planes = (uint16_t*)cache;
+        int* ex = after<int>(planes, (size_t)b.count * sr * b.n * ld * 2);
+        cudaStream_t s = p.streams[b.stream];
+        SPIN_CUDA_TRY(cudaMemsetAsync(nA + b.first, 0, b.count * sizeof(double), s));
+        p.kernels += 3;
+        BRET(launch_ozaki_split_batched(Av, (int)b.n, (int)b.n, false, sr, ex, planes, ld, nA + b.first, b.count, s));
+    }
+    std::vector<double> rel(count, -1.0);
+    for (int it = 0;; it++) {
+        for (size_t bi = 0; bi < p.buckets.size(); bi++) {
+            if (!active[bi]) continue;
+            const Bucket& b = p.buckets[bi];
+            BatchView Av, Xv, Rv;
+            views(b, Av, Xv, Rv);
+            const int64_t ld = tc_ld(b.n);
+            unsigned char* scratch = p.arena + b.arena_offset;
+            unsigned char* cache = scratch + (size_t)b.count * b.scratch_per;
+            uint16_t* aplanes = (uint16_t*)cache;
+            int* aex = after<int>(aplanes, (size_t)b.count * sr * b.n * ld * 2);
+            uint16_t* xplanes = (uint16_t*)scratch;
+            int* xex = after<int>(xplanes, (size_t)b.count * sr * b.n * ld * 2);
+            cudaStream_t s = p.streams[b.stream];
+            SPIN_CUDA_TRY(cudaMemsetAsync(nX + b.first, 0, b.count * sizeof(double), s));
+            SPIN_CUDA_TRY(cudaMemsetAsync(nR + b.first, 0, b.count * sizeof(double), s));
+            BRET(launch_ozaki_split_batched(Xv, (int)b.n, (int)b.n, true, sr, xex, xplanes, ld, nX + b.first,
+                                            b.count, s));
+            TcGemmParams q = {};
+            q.M = q.N = q.K = (int)b.n;
+            tc_pairs_ozaki(q, sr);
+            q.alpha = -1.0;
+            q.beta = 0.0;
+            q.add_identity = 1;
+            q.sumsq = nR + b.first;
+            q.err = p.err;
+            q.row_exp = aex;
+            q.col_exp = xex;
+            q.batch = b.count;
+            q.d_base = p.w_base + b.first;
+            q.d_ld = b.n;
+            p.kernels += 5;
+            BRET(launch_tc_gemm(TcOperand{aplanes, (int)b.n, sr, ld}, TcOperand{xplanes, (int)b.n, sr, ld}, q, s));
+        }
+        for (int i = 0; i < kStreams; i++) SPIN_CUDA_TRY(cudaStreamSynchronize(p.streams[i]));
+        SPIN_CUDA_TRY(cudaMemcpy(p.norms_host, p.norms, 3 * (size_t)count * sizeof(double), cudaMemcpyDeviceToHost));
+        bool all_done = true;
+        for (size_t bi = 0; bi < p.buckets.size(); bi++) {
+            const Bucket& b = p.buckets[bi];
+            if (!active[bi]) continue;
+            bool bucket_done = true;
+            for (int z = b.first; z < b.first + b.count; z++) {
+                const double* h = p.norms_host;
+                rel[z] = std::sqrt(h[2 * count + z]) / (std::sqrt(h[z]) * std::sqrt(h[count + z]));
+                if (!(rel[z] <= p.tol) && rel[z] == rel[z]) bucket_done = false;  // NaN: a singular leaf
+            }
+            if (bucket_done) active[bi] = 0;
+            all_done = all_done && bucket_done;
+        }
+        p.refine_iters = it;
+        if (all_done || it >= p.max_refine) break;
+        for (size_t bi = 0; bi < p.buckets.size(); bi++) {  // X <- X + X R
+            if (!active[bi]) continue;
+            const Bucket& b = p.buckets[bi];
+            BatchView Av, Xv, Rv;
+            views(b, Av, Xv, Rv);
+            const int64_t ld = tc_ld(b.n);
+            uint16_t* xp = (uint16_t*)(p.arena + b.arena_offset);
+            uint16_t* rp = xp + (int64_t)b.count * 3 * b.n * ld;
+            cudaStream_t s = p.streams[b.stream];
+            BRET(launch_split_planes_batched(Xv, (int)b.n, (int)b.n, false, 3, xp, ld, b.count, s));
+            BRET(launch_split_planes_batched(Rv, (int)b.n, (int)b.n, true, 3, rp, ld, b.count, s));
+            TcGemmParams q = {};
+            q.M = q.N = q.K = (int)b.n;
+            tc_pairs_bf16x6(q);
+            q.alpha = 1.0;
+            q.beta = 1.0;
+            q.err = p.err;
+            q.batch = b.count;
+            q.c_base = Xv.base;
+            q.c_ld = b.n;
+            q.d_base = p.x_base + b.first;
+            q.d_ld = b.n;
+            p.kernels += 3;
+            BRET(launch_tc_gemm(TcOperand{xp, (int)b.n, 3, ld}, TcOperand{rp, (int)b.n, 3, ld}, q, s));
+        }
+    }
+    // statuses: a failed leaf stays SPIN_ERR_SINGULAR; else converged or not
+    std::vector<int32_t> rec((size_t)count * INFO_WORDS);
+    SPIN_CUDA_TRY(cudaMemcpy(rec.data(), p.records, rec.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    int herr = 0;
+    SPIN_CUDA_TRY(cudaMemcpy(&herr, p.err, sizeof(int), cudaMemcpyDeviceToHost));
+    p.worst_rel = 0.0;
+    for (int z = 0; z < count; z++) {
+        int32_t& st = rec[(size_t)z * INFO_WORDS + INFO_STATUS];
+        if (st == 0 && herr) st = herr;
+        if (st == 0 && !(rel[z] <= p.tol)) st = SPIN_ERR_NOT_CONVERGED;
+        if (rel[z] == rel[z]) p.worst_rel = std::max(p.worst_rel, rel[z]);
+    }
+    SPIN_CUDA_TRY(cudaMemcpy(p.records, rec.data(), rec.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    return SPIN_OK;
+}
+
 int64_t batched_leaf(int64_t n, int leaf_opt) {
     int64_t L = leaf_opt > 0 ? leaf_opt : (n <= 128 ? n : 64);
     return std::min<int64_t>(L, n);
 }
 
 int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
-               int count, int leaf_opt, int* info_dev, cudaStream_t s) {
+               int count, const spin_opts& o, int* info_dev, cudaStream_t s) {
     free_plan(p);
+    const int leaf_opt = o.leaf;
+    const bool mixed = o.precision != SPIN_FP64;
     p.count = count;
     p.kernels = 0;
+    p.precision = o.precision;
+    p.tol = o.tol;
+    p.max_refine = o.max_refine;
+    p.fp64_levels = o.fp64_levels;
+    p.sr = o.residual_slices > 0 ? o.residual_slices : (o.tol >= 1e-11 ? 6 : 7);
+    p.refine_iters = 0;
+    p.worst_rel = -1.0;
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] < n[b]; });
@@ -156,8 +444,14 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
         b.count = j - i;
         b.first = i;
         b.ws_elems = std::max<size_t>(fp64_workspace_elems(b.n, b.leaf), 1);
+        if (mixed) b.ws_elems = std::max<size_t>(b.ws_elems, (size_t)b.n * (size_t)b.n);  // holds R
         b.ws_offset = ws_total;
         ws_total += b.ws_elems * (size_t)b.count;
+        b.scratch_per = mixed ? mixed_scratch_per(b.n, b.leaf, p.fp64_levels, p.sr) : 0;
+        b.cache_per = mixed ? mixed_cache_per(b.n, p.sr) : 0;
+        b.arena_offset = p.arena_bytes;
+        p.arena_bytes += (size_t)b.count * (b.scratch_per + b.cache_per);
+        b.stream = 0;
         p.buckets.push_back(b);
         i = j;
     }
@@ -168,6 +462,15 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
     if (cudaMalloc(&p.ws, ws_total * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return SPIN_ERR_OOM;
+    }
+    if (mixed) {
+        if (cudaMalloc(&p.arena, std::max<size_t>(p.arena_bytes, 256)) != cudaSuccess) {
+            cudaGetLastError();
+            return SPIN_ERR_OOM;
+        }
+        SPIN_CUDA_TRY(cudaMalloc(&p.norms, 3 * (size_t)count * sizeof(double)));
+        SPIN_CUDA_TRY(cudaMallocHost(&p.norms_host, 3 * (size_t)count * sizeof(double)));
+        SPIN_CUDA_TRY(cudaMalloc(&p.err, sizeof(int)));
     }
     p.ws_bytes = ws_total * sizeof(double);
     for (const Bucket& b : p.buckets)
@@ -206,6 +509,7 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
     SPIN_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     int rc = SPIN_OK;
     cudaError_t e = cudaMemsetAsync(p.records, 0, (size_t)count * INFO_WORDS * sizeof(int32_t), s);
+    if (e == cudaSuccess && mixed) e = cudaMemsetAsync(p.err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaEventRecord(p.fork, s);
     for (int i = 0; i < kStreams && e == cudaSuccess; i++) e = cudaStreamWaitEvent(p.streams[i], p.fork, 0);
     if (e != cudaSuccess) {
@@ -221,14 +525,20 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
     std::vector<double> load(kStreams, 0.0);
     for (int bi : by_work) {
         if (rc != SPIN_OK) break;
-        const Bucket& b = p.buckets[bi];
+        Bucket& b = p.buckets[bi];
         const int si = (int)(std::min_element(load.begin(), load.end()) - load.begin());
         load[si] += (double)b.count * b.n * b.n * b.n;
+        b.stream = si;
         BRun r{&p.kernels, p.streams[si], p.records + (int64_t)b.first * INFO_WORDS, 0, b.leaf, b.count,
                p.ws + b.ws_offset, (int64_t)b.ws_elems};
         BatchView Av{p.a_base + b.first, p.a_ld + b.first, 0, 0, 0};
         BatchView Xv{(const double* const*)(p.x_base + b.first), nullptr, b.n, 0, 0};
-        rc = binv(r, Av, Xv, (const double* const*)(p.w_base + b.first), 0, b.n);
+        if (mixed) {
+            BMix x{p.arena + b.arena_offset, b.count, p.fp64_levels, p.err, &p.kernels, p.streams[si]};
+            rc = binv_mixed(r, x, 0, Av, Xv, (const double* const*)(p.w_base + b.first), 0, b.n);
+        } else {
+            rc = binv(r, Av, Xv, (const double* const*)(p.w_base + b.first), 0, b.n);
+        }
     }
     for (int i = 0; i < kStreams; i++) {
         cudaError_t e2 = cudaEventRecord(p.join[i], p.streams[i]);
@@ -238,7 +548,7 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
             rc = SPIN_ERR_CUDA;
         }
     }
-    if (rc == SPIN_OK && info_dev != nullptr) {
+    if (rc == SPIN_OK && info_dev != nullptr && !mixed) {  // mixed: after the refinement
         p.kernels++;
         scatter_status_kernel<<<(count + 255) / 256, 256, 0, s>>>(p.records, p.user_index, count, info_dev);
         cudaError_t e3 = cudaGetLastError();
@@ -256,15 +566,23 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
     cudaError_t ei = cudaGraphInstantiate(&p.exec, graph, 0);
     cudaGraphDestroy(graph);
     SPIN_CUDA_TRY(ei);
+    p.graph_kernels = p.kernels;
     return SPIN_OK;
 }
 
 std::vector<uint64_t> make_key(const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
-                               int count, int leaf, int* info_dev) {
+                               int count, const spin_opts& o, int* info_dev) {
     std::vector<uint64_t> k;
-    k.reserve((size_t)count * 4 + 4);
+    k.reserve((size_t)count * 4 + 8);
     k.push_back((uint64_t)count);
-    k.push_back((uint64_t)(int64_t)leaf);
+    k.push_back((uint64_t)(int64_t)o.leaf);
+    k.push_back((uint64_t)(int64_t)o.precision);
+    uint64_t tb;
+    memcpy(&tb, &o.tol, sizeof(tb));
+    k.push_back(tb);
+    k.push_back((uint64_t)(int64_t)o.max_refine);
+    k.push_back((uint64_t)(int64_t)o.fp64_levels);
+    k.push_back((uint64_t)(int64_t)o.residual_slices);
     k.push_back((uint64_t)(uintptr_t)info_dev);
     int dev = 0;
     cudaGetDevice(&dev);
@@ -287,8 +605,12 @@ extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, d
                                    int count, const spin_opts* opts, int* info_dev, spin_stream_t stream) {
     if (count < 1 || A == nullptr || lda == nullptr || X == nullptr || n == nullptr) return SPIN_ERR_INVALID_ARG;
     spin_opts o = opts ? *opts : spin_opts_default();
-    if (o.precision != SPIN_FP64) return SPIN_ERR_NOT_IMPLEMENTED;
+    if (o.precision != SPIN_FP64 && o.precision != SPIN_MIXED_BF16X3) return SPIN_ERR_NOT_IMPLEMENTED;
+    const bool mixed = o.precision != SPIN_FP64;
     if (o.leaf < 0) return SPIN_ERR_INVALID_ARG;
+    if (mixed && (o.residual_slices < 0 || o.residual_slices > 7 || o.max_refine < 0 || !(o.tol > 0.0) ||
+                  o.fp64_levels < 0))
+        return SPIN_ERR_INVALID_ARG;
     for (int i = 0; i < count; i++) {
         if (n[i] < 1 || n[i] > 65536 || lda[i] < n[i] || A[i] == nullptr || X[i] == nullptr) return SPIN_ERR_INVALID_ARG;
         if (((uintptr_t)A[i] & 7u) || ((uintptr_t)X[i] & 7u)) return SPIN_ERR_INVALID_ARG;
@@ -298,9 +620,9 @@ extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, d
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_bmu);
     BatchPlan& p = g_plans[s];
-    std::vector<uint64_t> key = make_key(A, lda, X, n, count, o.leaf, info_dev);
+    std::vector<uint64_t> key = make_key(A, lda, X, n, count, o, info_dev);
     if (p.exec == nullptr || key != p.key) {
-        int rc = build_plan(p, A, lda, X, n, count, o.leaf, info_dev, s);
+        int rc = build_plan(p, A, lda, X, n, count, o, info_dev, s);
         if (rc != SPIN_OK) {
             free_plan(p);
             p.key.clear();
@@ -309,7 +631,27 @@ extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, d
         p.key = key;
     }
     SPIN_CUDA_TRY(cudaGraphLaunch(p.exec, s));
-    if (o.blocking) SPIN_CUDA_TRY(cudaStreamSynchronize(s));
+    if (mixed) {
+        SPIN_CUDA_TRY(cudaStreamSynchronize(s));
+        p.kernels = p.graph_kernels;
+        int rc = brefine(p);
+        if (rc != SPIN_OK) return rc;
+        if (info_dev != nullptr) p.kernels++;
+        if (info_dev != nullptr) {
+            scatter_status_kernel<<<(count + 255) / 256, 256, 0, s>>>(p.records, p.user_index, count, info_dev);
+            SPIN_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    if (o.blocking || mixed) SPIN_CUDA_TRY(cudaStreamSynchronize(s));
+    return SPIN_OK;
+}
+
+extern "C" int spin_batched_refine_info(spin_stream_t stream, int* refine_iters, double* worst_rel) {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    auto it = g_plans.find((cudaStream_t)stream);
+    if (it == g_plans.end() || it->second.exec == nullptr) return SPIN_ERR_INVALID_ARG;
+    if (refine_iters) *refine_iters = it->second.refine_iters;
+    if (worst_rel) *worst_rel = it->second.worst_rel;
     return SPIN_OK;
 }
 

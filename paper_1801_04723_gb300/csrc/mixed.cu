@@ -16,6 +16,44 @@
 
 namespace spin {
 
+void tc_pairs_bf16x3(TcGemmParams& p) {
+    const int8_t pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
+    p.num_pairs = 3;
+    for (int i = 0; i < 3; i++) {
+        p.pa[i] = pa[i];
+        p.pb[i] = pb[i];
+        p.pg[i] = 0;
+    }
+    p.exact = 0;
+}
+
+void tc_pairs_bf16x6(TcGemmParams& p) {
+    // planes 0 = hi, 1 = mid, 2 = lo: pairs of combined weight >= 2^-16
+    const int8_t pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+    p.num_pairs = 6;
+    for (int i = 0; i < 6; i++) {
+        p.pa[i] = pa[i];
+        p.pb[i] = pb[i];
+        p.pg[i] = 0;
+    }
+    p.exact = 0;
+}
+
+void tc_pairs_ozaki(TcGemmParams& p, int slices) {
+    int q = 0;
+    for (int w = 0; w < slices; w++)  // group w: pairs (t, u) with t + u = w
+        for (int t = 0; t <= w; t++) {
+            p.pa[q] = (int8_t)t;
+            p.pb[q] = (int8_t)(w - t);
+            p.pg[q] = (int8_t)w;
+            q++;
+        }
+    p.num_pairs = q;
+    for (int w = 0; w < slices; w++) p.group_shift[w] = -14 - 8 * w;
+    p.exact = 1;
+    p.chunk_kb = 16;  // runs of 1024: every partial sum is an integer of magnitude <= 2^24, exact in FP32
+}
+
 int MixScratch::reserve(size_t bytes) {
     if (bytes <= cap) return SPIN_OK;
     if (base) cudaFree(base);
@@ -89,14 +127,7 @@ int product_bf16x3(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double 
     p.M = (int)m;
     p.N = (int)n;
     p.K = (int)k;
-    p.num_pairs = 3;
-    const int8_t pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
-    for (int i = 0; i < 3; i++) {
-        p.pa[i] = pa[i];
-        p.pb[i] = pb[i];
-        p.pg[i] = 0;
-    }
-    p.exact = 0;
+    tc_pairs_bf16x3(p);
     p.alpha = alpha;
     p.beta = beta;
     p.C = C;
@@ -131,15 +162,7 @@ int product_bf16x6(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double 
     p.M = (int)m;
     p.N = (int)n;
     p.K = (int)k;
-    // planes 0 = hi, 1 = mid, 2 = lo: pairs of combined weight >= 2^-16
-    const int8_t pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
-    p.num_pairs = 6;
-    for (int i = 0; i < 6; i++) {
-        p.pa[i] = pa[i];
-        p.pb[i] = pb[i];
-        p.pg[i] = 0;
-    }
-    p.exact = 0;
+    tc_pairs_bf16x6(p);
     p.alpha = alpha;
     p.beta = beta;
     p.C = C;
@@ -158,18 +181,7 @@ int product_ozaki(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double a
     p.M = (int)m;
     p.N = (int)n;
     p.K = (int)k;
-    int q = 0;
-    for (int w = 0; w < slices; w++)  // group w: pairs (t, u) with t + u = w
-        for (int t = 0; t <= w; t++) {
-            p.pa[q] = (int8_t)t;
-            p.pb[q] = (int8_t)(w - t);
-            p.pg[q] = (int8_t)w;
-            q++;
-        }
-    p.num_pairs = q;
-    for (int w = 0; w < slices; w++) p.group_shift[w] = -14 - 8 * w;
-    p.exact = 1;
-    p.chunk_kb = 16;  // runs of 1024: every partial sum is an integer of magnitude <= 2^24, exact in FP32
+    tc_pairs_ozaki(p, slices);
     p.alpha = alpha;
     p.beta = beta;
     p.C = C;

@@ -4,7 +4,19 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "tc_gemm.h"
+
 namespace spin {
+
+constexpr int kSchurSlices = 7;  // digit slices of the FP64-class Schur complements
+constexpr int kLevelSlices = 4;  // digit slices of the level products in SPIN_MIXED_DIGITS
+constexpr int64_t kTcMin = 128;  // products smaller than this in m or n stay in FP64
+
+// Slice-pair schedules of the tensor-core product forms (fill pa, pb, pg,
+// num_pairs and the exactness fields of p).
+void tc_pairs_bf16x3(TcGemmParams& p);           // planes hi, lo: hi hi + hi lo + lo hi
+void tc_pairs_bf16x6(TcGemmParams& p);           // planes hi, mid, lo: pairs of weight >= 2^-16
+void tc_pairs_ozaki(TcGemmParams& p, int slices);  // digit pairs t + u < slices, exact runs
 
 // A growable device arena for split planes.
 struct MixScratch {

@@ -122,6 +122,19 @@ __device__ __forceinline__ double scaled_int(int x, int E) {
 
 static_assert(sizeof(SmemCtl) <= 256, "control block");
 
+// Row grow of D (and of C, or null) for problem z.
+__device__ __forceinline__ double* out_row(const TcGemmParams& p, int z, int grow) {
+    if (!p.batch) return p.D + (int64_t)grow * p.ldd;
+    const int64_t ld = p.d_lds ? p.d_lds[z] : p.d_ld;
+    return p.d_base[z] + (p.d_r0 + grow) * ld + p.d_c0;
+}
+__device__ __forceinline__ const double* in_row(const TcGemmParams& p, int z, int grow) {
+    if (!p.batch) return p.C ? p.C + (int64_t)grow * p.ldc : nullptr;
+    if (!p.c_base) return nullptr;
+    const int64_t ld = p.c_lds ? p.c_lds[z] : p.c_ld;
+    return p.c_base[z] + (p.c_r0 + grow) * ld + p.c_c0;
+}
+
 __device__ __forceinline__ void raise_timeout(SmemCtl* ctl, int* err) {
     ctl->abort = 1;
     if (err) atomicCAS(err, 0, SPIN_ERR_TIMEOUT);
@@ -156,7 +169,7 @@ template <int BN, int HALF, bool PAIR>
 __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl* ctl, volatile int* abort,
                                                  uint32_t lane_addr, int half, int grow, int col0,
                                                  int nchunks_per_pair, int lane, uint32_t tempty_c0,
-                                                 uint32_t tempty_c1) {
+                                                 uint32_t tempty_c1, int z) {
     const bool row_ok = grow < p.M;
     double sumsq = 0.0;
     // alpha = +-1 (every product of the method) is a sign flip of the integer
@@ -168,7 +181,8 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
     for (int j = 0; j < HALF; j++) acc[j] = 0;
     int chunk = 0, since_flush = 0;
     bool first_flush = true, ok = true;
-    const int erow = (p.row_exp && row_ok) ? p.row_exp[grow] : 0;
+    const int* col_exp = p.col_exp ? p.col_exp + (p.batch ? (int64_t)z * p.N : 0) : nullptr;
+    const int erow = (p.row_exp && row_ok) ? p.row_exp[(p.batch ? (int64_t)z * p.M : 0) + grow] : 0;
     for (int q = 0; q < p.num_pairs && ok; q++) {
         for (int c = 0; c < nchunks_per_pair && ok; c++) {
             const int buf = chunk & 1;
@@ -216,8 +230,8 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
                 // this thread's columns stays in TMEM until the last flush,
                 // which writes D once.
                 const int er = erow + p.group_shift[(int)p.pg[q]];
-                double* drow = p.D + (int64_t)grow * p.ldd;
-                const double* crow = p.C ? p.C + (int64_t)grow * p.ldc : nullptr;
+                double* drow = out_row(p, z, grow);
+                const double* crow = in_row(p, z, grow);
                 const uint32_t sum_addr = lane_addr + (uint32_t)(2 * BN + half * 2 * HALF);
 #pragma unroll
                 for (int jj = 0; jj < HALF; jj += 8) {
@@ -230,7 +244,7 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
                     for (int j = 0; j < 8; j++) {
                         const int gcol = col0 + jj + j;
                         const bool ok_ij = row_ok && gcol < p.N;
-                        const int ec = (p.col_exp && ok_ij) ? p.col_exp[gcol] : 0;
+                        const int ec = (col_exp && ok_ij) ? col_exp[gcol] : 0;
                         double val = scaled_int(alpha_sign * acc[jj + j], er + ec);
                         if (alpha_general) val *= p.alpha;
                         if (first_flush) {
@@ -282,6 +296,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     SmemCtl* ctl = reinterpret_cast<SmemCtl*>(base + STAGES * STAGE_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int z = p.batch ? (int)blockIdx.y : 0;  // problem of a batched launch
     // Grouped rasterisation: consecutive CTAs sweep a band of GROUP_M row
     // blocks column by column, so the CTAs resident at one time share a few
     // B column blocks and a few A row blocks (L2 reuse) instead of streaming
@@ -340,9 +355,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
                 for (int u = 0; u < KS; u++) {
                     tma_load_2d(smA + (s * KS + u) * A_TILE_BYTES, &tmA, (kb + u) * BK,
-                                p.pa[pair] * p.a_rows + m0, &ctl->full[s]);
+                                (int)(z * p.a_zrows) + p.pa[pair] * p.a_rows + m0, &ctl->full[s]);
                     tma_load_2d(smB + (s * KS + u) * B_TILE_BYTES, &tmB, (kb + u) * BK,
-                                p.pb[pair] * p.b_rows + n0, &ctl->full[s]);
+                                (int)(z * p.b_zrows) + p.pb[pair] * p.b_rows + n0, &ctl->full[s]);
                 }
                 it++;
                 return true;
@@ -450,8 +465,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     tmem_ld_32x32b_x16(lane_addr + (uint32_t)(half * HALF + cc), v);
                     tmem_ld_wait();
                     if (row_ok) {
-                        const double* crow = p.C ? p.C + (int64_t)grow * p.ldc : nullptr;
-                        double* drow = p.D + (int64_t)grow * p.ldd;
+                        const double* crow = in_row(p, z, grow);
+                        double* drow = out_row(p, z, grow);
 #pragma unroll
                         for (int j = 0; j < 16; j++) {
                             const int gcol = col0 + cc + j;
@@ -471,12 +486,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             if (lane == 0) mbar_arrive(&ctl->tempty[0]);
         } else {
             sumsq = exact_epilogue<BN, HALF, false>(p, ctl, abort, lane_addr, half, grow, col0, nchunks_per_pair,
-                                                    lane, 0u, 0u);
+                                                    lane, 0u, 0u, z);
         }
         if (p.sumsq) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) sumsq += __shfl_down_sync(0xffffffffu, sumsq, off);
-            if (lane == 0 && sumsq != 0.0) atomicAdd(p.sumsq, sumsq);
+            if (lane == 0 && sumsq != 0.0) atomicAdd(p.sumsq + (p.batch ? z : 0), sumsq);
         }
     }
 
@@ -524,6 +539,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();  // 0 issues the pair's MMAs
+    const int z = p.batch ? (int)blockIdx.y : 0;
     int m0, n0;  // the pair's tile; grouped rasterisation as in tc_gemm_kernel
     {
         const int num_m = (p.M + 2 * BM - 1) / (2 * BM), num_n = (p.N + PAIR_BN - 1) / PAIR_BN;
@@ -586,9 +602,9 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 #pragma unroll
                         for (int u = 0; u < KSUB_EXACT; u++) {
                             tma_load_2d_pair(smA + (s * KSUB_EXACT + u) * A_TILE_BYTES, &tmA, (kb + u) * BK,
-                                             p.pa[q] * p.a_rows + my_m0, bar);
+                                             (int)(z * p.a_zrows) + p.pa[q] * p.a_rows + my_m0, bar);
                             tma_load_2d_pair(smB + (s * KSUB_EXACT + u) * PAIR_B_BYTES, &tmB, (kb + u) * BK,
-                                             p.pb[q] * p.b_rows + my_n0, bar);
+                                             (int)(z * p.b_zrows) + p.pb[q] * p.b_rows + my_n0, bar);
                         }
                         it++;
                     }
@@ -654,11 +670,11 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         const uint32_t lane_addr = tmem_base + ((uint32_t)(quarter * 32) << 16);
         double sumsq = exact_epilogue<PAIR_BN, HALF, true>(
             p, ctl, abort, lane_addr, half, grow, n0 + half * HALF, nchunks_per_pair, lane,
-            mapa_u32(smem_u32(&ctl->tempty[0]), 0u), mapa_u32(smem_u32(&ctl->tempty[1]), 0u));
+            mapa_u32(smem_u32(&ctl->tempty[0]), 0u), mapa_u32(smem_u32(&ctl->tempty[1]), 0u), z);
         if (p.sumsq) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) sumsq += __shfl_down_sync(0xffffffffu, sumsq, off);
-            if (lane == 0 && sumsq != 0.0) atomicAdd(p.sumsq, sumsq);
+            if (lane == 0 && sumsq != 0.0) atomicAdd(p.sumsq + (p.batch ? z : 0), sumsq);
         }
     }
 
@@ -715,14 +731,35 @@ __device__ __forceinline__ void split3(double a, uint16_t& hi, uint16_t& mid, ui
     lo = bf16_bits(r1 - __bfloat162float(m));  // exact in FP32
 }
 
-__global__ void split_bf16x3p_rows_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols,
-                                          uint16_t* __restrict__ dst, int64_t ldd, int64_t plane) {
+// Operand source of a split: one FP64 view, or problem z's view of a batch.
+struct SrcOne {
+    const double* p;
+    int64_t ld;
+    __device__ __forceinline__ const double* row(int, int r) const { return p + (int64_t)r * ld; }
+};
+struct SrcMany {
+    BatchView v;
+    __device__ __forceinline__ const double* row(int z, int r) const {
+        const int64_t l = v.ld_of(z);
+        return v.base[z] + (v.r0 + r) * l + v.c0;
+    }
+};
+
+// Every split kernel handles problem z = blockIdx.z: its planes start at
+// dst + z * dzs, its exponents at ex + z * exs, its sum of squares at
+// sumsq[z * sss] (sss = 0: one shared sum).
+
+template <class Src>
+__global__ void split_bf16x3p_rows_kernel(Src src, int rows, int cols, uint16_t* __restrict__ dst, int64_t ldd,
+                                          int64_t plane, int64_t dzs) {
+    const int z = blockIdx.z;
+    dst += z * dzs;
     const int64_t total = (int64_t)rows * cols;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(idx / cols), c = (int)(idx % cols);
         uint16_t hi, mid, lo;
-        split3(src[(int64_t)r * lds + c], hi, mid, lo);
+        split3(src.row(z, r)[c], hi, mid, lo);
         const int64_t o = (int64_t)r * ldd + c;
         dst[o] = hi;
         dst[plane + o] = mid;
@@ -730,13 +767,16 @@ __global__ void split_bf16x3p_rows_kernel(const double* __restrict__ src, int64_
     }
 }
 
-__global__ void split_bf16x3p_cols_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols,
-                                          uint16_t* __restrict__ dst, int64_t ldd, int64_t plane) {
+template <class Src>
+__global__ void split_bf16x3p_cols_kernel(Src src, int rows, int cols, uint16_t* __restrict__ dst, int64_t ldd,
+                                          int64_t plane, int64_t dzs) {
     __shared__ double tile[32][33];
+    const int z = blockIdx.z;
+    dst += z * dzs;
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int r = r0 + i, c = c0 + threadIdx.x;
-        tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(int64_t)r * lds + c] : 0.0;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? src.row(z, r)[c] : 0.0;
     }
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -752,28 +792,34 @@ __global__ void split_bf16x3p_cols_kernel(const double* __restrict__ src, int64_
     }
 }
 
-// Row-major FP64 (rows x cols, lds) -> two BF16 planes [2][rows][ldd].
-__global__ void split_bf16x2_rows_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols,
-                                         uint16_t* __restrict__ dst, int64_t ldd, int64_t plane) {
+// Row-major FP64 (rows x cols) -> two BF16 planes [2][rows][ldd].
+template <class Src>
+__global__ void split_bf16x2_rows_kernel(Src src, int rows, int cols, uint16_t* __restrict__ dst, int64_t ldd,
+                                         int64_t plane, int64_t dzs) {
+    const int z = blockIdx.z;
+    dst += z * dzs;
     const int64_t total = (int64_t)rows * cols;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(idx / cols), c = (int)(idx % cols);
         uint16_t hi, lo;
-        split2(src[(int64_t)r * lds + c], hi, lo);
+        split2(src.row(z, r)[c], hi, lo);
         dst[(int64_t)r * ldd + c] = hi;
         dst[plane + (int64_t)r * ldd + c] = lo;
     }
 }
 
-// FP64 (rows=K x cols=N, lds) -> transposed BF16 planes [2][N][ldd] (N x K).
-__global__ void split_bf16x2_cols_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols,
-                                         uint16_t* __restrict__ dst, int64_t ldd, int64_t plane) {
+// FP64 (rows=K x cols=N) -> transposed BF16 planes [2][N][ldd] (N x K).
+template <class Src>
+__global__ void split_bf16x2_cols_kernel(Src src, int rows, int cols, uint16_t* __restrict__ dst, int64_t ldd,
+                                         int64_t plane, int64_t dzs) {
     __shared__ double tile[32][33];
+    const int z = blockIdx.z;
+    dst += z * dzs;
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int r = r0 + i, c = c0 + threadIdx.x;
-        tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(int64_t)r * lds + c] : 0.0;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? src.row(z, r)[c] : 0.0;
     }
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -796,16 +842,19 @@ __device__ __forceinline__ int exp_field(double x) {
 
 // Per-row max exponent of an FP64 matrix (one warp per row) and optional
 // sum of squares of all entries.
-__global__ void row_exp_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols, int* __restrict__ ex,
-                               double* sumsq) {
+template <class Src>
+__global__ void row_exp_kernel(Src src, int rows, int cols, int* __restrict__ ex, int64_t exs, double* sumsq,
+                               int64_t sss) {
+    const int z = blockIdx.z;
     const int warps = blockDim.x >> 5;
     const int r = blockIdx.x * warps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
+    const double* sr = src.row(z, r);
     int m = 0;
     double ss = 0.0;
     for (int c = lane; c < cols; c += 32) {
-        const double v = src[(int64_t)r * lds + c];
+        const double v = sr[c];
         m = max(m, exp_field(v));
         if (sumsq) ss = fma(v, v, ss);
     }
@@ -815,15 +864,17 @@ __global__ void row_exp_kernel(const double* __restrict__ src, int64_t lds, int 
         ss += __shfl_down_sync(0xffffffffu, ss, off);
     }
     if (lane == 0) {
-        ex[r] = m - 1022;
-        if (sumsq) atomicAdd(sumsq, ss);
+        ex[z * exs + r] = m - 1022;
+        if (sumsq) atomicAdd(sumsq + z * sss, ss);
     }
 }
 
 // Per-column max exponent: atomicMax of exponent fields on a zero start,
 // converted to the frexp convention by col_exp_finish_kernel.
-__global__ void col_exp_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols, int rows_per_block,
-                               int* __restrict__ ex, double* sumsq) {
+template <class Src>
+__global__ void col_exp_kernel(Src src, int rows, int cols, int rows_per_block, int* __restrict__ ex, int64_t exs,
+                               double* sumsq, int64_t sss) {
+    const int z = blockIdx.z;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int r0 = blockIdx.y * rows_per_block;
     const int r1 = min(rows, r0 + rows_per_block);
@@ -831,25 +882,25 @@ __global__ void col_exp_kernel(const double* __restrict__ src, int64_t lds, int 
     double ss = 0.0;
     if (c < cols)
         for (int r = r0; r < r1; r++) {
-            const double v = src[(int64_t)r * lds + c];
+            const double v = src.row(z, r)[c];
             m = max(m, exp_field(v));
             if (sumsq) ss = fma(v, v, ss);
         }
-    if (c < cols && m > 0) atomicMax(&ex[c], m);
+    if (c < cols && m > 0) atomicMax(&ex[z * exs + c], m);
     if (sumsq) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, off);
-        if ((threadIdx.x & 31) == 0 && ss != 0.0) atomicAdd(sumsq, ss);
+        if ((threadIdx.x & 31) == 0 && ss != 0.0) atomicAdd(sumsq + z * sss, ss);
     }
 }
 
-__global__ void col_exp_finish_kernel(int* ex, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void col_exp_finish_kernel(int* ex, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) ex[i] -= 1022;
 }
 
-__global__ void fill_int_kernel(int* p, int n, int v) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void fill_int_kernel(int* p, int64_t n, int v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
 }
 
@@ -897,27 +948,33 @@ __device__ __forceinline__ void digits(double x, int e, int nslices, uint16_t (&
 
 constexpr int kMaxSlices = 8;
 
-__global__ void ozaki_rows_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols,
-                                  const int* __restrict__ ex, int nslices, uint16_t* __restrict__ dst, int64_t ldd,
-                                  int64_t plane) {
+template <class Src>
+__global__ void ozaki_rows_kernel(Src src, int rows, int cols, const int* __restrict__ ex, int64_t exs, int nslices,
+                                  uint16_t* __restrict__ dst, int64_t ldd, int64_t plane, int64_t dzs) {
+    const int z = blockIdx.z;
+    dst += z * dzs;
+    ex += z * exs;
     const int64_t total = (int64_t)rows * cols;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(idx / cols), c = (int)(idx % cols);
         uint16_t d[kMaxSlices];
-        digits<kMaxSlices>(src[(int64_t)r * lds + c], ex[r], nslices, d);
-        for (int s = 0; s < nslices; s++) dst[s * plane + (int64_t)r * ldd + c] = d[s];
+        digits<kMaxSlices>(src.row(z, r)[c], ex[r], nslices, d);
+        for (int q = 0; q < nslices; q++) dst[q * plane + (int64_t)r * ldd + c] = d[q];
     }
 }
 
-__global__ void ozaki_cols_kernel(const double* __restrict__ src, int64_t lds, int rows, int cols,
-                                  const int* __restrict__ ex, int nslices, uint16_t* __restrict__ dst, int64_t ldd,
-                                  int64_t plane) {
+template <class Src>
+__global__ void ozaki_cols_kernel(Src src, int rows, int cols, const int* __restrict__ ex, int64_t exs, int nslices,
+                                  uint16_t* __restrict__ dst, int64_t ldd, int64_t plane, int64_t dzs) {
     __shared__ double tile[32][33];
+    const int z = blockIdx.z;
+    dst += z * dzs;
+    ex += z * exs;
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int r = r0 + i, c = c0 + threadIdx.x;
-        tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(int64_t)r * lds + c] : 0.0;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? src.row(z, r)[c] : 0.0;
     }
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -925,7 +982,7 @@ __global__ void ozaki_cols_kernel(const double* __restrict__ src, int64_t lds, i
         if (c < cols && r < rows) {
             uint16_t d[kMaxSlices];
             digits<kMaxSlices>(tile[threadIdx.x][i], ex[c], nslices, d);
-            for (int s = 0; s < nslices; s++) dst[s * plane + (int64_t)c * ldd + r] = d[s];
+            for (int q = 0; q < nslices; q++) dst[q * plane + (int64_t)c * ldd + r] = d[q];
         }
     }
 }
@@ -962,9 +1019,10 @@ int make_map(CUtensorMap* m, const uint16_t* base, int64_t inner, int64_t outer,
 template <int BN, bool EXACT, int EPI_WARPS>
 int launch_impl(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, cudaStream_t s) {
     CUtensorMap ta, tb;
-    int rc = make_map(&ta, a.base, p.K, (int64_t)a.rows * a.slices, a.ld, BM);
+    const int64_t nz = p.batch ? p.batch : 1;
+    int rc = make_map(&ta, a.base, p.K, (int64_t)a.rows * a.slices * nz, a.ld, BM);
     if (rc) return rc;
-    rc = make_map(&tb, b.base, p.K, (int64_t)b.rows * b.slices, b.ld, BN);
+    rc = make_map(&tb, b.base, p.K, (int64_t)b.rows * b.slices * nz, b.ld, BN);
     if (rc) return rc;
     static bool attr = false;
     auto kern = tc_gemm_kernel<BN, EXACT, EPI_WARPS>;
@@ -974,16 +1032,18 @@ int launch_impl(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, c
     }
     const int64_t tiles = (int64_t)((p.N + BN - 1) / BN) * ((p.M + BM - 1) / BM);
     if (tiles > INT32_MAX) return SPIN_ERR_INVALID_ARG;
-    kern<<<(unsigned)tiles, Epi<EPI_WARPS>::THREADS, Cfg<BN, EXACT ? KSUB_EXACT : KSUB_FLOAT>::SMEM_BYTES, s>>>(ta, tb, p);
+    kern<<<dim3((unsigned)tiles, (unsigned)nz), Epi<EPI_WARPS>::THREADS,
+           Cfg<BN, EXACT ? KSUB_EXACT : KSUB_FLOAT>::SMEM_BYTES, s>>>(ta, tb, p);
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
 }
 
 int launch_pair(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, cudaStream_t s) {
     CUtensorMap ta, tb;
-    int rc = make_map(&ta, a.base, p.K, (int64_t)a.rows * a.slices, a.ld, BM);
+    const int64_t nz = p.batch ? p.batch : 1;
+    int rc = make_map(&ta, a.base, p.K, (int64_t)a.rows * a.slices * nz, a.ld, BM);
     if (rc) return rc;
-    rc = make_map(&tb, b.base, p.K, (int64_t)b.rows * b.slices, b.ld, PAIR_BNH);
+    rc = make_map(&tb, b.base, p.K, (int64_t)b.rows * b.slices * nz, b.ld, PAIR_BNH);
     if (rc) return rc;
     static bool attr = false;
     auto kern = tc_gemm_pair_kernel<kExactEpiWarps>;
@@ -993,7 +1053,8 @@ int launch_pair(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, c
     }
     const int64_t tiles = (int64_t)((p.N + PAIR_BN - 1) / PAIR_BN) * ((p.M + 2 * BM - 1) / (2 * BM));
     if (2 * tiles > INT32_MAX) return SPIN_ERR_INVALID_ARG;
-    kern<<<(unsigned)(2 * tiles), Epi<kExactEpiWarps>::THREADS, PAIR_SMEM_BYTES, s>>>(ta, tb, p);
+    kern<<<dim3((unsigned)(2 * tiles), (unsigned)nz), Epi<kExactEpiWarps>::THREADS, PAIR_SMEM_BYTES, s>>>(ta, tb,
+                                                                                                       p);
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
 }
@@ -1017,70 +1078,102 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& p
     if (prm.K <= 0 || prm.num_pairs <= 0 || prm.num_pairs > kTcMaxPairs) return SPIN_ERR_INVALID_ARG;
     // runs <= 1024 (exactness) made of whole pipeline stages
     if (prm.exact && (prm.chunk_kb < 1 || prm.chunk_kb > 16 || prm.chunk_kb % KSUB_EXACT != 0)) return SPIN_ERR_INVALID_ARG;
+    if (prm.batch < 0 || prm.batch > 65535) return SPIN_ERR_INVALID_ARG;
+    if (prm.batch && (int64_t)prm.batch * a.rows * a.slices > INT32_MAX) return SPIN_ERR_INVALID_ARG;
+    if (prm.batch && (int64_t)prm.batch * b.rows * b.slices > INT32_MAX) return SPIN_ERR_INVALID_ARG;
     TcGemmParams p = prm;
     p.a_rows = a.rows;
     p.b_rows = b.rows;
+    p.a_zrows = p.batch ? (int64_t)a.rows * a.slices : 0;
+    p.b_zrows = p.batch ? (int64_t)b.rows * b.slices : 0;
     if (prm.exact)
         return use_pair_kernel() ? launch_pair(a, b, p, s) : launch_impl<kExactBN, true, kExactEpiWarps>(a, b, p, s);
     return launch_impl<kFloatBN, false, 8>(a, b, p, s);
 }
 
-int launch_split_bf16x2(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
-                        int64_t ldd, cudaStream_t s) {
-    if (rows <= 0 || cols <= 0) return SPIN_OK;
+namespace {
+
+// Grid of a row-wise split: blocks per problem so that the whole launch has
+// about 16 blocks per SM.
+dim3 rows_grid(int64_t total, int count) {
+    const int64_t per = std::max<int64_t>(1, (152 * 16) / std::max(1, count));
+    return dim3((unsigned)std::min<int64_t>((total + 255) / 256, per), 1, (unsigned)count);
+}
+
+template <class Src>
+int split_planes(Src src, int rows, int cols, bool transpose, int planes, uint16_t* dst, int64_t ldd, int count,
+                 cudaStream_t s) {
+    if (rows <= 0 || cols <= 0 || count <= 0) return SPIN_OK;
+    const int64_t plane = (int64_t)(transpose ? cols : rows) * ldd;
+    const int64_t dzs = planes * plane;
     if (!transpose) {
-        const int64_t plane = (int64_t)rows * ldd;
-        const int64_t total = (int64_t)rows * cols;
-        const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-        split_bf16x2_rows_kernel<<<blocks, 256, 0, s>>>(src, lds, rows, cols, dst, ldd, plane);
+        const dim3 g = rows_grid((int64_t)rows * cols, count);
+        if (planes == 2)
+            split_bf16x2_rows_kernel<Src><<<g, 256, 0, s>>>(src, rows, cols, dst, ldd, plane, dzs);
+        else
+            split_bf16x3p_rows_kernel<Src><<<g, 256, 0, s>>>(src, rows, cols, dst, ldd, plane, dzs);
     } else {
-        const int64_t plane = (int64_t)cols * ldd;
-        dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-        split_bf16x2_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(src, lds, rows, cols, dst, ldd, plane);
+        const dim3 g((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32), (unsigned)count);
+        if (planes == 2)
+            split_bf16x2_cols_kernel<Src><<<g, dim3(32, 8), 0, s>>>(src, rows, cols, dst, ldd, plane, dzs);
+        else
+            split_bf16x3p_cols_kernel<Src><<<g, dim3(32, 8), 0, s>>>(src, rows, cols, dst, ldd, plane, dzs);
     }
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
+}
+
+template <class Src>
+int split_digits(Src src, int rows, int cols, bool transpose, int nslices, int* ex, uint16_t* dst, int64_t ldd,
+                 double* sumsq, int64_t sss, int count, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0 || count <= 0) return SPIN_OK;
+    if (nslices < 1 || nslices > kMaxSlices) return SPIN_ERR_INVALID_ARG;
+    if (!transpose) {
+        const int64_t plane = (int64_t)rows * ldd, dzs = nslices * plane;
+        row_exp_kernel<Src><<<dim3((unsigned)((rows + 7) / 8), 1, (unsigned)count), 256, 0, s>>>(
+            src, rows, cols, ex, rows, sumsq, sss);
+        ozaki_rows_kernel<Src><<<rows_grid((int64_t)rows * cols, count), 256, 0, s>>>(src, rows, cols, ex, rows,
+                                                                                      nslices, dst, ldd, plane, dzs);
+    } else {
+        const int64_t plane = (int64_t)cols * ldd, dzs = nslices * plane, nex = (int64_t)cols * count;
+        fill_int_kernel<<<(unsigned)((nex + 255) / 256), 256, 0, s>>>(ex, nex, 0);
+        const int rpb = 256;
+        const dim3 g1((unsigned)((cols + 255) / 256), (unsigned)((rows + rpb - 1) / rpb), (unsigned)count);
+        col_exp_kernel<Src><<<g1, 256, 0, s>>>(src, rows, cols, rpb, ex, cols, sumsq, sss);
+        col_exp_finish_kernel<<<(unsigned)((nex + 255) / 256), 256, 0, s>>>(ex, nex);
+        const dim3 g((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32), (unsigned)count);
+        ozaki_cols_kernel<Src><<<g, dim3(32, 8), 0, s>>>(src, rows, cols, ex, cols, nslices, dst, ldd, plane, dzs);
+    }
+    SPIN_CUDA_TRY(cudaGetLastError());
+    return SPIN_OK;
+}
+
+}  // namespace
+
+int launch_split_bf16x2(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
+                        int64_t ldd, cudaStream_t s) {
+    return split_planes(SrcOne{src, lds}, rows, cols, transpose, 2, dst, ldd, 1, s);
 }
 
 int launch_split_bf16x3p(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
                          int64_t ldd, cudaStream_t s) {
-    if (rows <= 0 || cols <= 0) return SPIN_OK;
-    if (!transpose) {
-        const int64_t plane = (int64_t)rows * ldd;
-        const int64_t total = (int64_t)rows * cols;
-        const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-        split_bf16x3p_rows_kernel<<<blocks, 256, 0, s>>>(src, lds, rows, cols, dst, ldd, plane);
-    } else {
-        const int64_t plane = (int64_t)cols * ldd;
-        dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-        split_bf16x3p_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(src, lds, rows, cols, dst, ldd, plane);
-    }
-    SPIN_CUDA_TRY(cudaGetLastError());
-    return SPIN_OK;
+    return split_planes(SrcOne{src, lds}, rows, cols, transpose, 3, dst, ldd, 1, s);
 }
 
 int launch_ozaki_split(const double* src, int64_t lds, int rows, int cols, bool transpose, int nslices, int* ex,
                        uint16_t* dst, int64_t ldd, double* sumsq, cudaStream_t s) {
-    if (rows <= 0 || cols <= 0) return SPIN_OK;
-    if (nslices < 1 || nslices > kMaxSlices) return SPIN_ERR_INVALID_ARG;
-    if (!transpose) {
-        row_exp_kernel<<<(rows + 7) / 8, 256, 0, s>>>(src, lds, rows, cols, ex, sumsq);
-        const int64_t plane = (int64_t)rows * ldd;
-        const int64_t total = (int64_t)rows * cols;
-        const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-        ozaki_rows_kernel<<<blocks, 256, 0, s>>>(src, lds, rows, cols, ex, nslices, dst, ldd, plane);
-    } else {
-        fill_int_kernel<<<(cols + 255) / 256, 256, 0, s>>>(ex, cols, 0);
-        const int rpb = 256;
-        dim3 g1((unsigned)((cols + 255) / 256), (unsigned)((rows + rpb - 1) / rpb));
-        col_exp_kernel<<<g1, 256, 0, s>>>(src, lds, rows, cols, rpb, ex, sumsq);
-        col_exp_finish_kernel<<<(cols + 255) / 256, 256, 0, s>>>(ex, cols);
-        const int64_t plane = (int64_t)cols * ldd;
-        dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-        ozaki_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(src, lds, rows, cols, ex, nslices, dst, ldd, plane);
-    }
-    SPIN_CUDA_TRY(cudaGetLastError());
-    return SPIN_OK;
+    return split_digits(SrcOne{src, lds}, rows, cols, transpose, nslices, ex, dst, ldd, sumsq, 0, 1, s);
+}
+
+int launch_split_planes_batched(const BatchView& src, int rows, int cols, bool transpose, int planes,
+                                uint16_t* dst, int64_t ldd, int count, cudaStream_t s) {
+    if (planes != 2 && planes != 3) return SPIN_ERR_INVALID_ARG;
+    return split_planes(SrcMany{src}, rows, cols, transpose, planes, dst, ldd, count, s);
+}
+
+int launch_ozaki_split_batched(const BatchView& src, int rows, int cols, bool transpose, int nslices, int* ex,
+                               uint16_t* dst, int64_t ldd, double* sumsq, int count, cudaStream_t s) {
+    return split_digits(SrcMany{src}, rows, cols, transpose, nslices, ex, dst, ldd, sumsq, 1, count, s);
 }
 
 }  // namespace spin

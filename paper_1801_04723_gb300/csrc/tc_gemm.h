@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "common.cuh"
+
 namespace spin {
 
 constexpr int kTcMaxPairs = 32;
@@ -38,6 +40,21 @@ struct TcGemmParams {
     int add_identity;
     double* sumsq;           // if set: += sum of squares of the final D values
     int* err;                // set to SPIN_ERR_TIMEOUT if a bounded wait gives up
+    // Batched launches (batch > 0): problem z = blockIdx.y.  The operand
+    // planes of problem z follow those of problem z - 1 in the slice stack
+    // (a_zrows = slices * rows of one problem, filled by launch_tc_gemm);
+    // C and D of problem z are views base[z] + (r0 + i) * ld + c0 with ld =
+    // lds[z] (or the uniform ld when lds is null); row_exp / col_exp hold M
+    // (N) entries per problem; sumsq has one entry per problem.  C, ldc, D
+    // and ldd are unused.
+    int batch;
+    int64_t a_zrows, b_zrows;
+    const double* const* c_base;
+    const int64_t* c_lds;
+    int64_t c_ld, c_r0, c_c0;
+    double* const* d_base;
+    const int64_t* d_lds;
+    int64_t d_ld, d_r0, d_c0;
 };
 
 int64_t tc_ld(int64_t k);
@@ -52,5 +69,14 @@ int launch_split_bf16x2(const double* src, int64_t lds, int rows, int cols, bool
 // per-column) exponents in ex; sumsq (optional) += sum of squares of src.
 int launch_ozaki_split(const double* src, int64_t lds, int rows, int cols, bool transpose, int nslices, int* ex,
                        uint16_t* dst, int64_t ldd, double* sumsq, cudaStream_t s);
+
+// Batched forms: problem z's FP64 view is src(z); its planes start at
+// dst + z * planes * (transpose ? cols : rows) * ldd (the slice stack a
+// batched product expects), its exponents at ex + z * (rows or cols) and its
+// sum of squares at sumsq[z] (sumsq optional).
+int launch_split_planes_batched(const BatchView& src, int rows, int cols, bool transpose, int planes,
+                                uint16_t* dst, int64_t ldd, int count, cudaStream_t s);
+int launch_ozaki_split_batched(const BatchView& src, int rows, int cols, bool transpose, int nslices, int* ex,
+                               uint16_t* dst, int64_t ldd, double* sumsq, int count, cudaStream_t s);
 
 }  // namespace spin

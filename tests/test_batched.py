@@ -80,3 +80,49 @@ def test_batch_matches_single_calls(spin):
         xs, _ = spin.invert(a, leaf=64)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(x.cpu().numpy(), xs.cpu().numpy())
+
+
+def test_batch_mixed_precision(spin):
+    """Mixed form: tensor-core level products (orders >= 256 reach them),
+    FP64-class Schur complements and residuals, Newton-Schulz to 1e-10 for
+    every matrix; residuals re-checked by the oracle and against each
+    matrix's known inverse where it has one."""
+    orders = [32, 96, 200, 256, 300, 512, 640, 1024, 1024, 384]
+    mats, known = [], []
+    for i, n in enumerate(orders):
+        if i % 3 == 2:
+            A, V, d = inputs.householder_spd(n, seed=inputs.SEED_BASE + 40 + i, reflectors=16, cond=1e3)
+            mats.append(A)
+            known.append((V, d))
+        else:
+            mats.append(inputs.sdd(n, seed=2000 + i))
+            known.append(None)
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    Xs, info = spin.invert_batched(As, precision="bf16x3", tol=1e-10)
+    torch.cuda.synchronize()
+    assert info.cpu().tolist() == [0] * len(orders)
+    ri = spin.batched_refine_info()
+    assert 0 < ri["worst_rel_residual"] <= 1e-10
+    for A, X, kn in zip(mats, Xs, known):
+        X = X.cpu().numpy()
+        assert oracle.residual(A, X)[0] <= 1e-10
+        if kn is not None:
+            ref = inputs.householder_apply(kn[0], 1.0 / kn[1], np.eye(A.shape[0]))
+            assert np.linalg.norm(X - ref) / np.linalg.norm(ref) <= 1e3 * 10 * 1e-10
+
+
+def test_batch_mixed_strided_singular_and_replay(spin):
+    big = torch.zeros((700, 900), dtype=torch.float64, device="cuda:0")
+    a0 = inputs.spd_gram(300, seed=7)
+    big[10:310, 20:320] = torch.from_numpy(a0).cuda()
+    sing = np.eye(256)
+    sing[:, 100] = 0.0  # a zero column: the leaf holding it fails
+    a2 = inputs.sdd(512, seed=8)
+    As = [big[10:310, 20:320], torch.from_numpy(sing).cuda(), torch.from_numpy(a2).cuda()]
+    for _ in range(2):  # the second call replays the captured recursion
+        Xs, info = spin.invert_batched(As, precision="bf16x3", tol=1e-10)
+        torch.cuda.synchronize()
+        st = info.cpu().tolist()
+        assert st[0] == 0 and st[1] == 2 and st[2] == 0
+        assert oracle.residual(a0, Xs[0].cpu().numpy())[0] <= 1e-10
+        assert oracle.residual(a2, Xs[2].cpu().numpy())[0] <= 1e-10
