@@ -145,7 +145,7 @@ int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t
  * (batched products, one leaf cluster per matrix); buckets run concurrently
  * on streams forked from `stream`.  The launch sequence is captured into a
  * CUDA graph on the first call and replayed while the arguments (pointers,
- * orders, leading dimensions, info_dev, options) stay the same; the
+ * orders, leading dimensions, options) stay the same; the
  * workspace is library-owned.  The mixed form reads residual norms on the
  * host between refinement steps, so it returns when the batch is done (its
  * refinement launches are not part of the graph).  count <= 65535,

@@ -173,6 +173,11 @@ int binv(BRun& r, BatchView A, BatchView X, const double* const* wbase, int64_t 
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+#ifndef SPIN_TC_MIN_BATCHED
+#define SPIN_TC_MIN_BATCHED 32
+#endif
+constexpr int64_t kTcMinBatched = SPIN_TC_MIN_BATCHED;
+
 // Split-plane bytes per matrix for a bucket of order n: the largest level
 // product (bf16x3 planes, or digit planes for the top Schur complements),
 // the residual's digit planes of X and the update's three planes of X and R.
@@ -213,7 +218,11 @@ T* after(const void* p, size_t bytes) {
 // the form the single-matrix mixed path uses for this product.
 int bproduct(BMix& x, int depth, bool schur, int64_t m, int64_t n, int64_t k, double alpha, const BatchView& A,
              const BatchView& B, double beta, const BatchView& C, const BatchView& D) {
-    if (m < kTcMin || n < kTcMin || k < 64) {
+    // The batch's products are small and numerous: on the tensor cores a
+    // 128 x 256 tile that a 32 x 32 product fills to 1/32 still outruns the
+    // FP64 pipe (GB300's BF16 rate is ~1500x its FP64 rate), so only products
+    // below 32 in some dimension stay in FP64.
+    if (m < kTcMinBatched || n < kTcMinBatched || k < kTcMinBatched) {
         (*x.kernels)++;
         return launch_gemm_f64_batched(m, n, k, alpha, A, B, beta, C, D, x.count, x.s);
     }
@@ -417,7 +426,7 @@ int64_t batched_leaf(int64_t n, int leaf_opt) {
 }
 
 int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
-               int count, const spin_opts& o, int* info_dev, cudaStream_t s) {
+               int count, const spin_opts& o, cudaStream_t s) {
     free_plan(p);
     const int leaf_opt = o.leaf;
     const bool mixed = o.precision != SPIN_FP64;
@@ -503,7 +512,7 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
     // Capture on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured); the graph is launched on the
     // caller's stream.  Order: memset records, fork, buckets (largest first,
-    // least-loaded stream), join, scatter statuses.
+    // least-loaded stream), join.  The statuses are scattered after it.
     cudaGraph_t graph = nullptr;
     s = p.cap;
     SPIN_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -548,15 +557,6 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
             rc = SPIN_ERR_CUDA;
         }
     }
-    if (rc == SPIN_OK && info_dev != nullptr && !mixed) {  // mixed: after the refinement
-        p.kernels++;
-        scatter_status_kernel<<<(count + 255) / 256, 256, 0, s>>>(p.records, p.user_index, count, info_dev);
-        cudaError_t e3 = cudaGetLastError();
-        if (e3 != cudaSuccess) {
-            record_cuda_error(e3, "scatter", __FILE__, __LINE__);
-            rc = SPIN_ERR_CUDA;
-        }
-    }
     cudaError_t ec = cudaStreamEndCapture(s, &graph);
     if (rc != SPIN_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -571,7 +571,7 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
 }
 
 std::vector<uint64_t> make_key(const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
-                               int count, const spin_opts& o, int* info_dev) {
+                               int count, const spin_opts& o) {
     std::vector<uint64_t> k;
     k.reserve((size_t)count * 4 + 8);
     k.push_back((uint64_t)count);
@@ -583,7 +583,6 @@ std::vector<uint64_t> make_key(const double* const* A, const int64_t* lda, doubl
     k.push_back((uint64_t)(int64_t)o.max_refine);
     k.push_back((uint64_t)(int64_t)o.fp64_levels);
     k.push_back((uint64_t)(int64_t)o.residual_slices);
-    k.push_back((uint64_t)(uintptr_t)info_dev);
     int dev = 0;
     cudaGetDevice(&dev);
     k.push_back((uint64_t)dev);
@@ -620,9 +619,9 @@ extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, d
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_bmu);
     BatchPlan& p = g_plans[s];
-    std::vector<uint64_t> key = make_key(A, lda, X, n, count, o, info_dev);
+    std::vector<uint64_t> key = make_key(A, lda, X, n, count, o);
     if (p.exec == nullptr || key != p.key) {
-        int rc = build_plan(p, A, lda, X, n, count, o, info_dev, s);
+        int rc = build_plan(p, A, lda, X, n, count, o, s);
         if (rc != SPIN_OK) {
             free_plan(p);
             p.key.clear();
@@ -636,11 +635,15 @@ extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, d
         p.kernels = p.graph_kernels;
         int rc = brefine(p);
         if (rc != SPIN_OK) return rc;
-        if (info_dev != nullptr) p.kernels++;
-        if (info_dev != nullptr) {
-            scatter_status_kernel<<<(count + 255) / 256, 256, 0, s>>>(p.records, p.user_index, count, info_dev);
-            SPIN_CUDA_TRY(cudaGetLastError());
-        }
+    } else {
+        p.kernels = p.graph_kernels;
+    }
+    // statuses go to the caller's array outside the graph, so that a new
+    // info_dev does not force a new capture
+    if (info_dev != nullptr) {
+        p.kernels++;
+        scatter_status_kernel<<<(count + 255) / 256, 256, 0, s>>>(p.records, p.user_index, count, info_dev);
+        SPIN_CUDA_TRY(cudaGetLastError());
     }
     if (o.blocking || mixed) SPIN_CUDA_TRY(cudaStreamSynchronize(s));
     return SPIN_OK;
