@@ -98,6 +98,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: arrival window (s)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: Poisson arrival rate (req/s)")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--pretransform", type=int, default=0, choices=[0, 1, 2],
+                    help="single-matrix workloads: random butterfly transform around the recursion "
+                         "(1: always, 2: after a breakdown); the default workloads need none")
     ap.add_argument("--oracle-sizes", default="", help="reference arm: also time one oracle inversion at each of "
                     "these orders (all host threads, plus one thread at the smallest) and add them to the line")
     ap.add_argument("--serve-fp64-path", default="mixed", choices=["mixed", "plain"],
@@ -358,10 +361,11 @@ def oracle_size_sweep(w: dict, sizes: list) -> list:
 class SingleWork:
     """One matrix per rank: spin_invert_ex on a device-resident input."""
 
-    def __init__(self, spin, w, n, leaf, device):
+    def __init__(self, spin, w, n, leaf, device, pretransform=0):
         import torch
 
         self.spin, self.w, self.n, self.leaf = spin, w, n, leaf
+        self.pt = pretransform
         self.A, self.known = make_input(w, n, device)
         self.X = torch.empty_like(self.A)
         self.flops = 2.0 * float(n) ** 3
@@ -371,7 +375,8 @@ class SingleWork:
         self.h2d = self.d2h = 8 * n * n
 
     def step(self):
-        self.spin.invert(self.A, leaf=self.leaf, precision=self.w["precision"], out=self.X, blocking=False)
+        self.spin.invert(self.A, leaf=self.leaf, precision=self.w["precision"], out=self.X, blocking=False,
+                         pretransform=self.pt, rbt_seed=SEED_BASE + 5)
 
     def launches(self, recs, steps):
         return len(recs)
@@ -380,7 +385,8 @@ class SingleWork:
         return self.spin.sync(check=False)
 
     def e2e_step(self):
-        self.spin.invert_host(self.Ah.numpy(), leaf=self.leaf, precision=self.w["precision"], out=self.Xh.numpy())
+        self.spin.invert_host(self.Ah.numpy(), leaf=self.leaf, precision=self.w["precision"], out=self.Xh.numpy(),
+                              pretransform=self.pt, rbt_seed=SEED_BASE + 5)
 
     def accuracy(self, probes):
         out = {"rel_residual_est": freivalds_rel(self.A, self.X, probes, SEED_BASE + 77) if probes > 0 else None}
@@ -468,7 +474,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
     if w["family"] == "batch_sdd":
         work = BatchWork(spin, w, n, leaf, device, BATCH_COUNT)
     else:
-        work = SingleWork(spin, w, n, leaf, device)
+        work = SingleWork(spin, w, n, leaf, device, args.pretransform)
     stream = torch.cuda.current_stream()
     flops = work.flops
 
@@ -561,6 +567,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
     e2e_t = statistics.median(e2e_ok) if e2e_ok else None
     batch = isinstance(work, BatchWork)
     config = {"workload": args.workload, "n": n, "leaf": leaf, "precision": w["precision"],
+              **({"pretransform": args.pretransform} if args.pretransform else {}),
               "matrices_per_gpu": len(work.orders) if batch else 1, "parallelism": f"replicas{world}",
               "desc": w["desc"]}
     if batch:

@@ -85,6 +85,16 @@ typedef struct spin_opts {
     void* workspace;           /* optional caller device buffer (>= spin_workspace_bytes);
                                   NULL: the library uses its own cached per-device buffer     */
     size_t workspace_bytes;
+    int32_t pretransform;      /* for matrices whose leading blocks may be singular (the
+                                  recursion does not pivot across blocks):
+                                  0 (default) none;
+                                  1 random butterfly transform of depth 2: X = V (U^T A V)^-1 U^T
+                                    with U, V recursive butterflies (A padded with the identity
+                                    to a multiple of 4); the mixed modes then refine X against A;
+                                  2 the plain recursion first, and on a zero or non-finite pivot
+                                    the transform (the call then waits for the first attempt)  */
+    int32_t reserved0;
+    uint64_t rbt_seed;         /* seed of the butterflies' random diagonals (splitmix64)      */
 } spin_opts;
 
 /* Result record of one inversion. */
@@ -94,6 +104,8 @@ typedef struct spin_info {
     int64_t fail_leaf;         /* leaf index (execution order) whose pivot failed, else -1     */
     int64_t fail_col;          /* pivot column inside that leaf, else -1                       */
     double rel_residual;       /* last computed ||AX-I||_F/(||A||_F||X||_F); -1 if none        */
+    int32_t pretransformed;    /* 1 if the result came through the random butterfly transform */
+    int32_t reserved;
 } spin_info;
 
 spin_opts spin_opts_default(void);
@@ -153,6 +165,13 @@ int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t
  */
 int spin_invert_batched(const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
                         int count, const spin_opts* opts, int* info_dev, spin_stream_t stream);
+
+/* The random diagonals of the butterfly transform for order n (padded to
+ * np, a multiple of 2^depth): 2 * depth * np doubles written to out_dev,
+ * U's levels then V's, level k entry i = exp((u - 1/2) / 10) with u the
+ * 53-bit uniform of splitmix64(seed) at counter (b * depth + k) * np + i.
+ * For tests and for callers that apply the transform themselves. */
+int spin_rbt_diagonals(uint64_t seed, int64_t n, int depth, double* out_dev, spin_stream_t stream);
 
 /* Shape of the graph the latest spin_invert_batched on `stream` replays:
  * kernel launches per call and order buckets.  SPIN_ERR_INVALID_ARG if none. */

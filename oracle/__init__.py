@@ -19,15 +19,22 @@ numpy.  Functions:
 * :func:`counts` -- operation counters of the last :func:`strassen_inv` call
   (leaves, internal nodes, products, subtractions, scalar multiplications,
   product flops), which pin the recursion against Sec. 4 / Table 2.
+* :func:`rbt_inv` -- the random butterfly transform around Algorithm 1 for
+  matrices whose leading blocks are singular (dense definition; the
+  uniforms are passed in).
 
 Pins (tests under ``tests/test_oracle_*.py``): the 2x2 closed form, exact
 rational inverses by Cramer's rule for n <= 6, permutation and power-of-two
 diagonal matrices (exact), block-diagonal inputs, 2^k scaling, Householder
-matrices of known inverse, numpy/LAPACK inversion, and the operation counts.
+matrices of known inverse, numpy/LAPACK inversion, and the operation counts;
+for the butterfly transform: the order-2 closed form, |det W| = the product
+of its diagonal entries, orthogonality when every entry is 1, LAPACK's
+inverse, and a matrix with a singular leading block.
 """
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -193,6 +200,65 @@ def rel_diff(X: np.ndarray, Y: np.ndarray) -> float:
     """||X - Y||_F / ||Y||_F."""
     X, Y = _f64(X), _f64(Y)
     return _load().oracle_rel_diff(_ptr(X), X.shape[1], _ptr(Y), Y.shape[1], X.shape[0], X.shape[1])
+
+
+# ------------------------------------------------ random butterfly transform --
+#
+# The recursion (Algorithm 1) does not pivot across blocks; a matrix whose
+# leading block or Schur complement is singular breaks it.  The random
+# butterfly transform of Parker (1995), recursive form of Baboulin, Dongarra,
+# Herrmann and Tomov (2013): a butterfly of order m (h = m/2) is
+# B = [[R, S], [R, -S]] / sqrt(2) with R, S random diagonal h x h matrices;
+# the recursive butterfly of depth d is W = L_d ... L_1 where level k is
+# block diagonal with 2^(k-1) butterflies of order n / 2^(k-1); with U, V two
+# such matrices, A^-1 = V (U^T A V)^-1 U^T.  Diagonal entries exp(rho/10),
+# rho = u - 1/2 for uniforms u passed in (the caller draws them).
+# Everything below is the definition written out with dense matrices.
+
+def rbt_padded_order(n: int, depth: int = 2) -> int:
+    q = 2 ** depth
+    return -(-n // q) * q
+
+
+def rbt_butterfly(diag_levels: np.ndarray) -> np.ndarray:
+    """W = L_d ... L_1 from the level diagonals (d x np): level k (1-based,
+    row k-1) has blocks of order m = np / 2^(k-1), block j using R =
+    diag[j*m : j*m+h] and S = diag[j*m+h : (j+1)*m]."""
+    d, np_ = diag_levels.shape
+    W = np.eye(np_)
+    c = 1.0 / math.sqrt(2.0)
+    for k in range(1, d + 1):
+        m = np_ >> (k - 1)
+        h = m // 2
+        L = np.zeros((np_, np_))
+        for j in range(np_ // m):
+            b = j * m
+            for i in range(h):
+                r, s_ = diag_levels[k - 1, b + i], diag_levels[k - 1, b + h + i]
+                L[b + i, b + i] = r * c
+                L[b + i, b + h + i] = s_ * c
+                L[b + h + i, b + i] = r * c
+                L[b + h + i, b + h + i] = -s_ * c
+        W = L @ W
+    return W
+
+
+def rbt_inv(A: np.ndarray, leaf: int, u: np.ndarray, depth: int = 2):
+    """A^-1 = V (U^T pad(A) V)^-1 U^T, cropped to n x n, the middle inverse by
+    Algorithm 1 (:func:`strassen_inv`).  ``u``: 2 * depth * np uniforms in
+    [0, 1) (U's levels, then V's).  Returns (X, status, U, V)."""
+    A = _f64(A)
+    n = A.shape[0]
+    np_ = rbt_padded_order(n, depth)
+    diag = np.exp((np.asarray(u, dtype=np.float64).reshape(2, depth, np_) - 0.5) / 10.0)
+    U = rbt_butterfly(diag[0])
+    V = rbt_butterfly(diag[1])
+    Ap = np.eye(np_)
+    Ap[:n, :n] = A
+    Ar = U.T @ Ap @ V
+    Y, st = strassen_inv(Ar, leaf)
+    X = V @ Y @ U.T
+    return X[:n, :n].copy(), st, U, V
 
 
 def split(n: int) -> int:

@@ -15,6 +15,7 @@ from .binding import (  # noqa: F401
     Info,
     Opts,
     default_leaf,
+    rbt_diagonals,
     autotune_leaf,
     gemm_f64,
     gemm_bf16x3,

@@ -38,6 +38,9 @@ class Opts(ctypes.Structure):
         ("residual_slices", ctypes.c_int32),
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
+        ("pretransform", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("rbt_seed", ctypes.c_uint64),
     ]
 
 
@@ -48,10 +51,12 @@ class Info(ctypes.Structure):
         ("fail_leaf", ctypes.c_int64),
         ("fail_col", ctypes.c_int64),
         ("rel_residual", ctypes.c_double),
+        ("pretransformed", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class ProfRecord(ctypes.Structure):
@@ -140,6 +145,8 @@ def lib():
         L.spin_sync.argtypes = [vp, ctypes.POINTER(Info)]
         L.spin_sync.restype = ctypes.c_int
         L.spin_workspace_bytes.argtypes = [i64, ctypes.POINTER(Opts)]
+        L.spin_rbt_diagonals.argtypes = [ctypes.c_uint64, i64, ctypes.c_int, vp, vp]
+        L.spin_rbt_diagonals.restype = ctypes.c_int
         L.spin_workspace_bytes.restype = ctypes.c_size_t
         L.spin_default_leaf.argtypes = [i64, ctypes.c_int]
         L.spin_default_leaf.restype = ctypes.c_int
@@ -219,7 +226,7 @@ def _check_matrix(t, name):
 
 
 def make_opts(precision="fp64", leaf=0, tol=1e-10, max_refine=6, fp64_levels=2, blocking=True,
-              workspace=None, residual_slices=0) -> Opts:
+              workspace=None, residual_slices=0, pretransform=0, rbt_seed=0) -> Opts:
     o = lib().spin_opts_default()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.leaf = int(leaf)
@@ -228,6 +235,8 @@ def make_opts(precision="fp64", leaf=0, tol=1e-10, max_refine=6, fp64_levels=2, 
     o.fp64_levels = int(fp64_levels)
     o.blocking = 1 if blocking else 0
     o.residual_slices = int(residual_slices)
+    o.pretransform = int(pretransform)
+    o.rbt_seed = int(rbt_seed) & 0xFFFFFFFFFFFFFFFF
     if workspace is not None:
         o.workspace = ctypes.c_void_p(workspace.data_ptr())
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -236,7 +245,7 @@ def make_opts(precision="fp64", leaf=0, tol=1e-10, max_refine=6, fp64_levels=2, 
 
 def invert(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e-10, max_refine: int = 6,
            fp64_levels: int = 2, stream=None, check: bool = True, workspace=None, blocking: bool = True,
-           residual_slices: int = 0):
+           residual_slices: int = 0, pretransform: int = 0, rbt_seed: int = 0):
     """X = A^-1 on the device (spin_invert_ex).  Returns (X, info dict).
 
     With ``blocking=False`` the call only enqueues the work on the stream and
@@ -251,7 +260,8 @@ def invert(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e-10, 
         raise ValueError("A must be square")
     X = out if out is not None else torch.empty((n, n), dtype=torch.float64, device=A.device)
     _check_matrix(X, "X")
-    o = make_opts(precision, leaf, tol, max_refine, fp64_levels, blocking, workspace, residual_slices)
+    o = make_opts(precision, leaf, tol, max_refine, fp64_levels, blocking, workspace, residual_slices,
+                  pretransform, rbt_seed)
     if not blocking:
         rc = lib().spin_invert_ex(ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(X.data_ptr()),
                                   X.stride(0), n, ctypes.byref(o), None, _stream(stream))
@@ -276,7 +286,8 @@ def sync(stream=None, check: bool = True) -> dict:
     return info.as_dict()
 
 
-def invert_host(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e-10, stream=None):
+def invert_host(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e-10, stream=None,
+                pretransform: int = 0, rbt_seed: int = 0):
     """X = A^-1 with host (numpy or CPU torch, float64, C-contiguous) buffers."""
     import numpy as np
 
@@ -286,7 +297,7 @@ def invert_host(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e
         out = np.empty((n, n), dtype=np.float64)
     pa = A.ctypes.data if isinstance(A, np.ndarray) else A.data_ptr()
     px = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
-    o = make_opts(precision, leaf, tol)
+    o = make_opts(precision, leaf, tol, pretransform=pretransform, rbt_seed=rbt_seed)
     info = Info()
     rc = lib().spin_invert_host(ctypes.c_void_p(pa), n, ctypes.c_void_p(px), n, n, ctypes.byref(o),
                                 ctypes.byref(info), _stream(stream))
@@ -296,9 +307,25 @@ def invert_host(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e
 
 
 def workspace_bytes(n: int, *, leaf: int = 0, precision="fp64", fp64_levels: int = 2,
-                    residual_slices: int = 0) -> int:
-    o = make_opts(precision, leaf, fp64_levels=fp64_levels, residual_slices=residual_slices)
+                    residual_slices: int = 0, pretransform: int = 0) -> int:
+    o = make_opts(precision, leaf, fp64_levels=fp64_levels, residual_slices=residual_slices,
+                  pretransform=pretransform)
     return int(lib().spin_workspace_bytes(int(n), ctypes.byref(o)))
+
+
+def rbt_diagonals(seed: int, n: int, depth: int = 2, stream=None):
+    """The butterfly transform's random diagonals for order n
+    (spin_rbt_diagonals): a float64 CUDA tensor of 2 * depth * np entries."""
+    import torch
+
+    q = 2 ** depth
+    np_ = -(-int(n) // q) * q
+    out = torch.empty(2 * depth * np_, dtype=torch.float64, device="cuda")
+    rc = lib().spin_rbt_diagonals(ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), int(n), int(depth),
+                                  ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_rbt_diagonals")
+    return out
 
 
 def default_leaf(n: int, precision="fp64") -> int:

@@ -97,6 +97,7 @@ struct StreamState {
     int last_refine_iters = 0;     // host: result of the latest mixed-precision call
     double last_rel = -1.0;
     int last_host_status = 0;      // host-detected status (e.g. not converged)
+    int last_pretransformed = 0;   // host: the latest call went through the butterfly transform
 };
 
 std::mutex g_mu;
@@ -297,6 +298,8 @@ int read_info(StreamState* st, cudaStream_t s, spin_info* info) {
         info->fail_leaf = h[INFO_STATUS] ? h[INFO_LEAF] : -1;
         info->fail_col = h[INFO_STATUS] ? h[INFO_COL] : -1;
         info->rel_residual = st->last_rel;
+        info->pretransformed = st->last_pretransformed;
+        info->reserved = 0;
     }
     return status;
 }
@@ -337,9 +340,33 @@ MixLayout mix_layout(int64_t n, int64_t leaf, const spin_opts& o) {
     return L;
 }
 
-size_t workspace_bytes_for(int64_t n, int64_t leaf, const spin_opts& o) {
+size_t inner_bytes(int64_t n, int64_t leaf, const spin_opts& o) {
     if (o.precision == SPIN_FP64) return ws_fp64_elems(n, leaf) * sizeof(double);
     return mix_layout(n, leaf, o).total;
+}
+
+// Butterfly transform: [diagonals | Ar (np x np) | Y (np x np) | the
+// workspace of the recursion on order np (mixed: also the refinement's)].
+struct RbtLayout {
+    int64_t np;
+    size_t off_ar, off_y, off_inner, total;
+};
+
+RbtLayout rbt_layout(int64_t n, int64_t leaf, const spin_opts& o) {
+    RbtLayout R;
+    R.np = rbt_padded_order(n, kRbtDepth);
+    const size_t nn = (size_t)R.np * (size_t)R.np * sizeof(double);
+    R.off_ar = round256(2 * (size_t)kRbtDepth * (size_t)R.np * sizeof(double));
+    R.off_y = R.off_ar + round256(nn);
+    R.off_inner = R.off_y + round256(nn);
+    R.total = R.off_inner + inner_bytes(R.np, leaf, o);
+    return R;
+}
+
+size_t workspace_bytes_for(int64_t n, int64_t leaf, const spin_opts& o) {
+    if (o.pretransform == 1) return rbt_layout(n, leaf, o).total;
+    if (o.pretransform == 2) return std::max(inner_bytes(n, leaf, o), rbt_layout(n, leaf, o).total);
+    return inner_bytes(n, leaf, o);
 }
 
 // Newton-Schulz refinement X <- X + X (I - A X) (Bailey-style stabilisation
@@ -410,6 +437,64 @@ int refine(Run& r, StreamState* st, const double* A, int64_t lda, double* X, int
     }
 }
 
+// One attempt: the recursion on A (pretransform 0) or on U^T A V with the
+// transform undone afterwards (pretransform 1); mixed modes then refine
+// X against A itself.
+int enqueue_once(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, int64_t leaf, const spin_opts& o,
+                 bool rbt, StreamState* st, cudaStream_t s, unsigned char* ws) {
+    const bool mixed = o.precision != SPIN_FP64;
+    st->last_host_status = 0;
+    st->last_refine_iters = 0;
+    st->last_rel = -1.0;
+    st->last_pretransformed = rbt ? 1 : 0;
+    SPIN_CUDA_TRY(cudaMemsetAsync(st->info_dev, 0, INFO_WORDS * sizeof(int32_t), s));
+    Run r{s, st->info_dev, 0, leaf, st->prof.on ? &st->prof : nullptr};
+    // what the recursion inverts, where it writes, and its workspace
+    const double* Ain = A;
+    int64_t lda_in = lda, n_in = n;
+    double* Xout = X;
+    int64_t ldx_out = ldx;
+    unsigned char* inner = ws;
+    RbtLayout R{};
+    if (rbt) {
+        R = rbt_layout(n, leaf, o);
+        double* diag = (double*)ws;
+        double* Ar = (double*)(ws + R.off_ar);
+        RET(launch_rbt_diagonals(o.rbt_seed, R.np, kRbtDepth, diag, s));
+        RET(launch_rbt_forward(A, lda, n, Ar, R.np, kRbtDepth, diag, s));
+        Ain = Ar;
+        lda_in = n_in = R.np;
+        Xout = (double*)(ws + R.off_y);
+        ldx_out = R.np;
+        inner = ws + R.off_inner;
+    }
+    if (!mixed) {
+        RET(inv_rec(r, 0, Ain, lda_in, Xout, ldx_out, n_in, (double*)inner));
+        if (rbt) RET(launch_rbt_backward(Xout, R.np, kRbtDepth, (const double*)ws, X, ldx, n, s));
+        return SPIN_OK;
+    }
+    const MixLayout Lin = mix_layout(n_in, leaf, o);
+    r.precision = o.precision;
+    r.fp64_levels = o.fp64_levels;
+    r.scratch = inner + Lin.off_scratch;
+    r.scratch_bytes = Lin.scratch;
+    r.err = st->err_dev;
+    SPIN_CUDA_TRY(cudaMemsetAsync(st->err_dev, 0, sizeof(int), s));
+    RET(inv_rec(r, 0, Ain, lda_in, Xout, ldx_out, n_in, (double*)inner));
+    if (rbt) RET(launch_rbt_backward(Xout, R.np, kRbtDepth, (const double*)ws, X, ldx, n, s));
+    // a singular leaf makes the refinement meaningless: stop here
+    SPIN_CUDA_TRY(cudaMemcpyAsync(st->info_host, st->info_dev, INFO_WORDS * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, s));
+    SPIN_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st->info_host[INFO_STATUS] != 0) return SPIN_OK;
+    // the refinement's layout for order n fits in the recursion's (order >= n)
+    RET(refine(r, st, A, lda, X, ldx, n, o, mix_layout(n, leaf, o), inner));
+    int err = 0;
+    SPIN_CUDA_TRY(cudaMemcpy(&err, st->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) st->last_host_status = err;
+    return SPIN_OK;
+}
+
 int enqueue(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, const spin_opts& o,
             StreamState* st, cudaStream_t s) {
     const int64_t leaf = resolve_leaf(n, o.leaf, o.precision);
@@ -418,6 +503,7 @@ int enqueue(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, con
     const bool mixed = o.precision != SPIN_FP64;
     if (mixed && (o.residual_slices < 0 || o.residual_slices > 7 || o.max_refine < 0 || !(o.tol > 0.0)))
         return SPIN_ERR_INVALID_ARG;
+    if (o.pretransform < 0 || o.pretransform > 2) return SPIN_ERR_INVALID_ARG;
     const size_t need = workspace_bytes_for(n, leaf, o);
     unsigned char* ws;
     if (o.workspace != nullptr) {
@@ -427,31 +513,15 @@ int enqueue(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, con
         RET(ensure_ws(st, need));
         ws = (unsigned char*)st->ws;
     }
-    st->last_host_status = 0;
-    st->last_refine_iters = 0;
-    st->last_rel = -1.0;
-    SPIN_CUDA_TRY(cudaMemsetAsync(st->info_dev, 0, INFO_WORDS * sizeof(int32_t), s));
-    Run r{s, st->info_dev, 0, leaf, st->prof.on ? &st->prof : nullptr};
-    if (!mixed) return inv_rec(r, 0, A, lda, X, ldx, n, (double*)ws);
-
-    const MixLayout L = mix_layout(n, leaf, o);
-    r.precision = o.precision;
-    r.fp64_levels = o.fp64_levels;
-    r.scratch = ws + L.off_scratch;
-    r.scratch_bytes = L.scratch;
-    r.err = st->err_dev;
-    SPIN_CUDA_TRY(cudaMemsetAsync(st->err_dev, 0, sizeof(int), s));
-    RET(inv_rec(r, 0, A, lda, X, ldx, n, (double*)ws));
-    // a singular leaf makes the refinement meaningless: stop here
+    if (o.pretransform != 2) return enqueue_once(A, lda, X, ldx, n, leaf, o, o.pretransform == 1, st, s, ws);
+    // plain first; a zero or non-finite pivot (A11 or a Schur complement
+    // singular in working precision) sends the call through the transform
+    RET(enqueue_once(A, lda, X, ldx, n, leaf, o, false, st, s, ws));
     SPIN_CUDA_TRY(cudaMemcpyAsync(st->info_host, st->info_dev, INFO_WORDS * sizeof(int32_t),
                                   cudaMemcpyDeviceToHost, s));
     SPIN_CUDA_TRY(cudaStreamSynchronize(s));
-    if (st->info_host[INFO_STATUS] != 0) return SPIN_OK;
-    RET(refine(r, st, A, lda, X, ldx, n, o, L, ws));
-    int err = 0;
-    SPIN_CUDA_TRY(cudaMemcpy(&err, st->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) st->last_host_status = err;
-    return SPIN_OK;
+    if (st->info_host[INFO_STATUS] != SPIN_ERR_SINGULAR) return SPIN_OK;
+    return enqueue_once(A, lda, X, ldx, n, leaf, o, true, st, s, ws);
 }
 
 // ---- leaf autotuning ----

@@ -605,6 +605,7 @@ extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, d
     if (count < 1 || A == nullptr || lda == nullptr || X == nullptr || n == nullptr) return SPIN_ERR_INVALID_ARG;
     spin_opts o = opts ? *opts : spin_opts_default();
     if (o.precision != SPIN_FP64 && o.precision != SPIN_MIXED_BF16X3) return SPIN_ERR_NOT_IMPLEMENTED;
+    if (o.pretransform != 0) return SPIN_ERR_NOT_IMPLEMENTED;  // the batch has no butterfly transform
     const bool mixed = o.precision != SPIN_FP64;
     if (o.leaf < 0) return SPIN_ERR_INVALID_ARG;
     if (mixed && (o.residual_slices < 0 || o.residual_slices > 7 || o.max_refine < 0 || !(o.tol > 0.0) ||

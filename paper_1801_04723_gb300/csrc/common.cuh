@@ -62,6 +62,17 @@ int launch_leaf_gj_batched(const BatchView& src, const BatchView& dst, int64_t L
 int launch_leaf_gj(const double* A, int64_t lda, double* X, int64_t ldx, int64_t L, double* scratch,
                    int32_t* info, int leaf_index, cudaStream_t s);
 size_t leaf_scratch_elems(int64_t L);
+
+// Random butterfly transform (rbt.cu): depth, padded order (a multiple of
+// 2^depth), diagonals (2 * depth * np doubles: U's levels, then V's),
+// Ar = U^T pad(A) V, and X = crop(V Y U^T) (Y overwritten).
+constexpr int kRbtDepth = 2;
+int64_t rbt_padded_order(int64_t n, int depth);
+int launch_rbt_diagonals(uint64_t seed, int64_t np, int depth, double* out, cudaStream_t s);
+int launch_rbt_forward(const double* A, int64_t lda, int64_t n, double* Ar, int64_t np, int depth,
+                       const double* diag, cudaStream_t s);
+int launch_rbt_backward(double* Y, int64_t np, int depth, const double* diag, double* X, int64_t ldx, int64_t n,
+                        cudaStream_t s);
 constexpr int64_t kMaxLeaf = 4096;
 
 // FP64 recursion over caller-supplied workspace and info record (api.cu).

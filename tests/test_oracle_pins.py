@@ -325,3 +325,63 @@ def test_generators_deterministic():
     # splitmix64 reference outputs for seed 0 (Vigna's splitmix64.c, first three draws)
     z = inputs.splitmix64(0, np.arange(3, dtype=np.uint64))
     assert [int(x) for x in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+# ------------------------------------------------- random butterfly transform --
+
+def _u(seed, n, depth=2):
+    np_ = oracle.rbt_padded_order(n, depth)
+    return inputs.uniform01(seed, np.arange(2 * depth * np_, dtype=np.uint64))
+
+
+def test_rbt_order2_closed_form():
+    # one butterfly of order 2: [[r, s], [r, -s]] / sqrt(2)
+    r, s = 1.03, 0.97
+    W = oracle.rbt_butterfly(np.array([[r, s]]))
+    want = np.array([[r, s], [r, -s]]) / math.sqrt(2.0)
+    np.testing.assert_allclose(W, want, rtol=0, atol=4 * U)
+
+
+def test_rbt_determinant_is_product_of_diagonals():
+    # each block of order m has |det| = prod(r) prod(s) (the 1/sqrt(2)^m and
+    # the 2^(m/2) of [[R, S], [R, -S]] cancel); levels multiply
+    rng = np.random.default_rng(3)
+    for depth, np_ in ((1, 8), (2, 8), (3, 16), (2, 12)):
+        d = np.exp((rng.random((depth, np_)) - 0.5) / 10.0)
+        W = oracle.rbt_butterfly(d)
+        assert abs(abs(np.linalg.det(W)) - np.prod(d)) <= 1e-12 * np.prod(d)
+
+
+def test_rbt_unit_diagonals_are_orthogonal():
+    # R = S = I: every block is the orthogonal Haar butterfly, so W is orthogonal
+    W = oracle.rbt_butterfly(np.ones((2, 16)))
+    np.testing.assert_allclose(W @ W.T, np.eye(16), atol=1e-15)
+
+
+@pytest.mark.parametrize("n,leaf", [(50, 8), (64, 16), (33, 33)])
+def test_rbt_inverse_matches_lapack(n, leaf):
+    # nonsymmetric, moderately conditioned (the block recursion has no
+    # pivoting: its error grows with the conditioning of the leading blocks)
+    A = inputs.uniform(inputs.SEED_BASE + 60 + n, (n, n)) + 2.0 * math.sqrt(n) * np.eye(n)
+    X, st, U_, V_ = oracle.rbt_inv(A, leaf, _u(inputs.SEED_BASE + 70, n))
+    assert st == 0
+    ref = np.linalg.inv(A)
+    assert np.linalg.norm(X - ref) / np.linalg.norm(ref) <= 1e3 * np.linalg.cond(A) * U
+    assert oracle.residual(A, X)[0] <= 1e-13
+
+
+def test_rbt_handles_a_singular_leading_block():
+    # [[0, I], [I, 0]] blocks: A11 = 0, so Algorithm 1 fails at its first
+    # leaf; the transformed matrix's leading blocks are nonsingular
+    n = 40
+    A = np.zeros((n, n))
+    A[:20, 20:] = np.eye(20)
+    A[20:, :20] = np.eye(20)
+    A += 0.1 * inputs.uniform(inputs.SEED_BASE + 80, (n, n))
+    A[:20, :20] = 0.0
+    with pytest.raises(oracle.SingularError):
+        oracle.strassen_inv(A, 8)
+    X, st, _, _ = oracle.rbt_inv(A, 8, _u(inputs.SEED_BASE + 81, n))
+    assert st == 0
+    ref = np.linalg.inv(A)
+    assert np.linalg.norm(X - ref) / np.linalg.norm(ref) <= 1e4 * np.linalg.cond(A) * U
