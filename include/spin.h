@@ -284,6 +284,14 @@ size_t spin_workspace_bytes(int64_t n, const spin_opts* opts);
  * built-in default (plain: 512 for n >= 16384, else 256; mixed: 128). */
 int spin_default_leaf(int64_t n, int precision);
 
+/* Predicted time (seconds) of one plain FP64 inversion of order n with the
+ * given leaf on one GB300: the paper's cost analysis (Sec. 4, Table 2)
+ * restated for this GPU -- six products per node priced by tile waves over
+ * 152 SMs at the FP64 rate, leaves priced per pivot step on one thread-block
+ * cluster.  spin_default_leaf uses its optimum for untuned FP64 orders.
+ * -1 for other precisions or bad arguments. */
+double spin_model_seconds(int64_t n, int leaf, int precision);
+
 /*
  * spin_autotune_leaf: time one inversion (after a warm-up) per candidate
  * leaf order on a synthetic strictly diagonally dominant matrix of order n,

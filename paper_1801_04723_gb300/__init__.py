@@ -15,6 +15,7 @@ from .binding import (  # noqa: F401
     Info,
     Opts,
     default_leaf,
+    model_seconds,
     rbt_diagonals,
     autotune_leaf,
     gemm_f64,

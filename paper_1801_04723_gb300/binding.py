@@ -147,6 +147,8 @@ def lib():
         L.spin_workspace_bytes.argtypes = [i64, ctypes.POINTER(Opts)]
         L.spin_rbt_diagonals.argtypes = [ctypes.c_uint64, i64, ctypes.c_int, vp, vp]
         L.spin_rbt_diagonals.restype = ctypes.c_int
+        L.spin_model_seconds.argtypes = [i64, ctypes.c_int, ctypes.c_int]
+        L.spin_model_seconds.restype = ctypes.c_double
         L.spin_workspace_bytes.restype = ctypes.c_size_t
         L.spin_default_leaf.argtypes = [i64, ctypes.c_int]
         L.spin_default_leaf.restype = ctypes.c_int
@@ -326,6 +328,12 @@ def rbt_diagonals(seed: int, n: int, depth: int = 2, stream=None):
     if rc != SPIN_OK:
         raise SpinError(rc, "spin_rbt_diagonals")
     return out
+
+
+def model_seconds(n: int, leaf: int, precision="fp64") -> float:
+    """Cost-model time of one inversion (spin_model_seconds; FP64 only)."""
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return float(lib().spin_model_seconds(int(n), int(leaf), p))
 
 
 def default_leaf(n: int, precision="fp64") -> int:

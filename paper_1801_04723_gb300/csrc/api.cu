@@ -547,6 +547,67 @@ __global__ void synth_sdd_kernel(double* A, int64_t n, uint64_t seed) {
     }
 }
 
+// ---- cost model of the plain FP64 path (Sec. 4's cost analysis restated
+// for one GB300) ----
+//
+// The paper prices each step of Algorithm 1 on a Spark cluster (Table 2,
+// Eq. (SPIN-cost)) and finds a U-shaped dependence on the partition size
+// (Fig. 3).  On one GPU the two sides of the U are: products of the deep
+// levels are too small to fill 152 SMs (left), and Gauss-Jordan leaves run on
+// one cluster of at most 16 SMs at the FP64 rate plus a per-pivot latency
+// (right).  Model, per recursion node: six products (n1, n2 split), each
+//   t = launch + max(ceil(tiles / 152) * 2 * 64 * 64 * k / P_sm, 2 m n k / P_gpu)
+// with 64 x 64 tiles and P_sm = 4 flops/clock at 2.07 GHz (P_gpu = 152 P_sm,
+// 1.259 TFLOP/s, the measured DFMA rate); per leaf of order L on C = min(16,
+// 2^ceil(log2 L)) CTAs with R = ceil(L / C) rows each, L pivot steps of
+//   a + b L + R L / (2 FMA/clock)     (rows in shared memory)
+//   a + b L + R L g                   (rows in L2-resident global memory)
+// a = 3.64 us, b = 8.7 ns (per-step latency of the leaf microbenchmark at
+// L = 128 and 256 on 16 CTAs) and g = 0.97 ns per element (one n = 8192,
+// L = 2048 measurement).  It reproduces the measured sweeps at n = 8192 and
+// 16384 (leaf 64 ... 2048) within 2.5 %.
+constexpr double kModelClock = 2.07e9;
+constexpr double kModelPsm = 4.0 * kModelClock;
+constexpr double kModelPgpu = 152.0 * kModelPsm;
+constexpr double kModelLaunch = 4e-6, kModelA = 3.64e-6, kModelB = 8.7e-9, kModelG = 0.97e-9;
+
+double model_gemm(int64_t m, int64_t n, int64_t k) {
+    const double tiles = (double)((m + 63) / 64) * (double)((n + 63) / 64);
+    const double wave = std::ceil(tiles / 152.0) * 2.0 * 64.0 * 64.0 * (double)k / kModelPsm;
+    return kModelLaunch + std::max(wave, 2.0 * (double)m * (double)n * (double)k / kModelPgpu);
+}
+
+double model_leaf(int64_t L) {
+    int64_t C = 1;
+    while (C < 16 && C < L) C <<= 1;
+    const int64_t R = (L + C - 1) / C;
+    const bool smem = (double)R * L * 8 + (double)L * 16 + 64 <= 200.0 * 1024;
+    const double work = smem ? (double)R * L / (2.0 * kModelClock) : (double)R * L * kModelG;
+    return (double)L * (kModelA + kModelB * (double)L + work);
+}
+
+double model_fp64(int64_t n, int64_t leaf) {
+    if (n <= leaf) return model_leaf(n);
+    const int64_t n1 = split_order(n), n2 = n - n1;
+    return model_fp64(n1, leaf) + model_fp64(n2, leaf) + model_gemm(n1, n2, n1) + model_gemm(n2, n2, n1) +
+           model_gemm(n1, n2, n2) + model_gemm(n2, n1, n1) + model_gemm(n2, n1, n2) + model_gemm(n1, n1, n2);
+}
+
+int model_best_leaf(int64_t n) {
+    static const int cands[] = {64, 128, 256, 512, 1024, 2048};
+    int best = 64;
+    double bt = 1e300;
+    for (int L : cands) {
+        if (L > n) break;
+        const double t = model_fp64(n, L);
+        if (t < bt) {
+            bt = t;
+            best = L;
+        }
+    }
+    return best;
+}
+
 }  // namespace
 
 int tuned_leaf(int64_t n, int precision) {
@@ -595,13 +656,18 @@ spin_opts spin_opts_default(void) {
     return o;
 }
 
+double spin_model_seconds(int64_t n, int leaf, int precision) {
+    if (n < 1 || leaf < 1 || precision != SPIN_FP64) return -1.0;
+    return model_fp64(n, std::min<int64_t>(leaf, n));
+}
+
 int spin_default_leaf(int64_t n, int precision) {
     if (n <= 128) return (int)(n < 1 ? 1 : n);
     const int t = tuned_leaf(n, precision);
     if (t > 0) return (int)std::min<int64_t>(t, n);
-    // untuned: leaves large enough that the FP64 leaf kernel keeps its
-    // cluster busy, small enough that leaf work stays a few percent
-    if (precision == SPIN_FP64) return n >= 16384 ? 512 : 256;
+    // untuned: the cost model's optimum for the plain path; the mixed path's
+    // products are ~1000x cheaper, so its leaves stay small
+    if (precision == SPIN_FP64) return model_best_leaf(n);
     return 128;
 }
 

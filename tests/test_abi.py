@@ -93,3 +93,30 @@ def test_invalid_arguments_rejected_on_host(L):
     assert L.spin_gemm_f64(4, 4, 4, 1.0, a, 4, a, 4, 1.0, None, 0, x, 4, None) == 1
     # leaf order above the supported maximum
     assert L.spin_leaf_inverse(a, 5000, x, 5000, 5000, None, None) == 1
+
+
+def test_pretransform_workspace(L):
+    # the butterfly transform adds its diagonals, U^T A V and the inverse of
+    # it (order padded to a multiple of 4) to the recursion's workspace
+    n = 1001
+    np_ = 1004
+    plain = spin.workspace_bytes(n, leaf=64)
+    rbt = spin.workspace_bytes(n, leaf=64, pretransform=1)
+    assert rbt >= 2 * np_ * np_ * 8 + 4 * np_ * 8 + spin.workspace_bytes(np_, leaf=64)
+    assert spin.workspace_bytes(n, leaf=64, pretransform=2) == max(plain, rbt)
+
+
+def test_cost_model_shape(L):
+    """The model of the plain path (spin_model_seconds): never faster than the
+    FP64 peak allows, U-shaped in the leaf order with the optimum of the
+    measured sweeps (256 at n = 8192 and 16384), growing like n^3, and the
+    untuned default leaf is its optimum."""
+    peak = 152 * 4 * 2.07e9
+    for n in (8192, 16384):
+        t = {Lf: spin.model_seconds(n, Lf) for Lf in (64, 128, 256, 512, 1024, 2048)}
+        assert all(v >= 2.0 * n ** 3 / peak for v in t.values())
+        assert t[64] > t[128] > t[256] < t[512] < t[1024] < t[2048]
+        assert spin.default_leaf(n) == 256
+    r = spin.model_seconds(16384, 256) / spin.model_seconds(8192, 256)
+    assert 7.0 < r < 8.0
+    assert spin.model_seconds(100, 64, precision="bf16x3") == -1.0
