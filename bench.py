@@ -449,6 +449,23 @@ class BatchWork:
         return {"rel_residual_est": worst, "rel_residual_note": "max over 16 sampled matrices, 4 probes each"}
 
 
+def replica_rate(ms_local: float, flops_local: float, world: int, device):
+    """Replicas (one matrix per rank, no collective on the data path): the
+    job's time is the slowest rank's, its work the sum over ranks.  Returns
+    (ms, TFLOP/s of the whole job)."""
+    if world <= 1:
+        return ms_local, flops_local / (ms_local * 1e-3) / 1e12
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    f = torch.tensor([flops_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    return ms, float(f.item()) / (ms * 1e-3) / 1e12
+
+
 def run_ours(args, w: dict, n: int, leaf: int):
     import torch
 
@@ -503,14 +520,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
         barrier()
         recs = spin.profile_collect()
         info = work.finish()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * flops / (ms * 1e-3) / 1e12
+    ms, value = replica_rate(e0.elapsed_time(e1) / args.steps, flops, world, device)
     acc = work.accuracy(args.probes)
     if rank != 0:
         if world > 1:
