@@ -60,6 +60,9 @@ constexpr int GROUP_M = 8;  // row blocks per rasterisation band
 #define SPIN_EXACT_BN 128
 #define SPIN_EXACT_EPI_WARPS 8
 #endif
+#ifndef SPIN_EXACT_WIDE_MIN_TILES
+#define SPIN_EXACT_WIDE_MIN_TILES 608  // 4 waves of 152 SMs
+#endif
 #ifndef SPIN_FLOAT_BN
 #define SPIN_FLOAT_BN 256
 #endif
@@ -70,8 +73,18 @@ constexpr int GROUP_M = 8;  // row blocks per rasterisation band
 #define SPIN_KSUB_FLOAT 1
 #endif
 constexpr int kFloatBN = SPIN_FLOAT_BN;             // float-mode tile width
-constexpr int kExactBN = SPIN_EXACT_BN;             // exact-mode tile width
-constexpr int kExactEpiWarps = SPIN_EXACT_EPI_WARPS;  // exact-mode epilogue warps
+constexpr int kExactBN = SPIN_EXACT_BN;             // exact-mode tile width (small products)
+constexpr int kExactEpiWarps = SPIN_EXACT_EPI_WARPS;  // exact-mode epilogue warps (small products)
+// Large exact products use 128 x 256 tiles: an MMA of N = 256 per SM keeps
+// the tensor pipe busier than N = 128 (1254 vs 1136 TFLOP/s at n = 8192);
+// TMEM then holds only the two accumulators, the running FP64 sums go to D,
+// and 16 epilogue warps hold the int32 run sums (64 columns each).  Below a
+// few waves of tiles the narrower tiles win (more CTAs, no D traffic), and
+// so they do for long K (the n = 32768 residual: ~10 read-modify-write
+// passes over D per tile, and the wider tiles lower the clock under the
+// power cap without raising the work per clock).
+constexpr int64_t kExactWideMinTiles = SPIN_EXACT_WIDE_MIN_TILES;
+constexpr int kExactWideMaxK = 16384;
 constexpr uint32_t A_TILE_BYTES = BM * BK * 2;  // 16 KB
 // 64-wide k-blocks per pipeline stage.  The MMA issuer's fixed cost per
 // stage (barrier wait, commit) is spread over 4 * KSUB MMAs: two k-blocks
@@ -165,7 +178,7 @@ struct Epi {
 // accumulators belong to a CTA pair whose MMA issuer waits on the even
 // CTA's tempty barriers (cluster addresses tempty_c0 / tempty_c1); the
 // tfull barriers are this CTA's own (the issuer multicasts its commits).
-template <int BN, int HALF, bool PAIR>
+template <int BN, int HALF, bool PAIR, bool TMEM_SUMS = true, int DRAIN = 32>
 __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl* ctl, volatile int* abort,
                                                  uint32_t lane_addr, int half, int grow, int col0,
                                                  int nchunks_per_pair, int lane, uint32_t tempty_c0,
@@ -198,17 +211,17 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
             }
             tc_fence_after();
             {
-                // 32 columns per wait: two loads in flight, 32 registers
+                // DRAIN columns per wait (x16 loads in flight), DRAIN registers
 #pragma unroll
-                for (int c0 = 0; c0 < HALF; c0 += 32) {
-                    uint32_t v[32];
-                    tmem_ld_32x32b_x16(lane_addr + (uint32_t)(buf * BN + half * HALF + c0),
-                                       *reinterpret_cast<uint32_t(*)[16]>(&v[0]));
-                    tmem_ld_32x32b_x16(lane_addr + (uint32_t)(buf * BN + half * HALF + c0 + 16),
-                                       *reinterpret_cast<uint32_t(*)[16]>(&v[16]));
+                for (int c0 = 0; c0 < HALF; c0 += DRAIN) {
+                    uint32_t v[DRAIN];
+#pragma unroll
+                    for (int c1 = 0; c1 < DRAIN; c1 += 16)
+                        tmem_ld_32x32b_x16(lane_addr + (uint32_t)(buf * BN + half * HALF + c0 + c1),
+                                           *reinterpret_cast<uint32_t(*)[16]>(&v[c1]));
                     tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; j++) acc[c0 + j] += __float2int_rn(__uint_as_float(v[j]));
+                    for (int j = 0; j < DRAIN; j++) acc[c0 + j] += __float2int_rn(__uint_as_float(v[j]));
                 }
             }
             tc_fence_before();
@@ -233,40 +246,64 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
                 double* drow = out_row(p, z, grow);
                 const double* crow = in_row(p, z, grow);
                 const uint32_t sum_addr = lane_addr + (uint32_t)(2 * BN + half * 2 * HALF);
+                if constexpr (!TMEM_SUMS) {
+                    // 256-wide tiles fill TMEM with the two accumulators: the
+                    // running sums live in D itself (read-modify-write)
 #pragma unroll
-                for (int jj = 0; jj < HALF; jj += 8) {
-                    uint32_t w[16];  // 8 FP64 running sums as (lo, hi) words
-                    if (!first_flush) {
-                        tmem_ld_32x32b_x16(sum_addr + (uint32_t)(2 * jj), w);
-                        tmem_ld_wait();
-                    }
-#pragma unroll
-                    for (int j = 0; j < 8; j++) {
-                        const int gcol = col0 + jj + j;
+                    for (int j = 0; j < HALF; j++) {
+                        const int gcol = col0 + j;
                         const bool ok_ij = row_ok && gcol < p.N;
-                        const int ec = (col_exp && ok_ij) ? col_exp[gcol] : 0;
-                        double val = scaled_int(alpha_sign * acc[jj + j], er + ec);
-                        if (alpha_general) val *= p.alpha;
-                        if (first_flush) {
-                            if (p.beta != 0.0 && ok_ij) val = fma(p.beta, crow[gcol], val);
-                            if (p.add_identity && gcol == grow) val += 1.0;
-                        } else {
-                            val += __hiloint2double((int)w[2 * j + 1], (int)w[2 * j]);
-                        }
-                        if (last) {
-                            if (ok_ij) {
-                                drow[gcol] = val;
-                                sumsq = fma(val, val, sumsq);
+                        if (ok_ij) {
+                            const int ec = col_exp ? col_exp[gcol] : 0;
+                            double val = scaled_int(alpha_sign * acc[j], er + ec);
+                            if (alpha_general) val *= p.alpha;
+                            if (first_flush) {
+                                if (p.beta != 0.0) val = fma(p.beta, crow[gcol], val);
+                                if (p.add_identity && gcol == grow) val += 1.0;
+                            } else {
+                                val += drow[gcol];
                             }
-                        } else {
-                            w[2 * j] = (uint32_t)__double2loint(val);
-                            w[2 * j + 1] = (uint32_t)__double2hiint(val);
+                            drow[gcol] = val;
+                            if (last) sumsq = fma(val, val, sumsq);
                         }
-                        acc[jj + j] = 0;
+                        acc[j] = 0;
                     }
-                    if (!last) tmem_st_32x32b_x16(sum_addr + (uint32_t)(2 * jj), w);
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < HALF; jj += 8) {
+                        uint32_t w[16];  // 8 FP64 running sums as (lo, hi) words
+                        if (!first_flush) {
+                            tmem_ld_32x32b_x16(sum_addr + (uint32_t)(2 * jj), w);
+                            tmem_ld_wait();
+                        }
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            const int gcol = col0 + jj + j;
+                            const bool ok_ij = row_ok && gcol < p.N;
+                            const int ec = (col_exp && ok_ij) ? col_exp[gcol] : 0;
+                            double val = scaled_int(alpha_sign * acc[jj + j], er + ec);
+                            if (alpha_general) val *= p.alpha;
+                            if (first_flush) {
+                                if (p.beta != 0.0 && ok_ij) val = fma(p.beta, crow[gcol], val);
+                                if (p.add_identity && gcol == grow) val += 1.0;
+                            } else {
+                                val += __hiloint2double((int)w[2 * j + 1], (int)w[2 * j]);
+                            }
+                            if (last) {
+                                if (ok_ij) {
+                                    drow[gcol] = val;
+                                    sumsq = fma(val, val, sumsq);
+                                }
+                            } else {
+                                w[2 * j] = (uint32_t)__double2loint(val);
+                                w[2 * j + 1] = (uint32_t)__double2hiint(val);
+                            }
+                            acc[jj + j] = 0;
+                        }
+                        if (!last) tmem_st_32x32b_x16(sum_addr + (uint32_t)(2 * jj), w);
+                    }
+                    if (!last) tmem_st_wait();
                 }
-                if (!last) tmem_st_wait();
                 first_flush = false;
                 since_flush = 0;
             }
@@ -279,16 +316,20 @@ template <int BN, bool EXACT, int EPI_WARPS>
 __global__ void __maxnreg__(Epi<EPI_WARPS>::MAXREG)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const TcGemmParams p) {
-    constexpr int KS = EXACT ? KSUB_EXACT : KSUB_FLOAT;  // k-blocks per stage
+    // k-blocks per stage (256-wide exact tiles: one, for a 4-stage ring)
+    constexpr int KS = EXACT ? (BN >= 256 ? 1 : KSUB_EXACT) : KSUB_FLOAT;
+    // exact mode keeps the FP64 running sums in TMEM when they fit beside the
+    // two accumulators (128-wide tiles), else in D
+    constexpr bool TMEM_SUMS = !EXACT || 4 * BN <= 512;
     using C = Cfg<BN, KS>;
     constexpr int STAGES = C::STAGES;
     constexpr uint32_t B_TILE_BYTES = C::B_TILE_BYTES;
     constexpr uint32_t STAGE_BYTES = C::STAGE_BYTES;
-    // exact mode: two FP32 accumulators + the FP64 running sums (2 columns each)
-    constexpr uint32_t TMEM_COLS = EXACT ? 4 * BN : C::TMEM_COLS;
+    // exact mode: two FP32 accumulators (+ the FP64 running sums, 2 columns each)
+    constexpr uint32_t TMEM_COLS = EXACT ? (TMEM_SUMS ? 4 * BN : 2 * BN) : C::TMEM_COLS;
     static_assert(TMEM_COLS <= 512, "TMEM");
     constexpr int HALF = BN / (EPI_WARPS / 4);  // columns per epilogue warp
-    static_assert(EPI_WARPS % 4 == 0 && BN % (EPI_WARPS / 4) == 0 && HALF % 32 == 0, "epilogue split");
+    static_assert(EPI_WARPS % 4 == 0 && BN % (EPI_WARPS / 4) == 0 && HALF % 16 == 0, "epilogue split");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* smA = base;                              // [stage][sub] A tiles
@@ -485,8 +526,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->tempty[0]);
         } else {
-            sumsq = exact_epilogue<BN, HALF, false>(p, ctl, abort, lane_addr, half, grow, col0, nchunks_per_pair,
-                                                    lane, 0u, 0u, z);
+            sumsq = exact_epilogue<BN, HALF, false, TMEM_SUMS, (EPI_WARPS >= 16 ? 16 : 32)>(
+                p, ctl, abort, lane_addr, half, grow, col0, nchunks_per_pair, lane, 0u, 0u, z);
         }
         if (p.sumsq) {
 #pragma unroll
@@ -1027,13 +1068,13 @@ int launch_impl(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, c
     static bool attr = false;
     auto kern = tc_gemm_kernel<BN, EXACT, EPI_WARPS>;
     if (!attr) {
-        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<BN, EXACT ? KSUB_EXACT : KSUB_FLOAT>::SMEM_BYTES));
+        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<BN, EXACT ? (BN >= 256 ? 1 : KSUB_EXACT) : KSUB_FLOAT>::SMEM_BYTES));
         attr = true;
     }
     const int64_t tiles = (int64_t)((p.N + BN - 1) / BN) * ((p.M + BM - 1) / BM);
     if (tiles > INT32_MAX) return SPIN_ERR_INVALID_ARG;
     kern<<<dim3((unsigned)tiles, (unsigned)nz), Epi<EPI_WARPS>::THREADS,
-           Cfg<BN, EXACT ? KSUB_EXACT : KSUB_FLOAT>::SMEM_BYTES, s>>>(ta, tb, p);
+           Cfg<BN, EXACT ? (BN >= 256 ? 1 : KSUB_EXACT) : KSUB_FLOAT>::SMEM_BYTES, s>>>(ta, tb, p);
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
 }
@@ -1069,6 +1110,15 @@ bool use_pair_kernel() {
     return v != 0;
 }
 
+// Large exact products use the 256-wide tiles unless SPIN_TC_WIDE=0.
+bool use_wide_exact() {
+    static const int v = [] {
+        const char* e = getenv("SPIN_TC_WIDE");
+        return (e && e[0] == '0') ? 0 : 1;
+    }();
+    return v != 0;
+}
+
 }  // namespace
 
 int64_t tc_ld(int64_t k) { return (k + 7) / 8 * 8; }
@@ -1086,8 +1136,13 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& p
     p.b_rows = b.rows;
     p.a_zrows = p.batch ? (int64_t)a.rows * a.slices : 0;
     p.b_zrows = p.batch ? (int64_t)b.rows * b.slices : 0;
-    if (prm.exact)
-        return use_pair_kernel() ? launch_pair(a, b, p, s) : launch_impl<kExactBN, true, kExactEpiWarps>(a, b, p, s);
+    if (prm.exact) {
+        if (use_pair_kernel()) return launch_pair(a, b, p, s);
+        const int64_t wide_tiles = (int64_t)((p.M + BM - 1) / BM) * ((p.N + 255) / 256) * (p.batch ? p.batch : 1);
+        if (use_wide_exact() && wide_tiles >= kExactWideMinTiles && p.K <= kExactWideMaxK)
+            return launch_impl<256, true, 16>(a, b, p, s);
+        return launch_impl<kExactBN, true, kExactEpiWarps>(a, b, p, s);
+    }
     return launch_impl<kFloatBN, false, 8>(a, b, p, s);
 }
 

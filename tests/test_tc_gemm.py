@@ -161,3 +161,18 @@ def test_pair_kernel_exact():
     r = subprocess.run([sys.executable, "-c", PAIR_SCRIPT], cwd=root, env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0 and "PAIR-OK" in r.stdout, r.stdout + r.stderr
+
+
+def test_ozaki_wide_tiles_exact(spin):
+    # enough 128 x 256 tiles (20 x 32 = 640) for the wide exact kernel, whose
+    # running sums go through D; ragged K, beta C and the identity
+    m, n, k = 2560, 8192, 200
+    rng = np.random.default_rng(5)
+    A = rng.integers(-120, 121, size=(m, k)).astype(np.float64)
+    B = rng.integers(-120, 121, size=(k, n)).astype(np.float64)
+    C = rng.integers(-50, 50, size=(m, n)).astype(np.float64)
+    D = host(spin.gemm_ozaki(dev(A), dev(B), slices=3, alpha=-1.0, beta=1.0, C=dev(C), add_identity=True))
+    assert spin.take_device_error() == 0
+    want = C - A @ B  # integers below 2^22: exact in FP64
+    want[np.arange(m), np.arange(m)] += 1
+    np.testing.assert_array_equal(D, want)
