@@ -98,6 +98,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: arrival window (s)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: Poisson arrival rate (req/s)")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--fp64-levels", type=int, default=2,
+                    help="mixed workloads: top recursion levels with FP64-class Schur complements")
     ap.add_argument("--pretransform", type=int, default=0, choices=[0, 1, 2],
                     help="single-matrix workloads: random butterfly transform around the recursion "
                          "(1: always, 2: after a breakdown); the default workloads need none")
@@ -361,11 +363,12 @@ def oracle_size_sweep(w: dict, sizes: list) -> list:
 class SingleWork:
     """One matrix per rank: spin_invert_ex on a device-resident input."""
 
-    def __init__(self, spin, w, n, leaf, device, pretransform=0):
+    def __init__(self, spin, w, n, leaf, device, pretransform=0, fp64_levels=2):
         import torch
 
         self.spin, self.w, self.n, self.leaf = spin, w, n, leaf
         self.pt = pretransform
+        self.fl = fp64_levels
         self.A, self.known = make_input(w, n, device)
         self.X = torch.empty_like(self.A)
         self.flops = 2.0 * float(n) ** 3
@@ -376,7 +379,7 @@ class SingleWork:
 
     def step(self):
         self.spin.invert(self.A, leaf=self.leaf, precision=self.w["precision"], out=self.X, blocking=False,
-                         pretransform=self.pt, rbt_seed=SEED_BASE + 5)
+                         pretransform=self.pt, rbt_seed=SEED_BASE + 5, fp64_levels=self.fl)
 
     def launches(self, recs, steps):
         return len(recs)
@@ -491,7 +494,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
     if w["family"] == "batch_sdd":
         work = BatchWork(spin, w, n, leaf, device, BATCH_COUNT)
     else:
-        work = SingleWork(spin, w, n, leaf, device, args.pretransform)
+        work = SingleWork(spin, w, n, leaf, device, args.pretransform, args.fp64_levels)
     stream = torch.cuda.current_stream()
     flops = work.flops
 
@@ -578,6 +581,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
     batch = isinstance(work, BatchWork)
     config = {"workload": args.workload, "n": n, "leaf": leaf, "precision": w["precision"],
               **({"pretransform": args.pretransform} if args.pretransform else {}),
+              **({"fp64_levels": args.fp64_levels} if w["precision"] != "fp64" else {}),
               "matrices_per_gpu": len(work.orders) if batch else 1, "parallelism": f"replicas{world}",
               "desc": w["desc"]}
     if batch:

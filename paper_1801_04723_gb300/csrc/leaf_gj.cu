@@ -130,6 +130,9 @@ __device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int
 
     const int r0 = rank * R;
     const int nrows = max(0, min(R, L - r0));
+    const int col_threads = L < NT ? L : NT;  // elimination: threads per row
+    const int row_groups = NT / col_threads;  // ... and rows handled at once
+    const int tc = tid % col_threads, tr = tid / col_threads;
 
     for (size_t idx = tid; idx < (size_t)nrows * L; idx += NT) {
         const int r = (int)(idx / L), j = (int)(idx % L);
@@ -197,15 +200,21 @@ __device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int
         // window), or the L2-resident work rows when they live in global memory
         const double* rprow = ROWS_IN_SMEM ? cluster.map_shared_rank(M, owner) + (size_t)(p - owner * R) * L
                                            : gwork + (size_t)p * L;
-        for (int j = tid; j < L; j += NT) {
-            const double pj = (j == k) ? inv : rprow[j] * inv;
-            for (int r = 0; r < nrows; r++) {
-                if (r0 + r == p) continue;
-                const double f = fcol[r];
-                if (f == 0.0) continue;
-                double* mr = M + (size_t)r * L;
-                const double base = (j == k) ? 0.0 : mr[j];
-                mr[j] = fma(-f, pj, base);
+        // threads tile the rows x columns block: tc columns apart along a
+        // row (coalesced), tr row groups, so that narrow leaves (L < NT)
+        // keep every thread busy; each thread reads a pivot-row entry once
+        // per column it owns
+        if (tr < row_groups) {
+            for (int j = tc; j < L; j += col_threads) {
+                const double pj = (j == k) ? inv : rprow[j] * inv;
+                for (int r = tr; r < nrows; r += row_groups) {
+                    if (r0 + r == p) continue;
+                    const double f = fcol[r];
+                    if (f == 0.0) continue;
+                    double* mr = M + (size_t)r * L;
+                    const double base = (j == k) ? 0.0 : mr[j];
+                    mr[j] = fma(-f, pj, base);
+                }
             }
         }
         __syncthreads();

@@ -558,48 +558,53 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 // CTA.  At exit the even CTA accounts for every copy either CTA issued
 // (arming or cancelling the expected bytes of uses that only one CTA
 // issued) and waits for them, so no copy is in flight when the pair leaves.
-constexpr int PAIR_BN = 128, PAIR_BNH = PAIR_BN / 2;
-constexpr uint32_t PAIR_B_BYTES = PAIR_BNH * BK * 2;                         // 8 KB
-constexpr uint32_t PAIR_STAGE_BYTES = KSUB_EXACT * (A_TILE_BYTES + PAIR_B_BYTES);  // per CTA
-constexpr int PAIR_STAGES = (196608 / PAIR_STAGE_BYTES) > 8 ? 8 : (196608 / PAIR_STAGE_BYTES);
-constexpr uint32_t PAIR_TMEM_COLS = 4 * PAIR_BN;  // two accumulators + FP64 running sums
-constexpr size_t PAIR_SMEM_BYTES = 1024 + PAIR_STAGES * PAIR_STAGE_BYTES + 256;
-static_assert(PAIR_STAGES <= STAGES_MAX, "ring");
+template <int PBN>
+struct PairCfg {
+    static constexpr int BNH = PBN / 2;                                  // B rows per CTA
+    static constexpr uint32_t B_BYTES = BNH * BK * 2;
+    static constexpr uint32_t STAGE_BYTES = KSUB_EXACT * (A_TILE_BYTES + B_BYTES);  // per CTA
+    static constexpr int STAGES = (196608 / STAGE_BYTES) > 8 ? 8 : (196608 / STAGE_BYTES);
+    static constexpr bool TMEM_SUMS = 4 * PBN <= 512;  // FP64 running sums beside the accumulators
+    static constexpr uint32_t TMEM_COLS = TMEM_SUMS ? 4 * PBN : 2 * PBN;
+    static constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
+    static_assert(STAGES >= 2 && STAGES <= STAGES_MAX, "ring");
+};
 
-template <int EPI_WARPS>
+template <int PBN, int EPI_WARPS>
 __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(Epi<EPI_WARPS>::MAXREG)
 tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const TcGemmParams p) {
-    constexpr int HALF = PAIR_BN / (EPI_WARPS / 4);
-    static_assert(EPI_WARPS % 4 == 0 && PAIR_BN % (EPI_WARPS / 4) == 0 && HALF % 32 == 0, "epilogue split");
+    using C = PairCfg<PBN>;
+    constexpr int HALF = PBN / (EPI_WARPS / 4);
+    static_assert(EPI_WARPS % 4 == 0 && PBN % (EPI_WARPS / 4) == 0 && HALF % 16 == 0, "epilogue split");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* smA = base;                                    // [stage][sub] A tiles
-    unsigned char* smB = base + PAIR_STAGES * KSUB_EXACT * A_TILE_BYTES;  // [stage][sub] B tiles
-    SmemCtl* ctl = reinterpret_cast<SmemCtl*>(base + PAIR_STAGES * PAIR_STAGE_BYTES);
+    unsigned char* smB = base + C::STAGES * KSUB_EXACT * A_TILE_BYTES;  // [stage][sub] B tiles
+    SmemCtl* ctl = reinterpret_cast<SmemCtl*>(base + C::STAGES * C::STAGE_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();  // 0 issues the pair's MMAs
     const int z = p.batch ? (int)blockIdx.y : 0;
     int m0, n0;  // the pair's tile; grouped rasterisation as in tc_gemm_kernel
     {
-        const int num_m = (p.M + 2 * BM - 1) / (2 * BM), num_n = (p.N + PAIR_BN - 1) / PAIR_BN;
+        const int num_m = (p.M + 2 * BM - 1) / (2 * BM), num_n = (p.N + PBN - 1) / PBN;
         const int pid = (int)(blockIdx.x >> 1);
         const int per_group = GROUP_M * num_n;
         const int first_m = (pid / per_group) * GROUP_M;
         const int gsize = min(num_m - first_m, GROUP_M);
         const int in_group = pid % per_group;
         m0 = (first_m + in_group % gsize) * 2 * BM;
-        n0 = (in_group / gsize) * PAIR_BN;
+        n0 = (in_group / gsize) * PBN;
     }
     const int my_m0 = m0 + (int)rank * BM;        // this CTA's A rows = its TMEM lanes
-    const int my_n0 = n0 + (int)rank * PAIR_BNH;  // this CTA's B rows
+    const int my_n0 = n0 + (int)rank * C::BNH;  // this CTA's B rows
     const int KB = (p.K + BK - 1) / BK;
     const int chunk_kb = p.chunk_kb;
     const int nchunks_per_pair = (KB + chunk_kb - 1) / chunk_kb;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < PAIR_STAGES; s++) {
+        for (int s = 0; s < C::STAGES; s++) {
             mbar_init(&ctl->full[s], 1);
             mbar_init(&ctl->empty[s], 1);
         }
@@ -615,7 +620,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         prefetch_tensormap(&tmB);
     }
     if (warp == 1) {
-        tmem_alloc_pair(&ctl->tmem_base, PAIR_TMEM_COLS);
+        tmem_alloc_pair(&ctl->tmem_base, C::TMEM_COLS);
         tmem_relinquish_pair();
     }
     tc_fence_before();
@@ -634,17 +639,17 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                 for (int c = 0; c < nchunks_per_pair && ok; c++) {
                     const int kb1 = min(KB, (c + 1) * chunk_kb);
                     for (int kb = c * chunk_kb; kb < kb1; kb += KSUB_EXACT) {
-                        const int s = it % PAIR_STAGES;
-                        const uint32_t ph = (uint32_t)((it / PAIR_STAGES) & 1);
+                        const int s = it % C::STAGES;
+                        const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
                         ok = mbar_wait_cluster(&ctl->empty[s], ph ^ 1u, abort, WAIT_LIMIT_NS) && !*abort;
                         if (!ok) break;
-                        if (rank == 0) mbar_arrive_expect_tx(&ctl->full[s], 2 * PAIR_STAGE_BYTES);
+                        if (rank == 0) mbar_arrive_expect_tx(&ctl->full[s], 2 * C::STAGE_BYTES);
                         const uint32_t bar = full0 + (uint32_t)(s * sizeof(uint64_t));
 #pragma unroll
                         for (int u = 0; u < KSUB_EXACT; u++) {
                             tma_load_2d_pair(smA + (s * KSUB_EXACT + u) * A_TILE_BYTES, &tmA, (kb + u) * BK,
                                              (int)(z * p.a_zrows) + p.pa[q] * p.a_rows + my_m0, bar);
-                            tma_load_2d_pair(smB + (s * KSUB_EXACT + u) * PAIR_B_BYTES, &tmB, (kb + u) * BK,
+                            tma_load_2d_pair(smB + (s * KSUB_EXACT + u) * C::B_BYTES, &tmB, (kb + u) * BK,
                                              (int)(z * p.b_zrows) + p.pb[q] * p.b_rows + my_n0, bar);
                         }
                         it++;
@@ -659,7 +664,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             // --------------------------------- MMA issuer (even CTA), M = 256
             bool ok = ld_cluster_u32(mapa_u32(smem_u32(&ctl->tmem_base), 1u)) == tmem_base;
             if (!ok) raise_pair_error(ctl, p.err, SPIN_ERR_CUDA);  // both CTAs must hold the same columns
-            const uint32_t idesc = idesc_bf16_f32(2 * BM, PAIR_BN);
+            const uint32_t idesc = idesc_bf16_f32(2 * BM, PBN);
             int it = 0, chunk = 0;
             for (int q = 0; q < p.num_pairs && ok; q++)
                 for (int c = 0; c < nchunks_per_pair && ok; c++) {
@@ -668,16 +673,16 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     ok = mbar_wait_cluster(&ctl->tempty[buf], (use & 1u) ^ 1u, abort, WAIT_LIMIT_NS);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t d = tmem_base + (uint32_t)(buf * PAIR_BN);
+                    const uint32_t d = tmem_base + (uint32_t)(buf * PBN);
                     const int kb0 = c * chunk_kb, kb1 = min(KB, (c + 1) * chunk_kb);
                     for (int kb = kb0; kb < kb1 && ok; kb += KSUB_EXACT) {
-                        const int s = it % PAIR_STAGES;
-                        ok = mbar_wait_cluster(&ctl->full[s], (uint32_t)((it / PAIR_STAGES) & 1), abort,
+                        const int s = it % C::STAGES;
+                        ok = mbar_wait_cluster(&ctl->full[s], (uint32_t)((it / C::STAGES) & 1), abort,
                                                WAIT_LIMIT_NS);
                         if (!ok) break;
                         tc_fence_after();
                         const uint64_t ad0 = sdesc_kmajor_sw128(smem_u32(smA + s * KSUB_EXACT * A_TILE_BYTES));
-                        const uint64_t bd0 = sdesc_kmajor_sw128(smem_u32(smB + s * KSUB_EXACT * PAIR_B_BYTES));
+                        const uint64_t bd0 = sdesc_kmajor_sw128(smem_u32(smB + s * KSUB_EXACT * C::B_BYTES));
                         const int nsub = min(KSUB_EXACT, kb1 - kb);
 #pragma unroll
                         for (int u = 0; u < KSUB_EXACT; u++) {
@@ -685,7 +690,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 #pragma unroll
                                 for (int k = 0; k < BK / 16; k++)
                                     mma_bf16_pair(d, ad0 + ((u * A_TILE_BYTES + k * 32) >> 4),
-                                                  bd0 + ((u * PAIR_B_BYTES + k * 32) >> 4), idesc,
+                                                  bd0 + ((u * C::B_BYTES + k * 32) >> 4), idesc,
                                                   (kb == kb0 && u == 0 && k == 0) ? 0u : 1u);
                             }
                         }
@@ -709,7 +714,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         const int half = e >> 2;
         const int grow = my_m0 + quarter * 32 + lane;
         const uint32_t lane_addr = tmem_base + ((uint32_t)(quarter * 32) << 16);
-        double sumsq = exact_epilogue<PAIR_BN, HALF, true>(
+        double sumsq = exact_epilogue<PBN, HALF, true, C::TMEM_SUMS, (EPI_WARPS >= 16 ? 16 : 32)>(
             p, ctl, abort, lane_addr, half, grow, n0 + half * HALF, nchunks_per_pair, lane,
             mapa_u32(smem_u32(&ctl->tempty[0]), 0u), mapa_u32(smem_u32(&ctl->tempty[1]), 0u), z);
         if (p.sumsq) {
@@ -722,25 +727,25 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     tc_fence_before();
     cluster_sync_all();  // both producers have stopped; no MMA of the pair is in flight
     if (rank == 0 && threadIdx.x == 0) {
-        // Copies still in flight can only belong to the last PAIR_STAGES uses
-        // (a use is issued after the use PAIR_STAGES earlier was consumed).
+        // Copies still in flight can only belong to the last C::STAGES uses
+        // (a use is issued after the use C::STAGES earlier was consumed).
         const int own = ctl->issued;
         const int peer = (int)ld_cluster_u32(mapa_u32(smem_u32(&ctl->issued), 1u));
         const int hi = max(own, peer);
-        for (int j = max(0, hi - PAIR_STAGES); j < hi; j++) {
-            uint64_t* bar = &ctl->full[j % PAIR_STAGES];
+        for (int j = max(0, hi - C::STAGES); j < hi; j++) {
+            uint64_t* bar = &ctl->full[j % C::STAGES];
             if (j >= own)
-                mbar_arrive_expect_tx(bar, PAIR_STAGE_BYTES);  // only the odd CTA issued this use
+                mbar_arrive_expect_tx(bar, C::STAGE_BYTES);  // only the odd CTA issued this use
             else if (j >= peer)
-                mbar_complete_tx(bar, PAIR_STAGE_BYTES);  // the odd CTA's share will not come
+                mbar_complete_tx(bar, C::STAGE_BYTES);  // the odd CTA's share will not come
             volatile int never = 0;
-            mbar_wait_cluster(bar, (uint32_t)((j / PAIR_STAGES) & 1), &never, WAIT_LIMIT_NS);
+            mbar_wait_cluster(bar, (uint32_t)((j / C::STAGES) & 1), &never, WAIT_LIMIT_NS);
         }
     }
     cluster_sync_all();  // no copy into either CTA is in flight
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc_pair(tmem_base, PAIR_TMEM_COLS);
+        tmem_dealloc_pair(tmem_base, C::TMEM_COLS);
     }
 }
 
@@ -1079,23 +1084,24 @@ int launch_impl(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, c
     return SPIN_OK;
 }
 
+template <int PBN, int EPI_WARPS>
 int launch_pair(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, cudaStream_t s) {
+    using C = PairCfg<PBN>;
     CUtensorMap ta, tb;
     const int64_t nz = p.batch ? p.batch : 1;
     int rc = make_map(&ta, a.base, p.K, (int64_t)a.rows * a.slices * nz, a.ld, BM);
     if (rc) return rc;
-    rc = make_map(&tb, b.base, p.K, (int64_t)b.rows * b.slices * nz, b.ld, PAIR_BNH);
+    rc = make_map(&tb, b.base, p.K, (int64_t)b.rows * b.slices * nz, b.ld, C::BNH);
     if (rc) return rc;
     static bool attr = false;
-    auto kern = tc_gemm_pair_kernel<kExactEpiWarps>;
+    auto kern = tc_gemm_pair_kernel<PBN, EPI_WARPS>;
     if (!attr) {
-        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PAIR_SMEM_BYTES));
+        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES));
         attr = true;
     }
-    const int64_t tiles = (int64_t)((p.N + PAIR_BN - 1) / PAIR_BN) * ((p.M + 2 * BM - 1) / (2 * BM));
+    const int64_t tiles = (int64_t)((p.N + PBN - 1) / PBN) * ((p.M + 2 * BM - 1) / (2 * BM));
     if (2 * tiles > INT32_MAX) return SPIN_ERR_INVALID_ARG;
-    kern<<<dim3((unsigned)(2 * tiles), (unsigned)nz), Epi<kExactEpiWarps>::THREADS, PAIR_SMEM_BYTES, s>>>(ta, tb,
-                                                                                                       p);
+    kern<<<dim3((unsigned)(2 * tiles), (unsigned)nz), Epi<EPI_WARPS>::THREADS, C::SMEM_BYTES, s>>>(ta, tb, p);
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
 }
@@ -1137,8 +1143,13 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& p
     p.a_zrows = p.batch ? (int64_t)a.rows * a.slices : 0;
     p.b_zrows = p.batch ? (int64_t)b.rows * b.slices : 0;
     if (prm.exact) {
-        if (use_pair_kernel()) return launch_pair(a, b, p, s);
-        const int64_t wide_tiles = (int64_t)((p.M + BM - 1) / BM) * ((p.N + 255) / 256) * (p.batch ? p.batch : 1);
+        // per problem: many small problems of a batch stay on the narrow tiles
+        const int64_t wide_tiles = (int64_t)((p.M + BM - 1) / BM) * ((p.N + 255) / 256);
+        if (use_pair_kernel()) {
+            if (use_wide_exact() && wide_tiles >= 2 * kExactWideMinTiles)
+                return launch_pair<256, 16>(a, b, p, s);
+            return launch_pair<128, kExactEpiWarps>(a, b, p, s);
+        }
         if (use_wide_exact() && wide_tiles >= kExactWideMinTiles && p.K <= kExactWideMaxK)
             return launch_impl<256, true, 16>(a, b, p, s);
         return launch_impl<kExactBN, true, kExactEpiWarps>(a, b, p, s);
