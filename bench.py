@@ -98,6 +98,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: arrival window (s)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: Poisson arrival rate (req/s)")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-priority-order", type=int, default=1024,
+                    help="serving: requests of order <= this run on high-priority streams (0: off)")
     ap.add_argument("--fp64-levels", type=int, default=2,
                     help="mixed workloads: top recursion levels with FP64-class Schur complements")
     ap.add_argument("--pretransform", type=int, default=0, choices=[0, 1, 2],
@@ -670,7 +672,8 @@ def run_serve(args, w: dict):
     # Offered load beyond what the GPU serves makes the queue grow; requests
     # whose A would take the queued bytes above 48 GB are shed (the A of
     # queued requests stays in the client's device memory).
-    srv = spin.Server(hbm_budget_bytes=150 << 30, max_slots=args.serve_slots, max_queued_bytes=48 << 30)
+    srv = spin.Server(hbm_budget_bytes=150 << 30, max_slots=args.serve_slots, max_queued_bytes=48 << 30,
+                      priority_order=args.serve_priority_order)
     pending = {}
     done = []
     shed = 0
@@ -730,6 +733,7 @@ def run_serve(args, w: dict):
         "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
         "config": {"workload": "serve", "rate_req_s": args.serve_rate, "arrival_window_s": args.serve_seconds,
                    "requests": len(trace), "n_range": [64, min(8192, w["n"])], "slots": args.serve_slots,
+                   "priority_order": args.serve_priority_order,
                    "hbm_budget_gb": 150, "fp64_class_path": args.serve_fp64_path, "desc": w["desc"]},
         "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat[-1] if lat else None,
         "offered_req_s": len(trace) / args.serve_seconds,

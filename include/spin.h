@@ -195,7 +195,9 @@ int spin_batched_refine_info(spin_stream_t stream, int* refine_iters, double* wo
 typedef struct spin_serve_cfg {
     size_t hbm_budget_bytes;  /* device memory the server may hold for requests       */
     int32_t max_slots;        /* requests running at once (one stream and thread each) */
-    int32_t reserved;
+    int32_t priority_order;   /* 0: off; else requests of order <= this run on
+                                 high-priority streams, so that their kernels are
+                                 scheduled ahead of a large request's pending blocks */
     size_t max_queued_bytes;  /* load shedding: 0 = unbounded queue; else a submit whose
                                  A (n*n*8 bytes) would take the bytes of A held by
                                  queued, not yet admitted, requests above this is

@@ -76,7 +76,7 @@ KERNEL_KINDS = {0: "leaf_gj", 1: "gemm_f64", 2: "gemm_tc", 3: "split", 4: "resid
 
 
 class ServeCfg(ctypes.Structure):
-    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("priority_order", ctypes.c_int32),
                 ("max_queued_bytes", ctypes.c_size_t)]
 
 
@@ -518,8 +518,9 @@ class Server:
     With ``max_queued_bytes`` a submit that would overfill the queue is shed:
     ``submit`` returns None."""
 
-    def __init__(self, hbm_budget_bytes: int, max_slots: int = 4, max_queued_bytes: int = 0):
-        cfg = ServeCfg(int(hbm_budget_bytes), int(max_slots), 0, int(max_queued_bytes))
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 4, max_queued_bytes: int = 0,
+                 priority_order: int = 0):
+        cfg = ServeCfg(int(hbm_budget_bytes), int(max_slots), int(priority_order), int(max_queued_bytes))
         h = ctypes.c_void_p()
         rc = lib().spin_serve_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != SPIN_OK:

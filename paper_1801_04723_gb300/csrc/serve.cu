@@ -64,7 +64,8 @@ struct spin_server {
     uint64_t next_ticket = 1;
     bool stop = false;
     std::vector<std::thread> workers;
-    std::vector<cudaStream_t> streams;
+    std::vector<cudaStream_t> streams;       // per slot, default priority
+    std::vector<cudaStream_t> hi_streams;    // per slot, high priority (small requests)
     cudaStream_t copy_stream = nullptr;
     // counters
     uint64_t submitted = 0, completed = 0, rejected = 0, shed = 0;
@@ -83,7 +84,6 @@ size_t request_workspace(int64_t n, int precision, double tol) {
 
 void worker_loop(spin_server* sv, int slot) {
     cudaSetDevice(sv->device);
-    cudaStream_t s = sv->streams[slot];
     while (true) {
         std::shared_ptr<Request> rq;
         {
@@ -104,6 +104,8 @@ void worker_loop(spin_server* sv, int slot) {
         }
         rq->t_start = Clock::now();
         const int64_t n = rq->n;
+        cudaStream_t s = (sv->cfg.priority_order > 0 && n <= sv->cfg.priority_order) ? sv->hi_streams[slot]
+                                                                                       : sv->streams[slot];
         const size_t nn = (size_t)n * (size_t)n * sizeof(double);
         const size_t ws_bytes = request_workspace(n, rq->precision, rq->tol);
         double* Ad = nullptr;
@@ -155,7 +157,8 @@ void worker_loop(spin_server* sv, int slot) {
 using namespace spin;
 
 extern "C" int spin_serve_create(const spin_serve_cfg* cfg, spin_server** out) {
-    if (cfg == nullptr || out == nullptr || cfg->max_slots < 1 || cfg->max_slots > 64 || cfg->hbm_budget_bytes == 0)
+    if (cfg == nullptr || out == nullptr || cfg->max_slots < 1 || cfg->max_slots > 64 || cfg->hbm_budget_bytes == 0 ||
+        cfg->priority_order < 0)
         return SPIN_ERR_INVALID_ARG;
     auto* sv = new spin_server();
     sv->cfg = *cfg;
@@ -174,8 +177,12 @@ extern "C" int spin_serve_create(const spin_serve_cfg* cfg, spin_server** out) {
     }
     uint64_t keep = cfg->hbm_budget_bytes;  // keep freed blocks for reuse up to the budget
     cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    int prio_lo = 0, prio_hi = 0;  // numerically: least and greatest priority
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     sv->streams.resize(cfg->max_slots);
-    for (auto& st : sv->streams) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    sv->hi_streams.resize(cfg->max_slots);
+    for (auto& st : sv->streams) cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio_lo);
+    for (auto& st : sv->hi_streams) cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio_hi);
     cudaStreamCreateWithFlags(&sv->copy_stream, cudaStreamNonBlocking);
     for (int i = 0; i < cfg->max_slots; i++) sv->workers.emplace_back(worker_loop, sv, i);
     *out = sv;
@@ -298,6 +305,7 @@ extern "C" int spin_serve_destroy(spin_server* sv) {
         if (kv.second->X) cudaFreeAsync(kv.second->X, sv->copy_stream);
     cudaStreamSynchronize(sv->copy_stream);
     for (auto& st : sv->streams) cudaStreamDestroy(st);
+    for (auto& st : sv->hi_streams) cudaStreamDestroy(st);
     cudaStreamDestroy(sv->copy_stream);
     cudaMemPoolDestroy(sv->pool);
     delete sv;

@@ -23,10 +23,12 @@ def spin():
     return s
 
 
-def test_serve_mix_equals_alone(spin):
+@pytest.mark.parametrize("priority_order", [0, 512])
+def test_serve_mix_equals_alone(spin, priority_order):
+    # priority_order: requests of order <= 512 on high-priority streams
     trace = inputs.serve_trace(inputs.SEED_BASE + 4004, rate=400.0, duration=0.08, lo=64, hi=1024)
     assert len(trace) >= 20
-    srv = spin.Server(hbm_budget_bytes=16 << 30, max_slots=4)
+    srv = spin.Server(hbm_budget_bytes=16 << 30, max_slots=4, priority_order=priority_order)
     reqs = []
     t0 = time.perf_counter()
     for j, (t_arr, n, alpha, mixed) in enumerate(trace):
