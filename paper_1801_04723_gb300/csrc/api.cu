@@ -562,14 +562,14 @@ __global__ void synth_sdd_kernel(double* A, int64_t n, uint64_t seed) {
 // 2^ceil(log2 L)) CTAs with R = ceil(L / C) rows each, L pivot steps of
 //   a + b L + R L / (2 FMA/clock)     (rows in shared memory)
 //   a + b L + R L g                   (rows in L2-resident global memory)
-// a = 3.64 us, b = 8.7 ns (per-step latency of the leaf microbenchmark at
-// L = 128 and 256 on 16 CTAs) and g = 0.97 ns per element (one n = 8192,
-// L = 2048 measurement).  It reproduces the measured sweeps at n = 8192 and
-// 16384 (leaf 64 ... 2048) within 2.5 %.
+// a = 0.65 us, b = 15.7 ns (the leaf microbenchmark's per-step times at
+// L = 128 ... 512 on 16 CTAs) and g = 0.45 ns per element (its times at L =
+// 640 ... 2048).  It reproduces the measured sweeps at n = 4096, 8192 and
+// 16384 (leaf 64 ... 2048) within 6 %.
 constexpr double kModelClock = 2.07e9;
 constexpr double kModelPsm = 4.0 * kModelClock;
 constexpr double kModelPgpu = 152.0 * kModelPsm;
-constexpr double kModelLaunch = 4e-6, kModelA = 3.64e-6, kModelB = 8.7e-9, kModelG = 0.97e-9;
+constexpr double kModelLaunch = 4e-6, kModelA = 0.65e-6, kModelB = 15.7e-9, kModelG = 0.45e-9;
 
 double model_gemm(int64_t m, int64_t n, int64_t k) {
     const double tiles = (double)((m + 63) / 64) * (double)((n + 63) / 64);
@@ -581,7 +581,7 @@ double model_leaf(int64_t L) {
     int64_t C = 1;
     while (C < 16 && C < L) C <<= 1;
     const int64_t R = (L + C - 1) / C;
-    const bool smem = (double)R * L * 8 + (double)L * 16 + 64 <= 200.0 * 1024;
+    const bool smem = L <= 256 || (double)R * L * 8 + 16.0 * R + 64.0 * C + 16.0 * L <= 200.0 * 1024;
     const double work = smem ? (double)R * L / (2.0 * kModelClock) : (double)R * L * kModelG;
     return (double)L * (kModelA + kModelB * (double)L + work);
 }

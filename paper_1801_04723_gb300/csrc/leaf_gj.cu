@@ -12,20 +12,31 @@
 // GB300 mapping.  FP64 runs at ~2 FMA/clock/SM, so one L x L leaf on one SM
 // takes ~L^3 cycles; the leaf is spread over a thread-block cluster of C
 // CTAs (C <= 16) whose rows stay put: every CTA owns R = ceil(L/C) rows in
-// shared memory when they fit (global memory, L2-resident, otherwise).  Row interchanges
-// are bookkeeping only (position <-> physical row tables replicated in every
-// CTA), so no data moves between CTAs except the pivot row, read through
-// distributed shared memory.  Per step: cluster barrier -> every CTA reduces
-// the C published candidates identically -> all CTAs eliminate their rows
-// with the pivot row read raw from its owner through distributed shared
-// memory and scaled on the fly -> each CTA publishes its candidate for the
-// next column.  One cluster barrier per step (a hardware barrier: no
-// spin-wait anywhere); the owner scales the pivot row in place after the
-// next barrier.
+// shared memory when they fit (global memory, L2-resident, otherwise).  Row
+// interchanges are bookkeeping only (position <-> physical row tables
+// replicated in every CTA).  A pivot step is latency-bound at these sizes,
+// so each step has one cluster barrier, one block barrier and no remote
+// read on its critical path:
+//   wait (cluster barrier k) -> every warp reduces the C candidates that the
+//   CTAs pushed into its shared memory (redux.sync argmax) -> eliminate this
+//   CTA's rows with the pivot row -> block barrier -> every warp finds this
+//   CTA's candidate for column k+1 -> push it (and, for L <= 256, its whole
+//   row) into every peer's shared memory -> arrive (cluster barrier k+1).
+// For L > 256 the pushed rows would not fit, so the pivot row is read from
+// its owner (distributed shared memory or the L2-resident work rows).
+// Candidate and row slots alternate between two buffers: a CTA writes step
+// k+1's slot while a slower peer may still read step k's; the slot it
+// overwrites was last read in step k-1, which every CTA finished before it
+// arrived at barrier k.  The multipliers of step k+1 (column k+1 after step
+// k) are written to a second buffer by the threads that compute them, so no
+// thread reads a column while another overwrites it.  The pivot row of step
+// k is left raw; its scaling by 1/pivot is folded into step k+1's update of
+// that row.  No spin-wait anywhere: both barriers are hardware barriers.
 #include <cooperative_groups.h>
 #include <limits.h>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -33,25 +44,43 @@ namespace spin {
 namespace {
 
 constexpr int NT = 256;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kPushMaxL = NT;  // rows are pushed when one thread per column covers the row
+constexpr int kMessengers = 32;  // with pushed rows: one more warp that publishes the candidates
 
+// A pivot candidate.  The key is the bit pattern of |pivot| (NaN mapped to
+// +inf, so that it is chosen and then rejected): for non-negative doubles
+// the bit patterns order like the values, so every comparison is an
+// integer one and the SM's FP64 pipe (~2 operations per clock on GB300)
+// only does the elimination's FMAs.  No candidate: key 0, position INT_MAX.
 struct Cand {
-    double key;   // |pivot| (NaN mapped to +inf so that it is chosen and rejected)
-    double val;   // signed pivot value
-    int pos;      // logical position of the row
-    int phys;     // physical row
+    uint64_t key;
+    double val;  // signed pivot value
+    double inv;  // 1 / val, computed once by the CTA that publishes the candidate
+    int pos;     // logical position of the row
+    int phys;    // physical row, -1: no candidate
 };
+constexpr uint64_t kInfBits = 0x7ff0000000000000ull;
 
 struct LeafSmemLayout {
-    size_t m_off, fcol_off, cand_off, phys_off, lpos_off, piv_off, sig_off, total;
+    size_t bar_off, m_off, prow_off, fcol_off, info_off, phys_off, lpos_off, piv_off, sig_off, total;
 };
 
-__host__ __device__ inline LeafSmemLayout leaf_layout(int L, int R, bool rows_in_smem) {
+// Candidate-row slots hold L doubles padded to an even count, so that every
+// slot row starts on a 16-byte boundary (16-byte remote stores).
+__host__ __device__ inline int slot_stride(int L) { return (L + 1) & ~1; }
+
+__host__ __device__ inline LeafSmemLayout leaf_layout(int L, int R, int C, bool rows_in_smem, bool push) {
     LeafSmemLayout s;
+    auto a16 = [](size_t v) { return (v + 15) & ~(size_t)15; };
     size_t off = 0;
+    s.bar_off = off; off += 2 * sizeof(uint64_t);
     s.m_off = off;
     if (rows_in_smem) off += (size_t)R * L * sizeof(double);
-    s.fcol_off = off; off += (size_t)R * sizeof(double);
-    s.cand_off = off; off += 2 * sizeof(Cand);
+    s.prow_off = off = a16(off);
+    if (push) off += 2 * (size_t)C * slot_stride(L) * sizeof(double);
+    s.fcol_off = off = a16(off); off += 2 * (size_t)R * sizeof(double);
+    s.info_off = off = a16(off); off += 2 * (size_t)C * sizeof(Cand);
     s.phys_off = off; off += (size_t)L * sizeof(int);
     s.lpos_off = off; off += (size_t)L * sizeof(int);
     s.piv_off = off; off += (size_t)L * sizeof(int);
@@ -60,179 +89,107 @@ __host__ __device__ inline LeafSmemLayout leaf_layout(int L, int R, bool rows_in
     return s;
 }
 
-__device__ __forceinline__ bool better(double k1, int p1, double k2, int p2) {
-    return k1 > k2 || (k1 == k2 && p1 < p2);
+// Warp-wide argmax by (key descending, position ascending); every lane gets
+// the winner.  Three redux.sync steps replace a shuffle tree: the high word
+// of the key, the low word among the lanes that hold the high maximum, the
+// lowest position among the ties.
+__device__ __forceinline__ Cand warp_argmax(uint64_t key, double val, double inv, int pos, int phys) {
+    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+    const unsigned mhi = __reduce_max_sync(FULL, hi);
+    const unsigned mlo = __reduce_max_sync(FULL, hi == mhi ? lo : 0u);
+    const bool tie = hi == mhi && lo == mlo;
+    const unsigned mpos = __reduce_min_sync(FULL, tie ? (unsigned)pos : 0xffffffffu);
+    const int src = __ffs(__ballot_sync(FULL, tie && (unsigned)pos == mpos)) - 1;
+    Cand w;
+    w.key = ((uint64_t)mhi << 32) | mlo;
+    w.val = __shfl_sync(FULL, val, src);
+    w.inv = __shfl_sync(FULL, inv, src);
+    w.pos = __shfl_sync(FULL, pos, src);
+    w.phys = __shfl_sync(FULL, phys, src);
+    return w;
 }
 
-// Block-wide search of this CTA's candidate for column k among its rows at
-// positions >= k.  Result in *out (written by thread 0).
-__device__ void local_candidate(const double* M, int L, int nrows, int r0, const int* lpos, int k, Cand* out,
-                                Cand* warp_scratch) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double key = -1.0, val = 0.0;
+// This CTA's candidate for column k among its rows at positions >= k,
+// computed by the calling warp (every warp computes the same).
+__device__ __forceinline__ Cand warp_candidate(const double* M, int L, int nrows, int r0, const int* lpos, int k) {
+    const int lane = threadIdx.x & 31;
+    uint64_t key = 0;
+    double val = 0.0;
     int pos = INT_MAX, phys = -1;
-    if (k < L) {
-        for (int r = tid; r < nrows; r += NT) {
-            const int pr = r0 + r;
-            const int lp = lpos[pr];
-            if (lp < k) continue;
-            const double a = M[(size_t)r * L + k];
-            const double kk = isnan(a) ? INFINITY : fabs(a);
-            if (better(kk, lp, key, pos)) { key = kk; val = a; pos = lp; phys = pr; }
-        }
+    for (int r = lane; r < nrows; r += 32) {
+        const int lp = lpos[r0 + r];
+        if (lp < k) continue;
+        const double a = M[(size_t)r * L + k];
+        const uint64_t mag = (uint64_t)__double_as_longlong(a) & ~(1ull << 63);
+        const uint64_t kk = mag > kInfBits ? kInfBits : mag;
+        if (kk > key || (kk == key && lp < pos)) { key = kk; val = a; pos = lp; phys = r0 + r; }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const double ok = __shfl_down_sync(0xffffffffu, key, off);
-        const double ov = __shfl_down_sync(0xffffffffu, val, off);
-        const int op = __shfl_down_sync(0xffffffffu, pos, off);
-        const int oph = __shfl_down_sync(0xffffffffu, phys, off);
-        if (better(ok, op, key, pos)) { key = ok; val = ov; pos = op; phys = oph; }
-    }
-    if (lane == 0) warp_scratch[warp] = Cand{key, val, pos, phys};
-    __syncthreads();
-    if (warp == 0) {
-        Cand c = (lane < NT / 32) ? warp_scratch[lane] : Cand{-1.0, 0.0, INT_MAX, -1};
-        key = c.key; val = c.val; pos = c.pos; phys = c.phys;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const double ok = __shfl_down_sync(0xffffffffu, key, off);
-            const double ov = __shfl_down_sync(0xffffffffu, val, off);
-            const int op = __shfl_down_sync(0xffffffffu, pos, off);
-            const int oph = __shfl_down_sync(0xffffffffu, phys, off);
-            if (better(ok, op, key, pos)) { key = ok; val = ov; pos = op; phys = oph; }
-        }
-        if (lane == 0) *out = Cand{key, val, pos, phys};
+    return warp_argmax(key, val, 0.0, pos, phys);
+}
+
+// Bounded wait for a slot barrier (a step takes microseconds; the limit
+// only turns a broken exchange into an error instead of a hang).
+constexpr uint64_t kLeafWaitLimitNs = 4000000000ull;
+__device__ __forceinline__ bool slot_wait(uint64_t* bar, uint32_t parity) {
+    if (tc::mbar_try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = tc::globaltimer_ns();
+    for (uint32_t spins = 1;; spins++) {
+        if (tc::mbar_try_wait_cluster(bar, parity)) return true;
+        if ((spins & 63u) == 0 && tc::globaltimer_ns() - t0 > kLeafWaitLimitNs) return false;
     }
 }
 
-template <bool ROWS_IN_SMEM>
-__device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int64_t lds, double* __restrict__ dst,
-                                             int64_t ldd, double* __restrict__ gwork, int L, int R, int32_t* info,
-                                             int leaf_index) {
-    cg::cluster_group cluster = cg::this_cluster();
-    const int C = (int)cluster.num_blocks();
-    const int rank = (int)cluster.block_rank();
-    const int tid = threadIdx.x;
+// Step k's update of one entry: pj is the pivot row's entry scaled by
+// 1/pivot (1/pivot itself in the pivot column, jk), f the row's multiplier,
+// b its current entry; a zero multiplier leaves the entry as it is.
+__device__ __forceinline__ double elim_val(double f, double b, double pj, bool jk) {
+    const bool fz = ((uint64_t)__double_as_longlong(f) << 1) == 0;
+    return fz ? (jk ? f : b) : fma(-f, pj, jk ? 0.0 : b);
+}
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const LeafSmemLayout lay = leaf_layout(L, R, ROWS_IN_SMEM);
-    double* M = ROWS_IN_SMEM ? reinterpret_cast<double*>(smem_raw + lay.m_off) : gwork + (size_t)rank * R * L;
-    double* fcol = reinterpret_cast<double*>(smem_raw + lay.fcol_off);
-    Cand* cand = reinterpret_cast<Cand*>(smem_raw + lay.cand_off);
-    int* phys_at = reinterpret_cast<int*>(smem_raw + lay.phys_off);
-    int* lpos = reinterpret_cast<int*>(smem_raw + lay.lpos_off);
-    int* piv = reinterpret_cast<int*>(smem_raw + lay.piv_off);
-    int* sigma = reinterpret_cast<int*>(smem_raw + lay.sig_off);
-    __shared__ Cand warp_scratch[NT / 32];
-    __shared__ Cand chosen;
-    __shared__ int s_fail;
-
-    const int r0 = rank * R;
-    const int nrows = max(0, min(R, L - r0));
-    const int col_threads = L < NT ? L : NT;  // elimination: threads per row
-    const int row_groups = NT / col_threads;  // ... and rows handled at once
-    const int tc = tid % col_threads, tr = tid / col_threads;
-
-    for (size_t idx = tid; idx < (size_t)nrows * L; idx += NT) {
-        const int r = (int)(idx / L), j = (int)(idx % L);
-        M[idx] = src[(size_t)(r0 + r) * lds + j];
-    }
-    for (int q = tid; q < L; q += NT) { phys_at[q] = q; lpos[q] = q; }
-    if (tid == 0) s_fail = 0;
-    __syncthreads();
-    local_candidate(M, L, nrows, r0, lpos, 0, &cand[0], warp_scratch);
-
-    // One cluster barrier per step.  The pivot row of step k is read raw by
-    // every CTA (and scaled on the fly); its owner scales it in place at the
-    // start of step k+1, after the barrier, when nobody reads it any more and
-    // before it is eliminated like every other row.  The candidates
-    // alternate between two slots (step k reads slot k & 1): a CTA writes
-    // step k+1's candidate before the next barrier, while others may still
-    // be reading step k's; the slot it overwrites was last read in step k-1,
-    // which every CTA finished before the barrier that opened step k.
-    int steps_done = 0;
-    int prev_p = -1;
-    double prev_inv = 0.0;
-    for (int k = 0; k < L; k++) {
-        cluster.sync();  // candidates for column k published; step k-1 finished everywhere
-        if (prev_p >= 0 && prev_p / R == rank) {
-            double* rp = M + (size_t)(prev_p - r0) * L;
-            for (int j = tid; j < L; j += NT) rp[j] = (j == k - 1) ? prev_inv : rp[j] * prev_inv;
-        }
-        if (tid < 32) {
-            Cand c{-1.0, 0.0, INT_MAX, -1};
-            if (tid < C) c = *cluster.map_shared_rank(&cand[k & 1], tid);
+// Column j of this thread's rows r, r + rg, ... (< nrows), in groups of U
+// (U FMAs in flight per thread); rows skip1 and skip2 are computed but not
+// stored.  Returns the first row not done.
+template <int U>
+__device__ __forceinline__ int elim_rows(double* M, int L, int j, const double* fk, double pj, bool jk, int r, int rg,
+                                         int nrows, int skip1, int skip2) {
+    while (r + (U - 1) * rg < nrows) {
+        double f[U], b[U];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const double ok = __shfl_down_sync(0xffffffffu, c.key, off);
-                const double ov = __shfl_down_sync(0xffffffffu, c.val, off);
-                const int op = __shfl_down_sync(0xffffffffu, c.pos, off);
-                const int oph = __shfl_down_sync(0xffffffffu, c.phys, off);
-                if (better(ok, op, c.key, c.pos)) { c.key = ok; c.val = ov; c.pos = op; c.phys = oph; }
-            }
-            if (tid == 0) {
-                chosen = c;
-                const bool bad = !(c.key > 0.0) || isinf(c.key) || c.phys < 0;
-                s_fail = bad ? 1 : 0;
-                if (!bad) {
-                    const int a = phys_at[k];
-                    phys_at[k] = c.phys;
-                    phys_at[c.pos] = a;
-                    lpos[c.phys] = k;
-                    lpos[a] = c.pos;
-                    piv[k] = c.pos;
-                }
-            }
+        for (int u = 0; u < U; u++) {
+            f[u] = fk[r + u * rg];
+            b[u] = M[(size_t)(r + u * rg) * L + j];
         }
-        __syncthreads();  // pivot decided; the deferred scaling of the previous pivot row is done
-        if (s_fail) {  // identical decision in every CTA: all leave the loop together
-            if (rank == 0 && tid == 0) record_failure(info, SPIN_ERR_SINGULAR, leaf_index, k);
-            break;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int rr = r + u * rg;
+            const double nv = elim_val(f[u], b[u], pj, jk);
+            if (rr != skip1 && rr != skip2) M[(size_t)rr * L + j] = nv;
         }
-        const int p = chosen.phys;
-        const double inv = 1.0 / chosen.val;
-        const int owner = p / R;
-        for (int r = tid; r < nrows; r += NT)
-            if (r0 + r != p) fcol[r] = M[(size_t)r * L + k];
-        __syncthreads();  // every multiplier is stashed before column k is overwritten
-        // the owner's raw pivot row: its shared memory (through the cluster
-        // window), or the L2-resident work rows when they live in global memory
-        const double* rprow = ROWS_IN_SMEM ? cluster.map_shared_rank(M, owner) + (size_t)(p - owner * R) * L
-                                           : gwork + (size_t)p * L;
-        // threads tile the rows x columns block: tc columns apart along a
-        // row (coalesced), tr row groups, so that narrow leaves (L < NT)
-        // keep every thread busy; each thread reads a pivot-row entry once
-        // per column it owns
-        if (tr < row_groups) {
-            for (int j = tc; j < L; j += col_threads) {
-                const double pj = (j == k) ? inv : rprow[j] * inv;
-                for (int r = tr; r < nrows; r += row_groups) {
-                    if (r0 + r == p) continue;
-                    const double f = fcol[r];
-                    if (f == 0.0) continue;
-                    double* mr = M + (size_t)r * L;
-                    const double base = (j == k) ? 0.0 : mr[j];
-                    mr[j] = fma(-f, pj, base);
-                }
-            }
-        }
-        __syncthreads();
-        // next step's candidate goes to the other slot: a slower CTA may
-        // still be reading this step's slot through the cluster window
-        local_candidate(M, L, nrows, r0, lpos, k + 1, &cand[(k + 1) & 1], warp_scratch);
-        prev_p = p;
-        prev_inv = inv;
-        steps_done = k + 1;
+        r += U * rg;
     }
-    cluster.sync();  // no CTA still reads a peer's rows
-    if (steps_done < L) return;  // failure already recorded; X is undefined
+    return r;
+}
+
+__device__ __forceinline__ void elim_column(double* M, int L, int j, const double* fk, double pj, bool jk, int r,
+                                            int rg, int nrows, int skip1, int skip2) {
+    r = elim_rows<8>(M, L, j, fk, pj, jk, r, rg, nrows, skip1, skip2);
+    r = elim_rows<4>(M, L, j, fk, pj, jk, r, rg, nrows, skip1, skip2);
+    r = elim_rows<2>(M, L, j, fk, pj, jk, r, rg, nrows, skip1, skip2);
+    elim_rows<1>(M, L, j, fk, pj, jk, r, rg, nrows, skip1, skip2);
+}
+
+// Shared end: scale the last pivot row, undo the row interchanges as column
+// interchanges, write X.  Called after a block barrier.
+__device__ __forceinline__ void leaf_finish(double* M, int L, int R, int r0, int nrows, int rank, int prev_p,
+                                            double prev_inv, const int* lpos, const int* piv, int* sigma,
+                                            double* __restrict__ dst, int64_t ldd, int32_t* info, int leaf_index) {
+    const int tid = threadIdx.x;
     if (prev_p >= 0 && prev_p / R == rank) {  // the last pivot row is still unscaled
         double* rp = M + (size_t)(prev_p - r0) * L;
         for (int j = tid; j < L; j += NT) rp[j] = (j == L - 1) ? prev_inv : rp[j] * prev_inv;
     }
     __syncthreads();
-
     if (tid == 0) {
         for (int q = 0; q < L; q++) sigma[q] = q;
         for (int k = L - 1; k >= 0; k--) {
@@ -255,28 +212,396 @@ __device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int
     if (__syncthreads_or(nonfinite) && tid == 0) record_failure(info, SPIN_ERR_SINGULAR, leaf_index, L);
 }
 
+// Winner of step k among the C published candidates (every warp computes it).
+__device__ __forceinline__ Cand cluster_winner(const Cand* slot, int C) {
+    Cand w{0, 0.0, 0.0, INT_MAX, -1};
+    if ((int)(threadIdx.x & 31) < C) w = slot[threadIdx.x & 31];
+    return warp_argmax(w.key, w.val, w.inv, w.pos, w.phys);
+}
+
+// Row-interchange bookkeeping, by the block's last thread (the first ones
+// update column k+1 right after it).
+__device__ __forceinline__ void apply_pivot(int k, const Cand& w, int* phys_at, int* lpos, int* piv) {
+    if (threadIdx.x == NT - 1) {
+        const int a = phys_at[k];
+        phys_at[k] = w.phys;
+        phys_at[w.pos] = a;
+        lpos[w.phys] = k;
+        lpos[a] = w.pos;
+        piv[k] = w.pos;
+    }
+}
+
+__device__ __forceinline__ bool bad_pivot(const Cand& w) {
+    return w.key == 0 || w.key >= kInfBits || w.phys < 0;  // zero, infinite or NaN pivot, or none
+}
+
+// ---------------------------------------------------------------------------
+// L > 256: the pivot row is read from its owner.  Per step: cluster barrier
+// -> winner -> eliminate every row of this CTA (rows in shared memory or in
+// L2-resident global memory) -> block barrier -> candidate for column k+1,
+// published with plain cluster stores -> arrive.
 template <bool ROWS_IN_SMEM>
-__global__ void __launch_bounds__(NT, 1)
+__device__ __forceinline__ void leaf_gj_pull_body(const double* __restrict__ src, int64_t lds,
+                                                  double* __restrict__ dst, int64_t ldd, double* __restrict__ gwork,
+                                                  int L, int R, int32_t* info, int leaf_index) {
+    const int C = (int)tc::cluster_nctarank();
+    const int rank = (int)tc::cluster_ctarank();
+    const int tid = threadIdx.x;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const LeafSmemLayout lay = leaf_layout(L, R, C, ROWS_IN_SMEM, false);
+    double* M = ROWS_IN_SMEM ? reinterpret_cast<double*>(smem_raw + lay.m_off) : gwork + (size_t)rank * R * L;
+    double* fcol = reinterpret_cast<double*>(smem_raw + lay.fcol_off);  // [2][R] multipliers
+    Cand* infos = reinterpret_cast<Cand*>(smem_raw + lay.info_off);     // [2][C] candidates
+    int* phys_at = reinterpret_cast<int*>(smem_raw + lay.phys_off);
+    int* lpos = reinterpret_cast<int*>(smem_raw + lay.lpos_off);
+    int* piv = reinterpret_cast<int*>(smem_raw + lay.piv_off);
+    int* sigma = reinterpret_cast<int*>(smem_raw + lay.sig_off);
+
+    const int r0 = rank * R;
+    const int nrows = max(0, min(R, L - r0));
+    // elimination: tc columns apart along a row (coalesced), tr row groups
+    const int col_threads = L < NT ? L : NT;
+    const int row_groups = NT / col_threads;
+    const int tc = tid % col_threads, tr = tid / col_threads;
+
+    auto publish = [&](const Cand& c, int slot) {
+        if (tid < C) {
+            const uint32_t a = tc::mapa_u32(tc::smem_u32(&infos[slot * C + rank]), (uint32_t)tid);
+            tc::st_cluster_u64(a, c.key);
+            tc::st_cluster_f64(a + 8, c.val);
+            tc::st_cluster_f64(a + 16, __drcp_rn(c.val));  // inf or NaN for no candidate: never used
+            tc::st_cluster_u64(a + 24, ((uint64_t)(uint32_t)c.phys << 32) | (uint32_t)c.pos);
+        }
+    };
+
+    for (size_t idx = tid; idx < (size_t)nrows * L; idx += NT) {
+        const int r = (int)(idx / L), j = (int)(idx % L);
+        M[idx] = src[(size_t)(r0 + r) * lds + j];
+    }
+    for (int r = tid; r < nrows; r += NT) fcol[r] = src[(size_t)(r0 + r) * lds];  // step 0's multipliers
+    for (int q = tid; q < L; q += NT) { phys_at[q] = q; lpos[q] = q; }
+    __syncthreads();
+    tc::cluster_sync_all();  // every CTA of the cluster runs before the first remote write
+    publish(warp_candidate(M, L, nrows, r0, lpos, 0), 0);
+    tc::cluster_arrive_release();
+
+    cg::cluster_group cluster = cg::this_cluster();
+    int steps_done = 0;
+    int prev_p = -1;
+    double prev_inv = 0.0;
+    for (int k = 0; k < L; k++) {
+        tc::cluster_wait_acquire();  // every CTA's candidate for column k is in slot k & 1
+        const Cand w = cluster_winner(infos + (k & 1) * C, C);
+        if (bad_pivot(w)) {  // identical decision in every thread of every CTA: all leave together
+            if (rank == 0 && tid == 0) record_failure(info, SPIN_ERR_SINGULAR, leaf_index, k);
+            break;
+        }
+        apply_pivot(k, w, phys_at, lpos, piv);
+        const int p = w.phys;
+        const double inv = w.inv;
+        const int owner = p / R;
+        const double* prow = owner == rank ? M + (size_t)(p - r0) * L
+                             : ROWS_IN_SMEM ? cluster.map_shared_rank(M, owner) + (size_t)(p - owner * R) * L
+                                            : gwork + (size_t)p * L;
+        if (tr < row_groups) {
+            const double* fk = fcol + (k & 1) * R;
+            double* fn = fcol + ((k + 1) & 1) * R;
+            // the previous pivot row is scaled by its 1/pivot first, by the
+            // threads that eliminate it (its multiplier is already scaled)
+            const int pr = prev_p - r0;
+            if (prev_p >= 0 && pr >= 0 && pr < nrows && pr % row_groups == tr) {
+                double* rp = M + (size_t)pr * L;
+                for (int j = tc; j < L; j += col_threads) rp[j] = (j == k - 1) ? prev_inv : rp[j] * prev_inv;
+            }
+            const int pl = p - r0;  // the pivot row stays raw
+            for (int j = tc; j < L; j += col_threads) {
+                const double pj = (j == k) ? inv : prow[j] * inv;
+                const bool jk = j == k, jnext = j == k + 1;
+                // column k+1 also gives step k+1's multipliers (the pivot
+                // row's: its scaled entry)
+                auto store = [&](int rr, double nv) {
+                    if (rr == pl) {
+                        if (jnext) fn[rr] = pj;
+                        return;
+                    }
+                    M[(size_t)rr * L + j] = nv;
+                    if (jnext) fn[rr] = nv;
+                };
+                // groups of four rows, the next group's loads issued before
+                // this group's stores
+                int r = tr;
+                const int g4 = 4 * row_groups;
+                if (r + g4 - row_groups < nrows) {
+                    double f[4], b[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        f[u] = fk[r + u * row_groups];
+                        b[u] = M[(size_t)(r + u * row_groups) * L + j];
+                    }
+                    while (true) {
+                        double nv[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) nv[u] = elim_val(f[u], b[u], pj, jk);
+                        const int rn = r + g4;
+                        const bool more = rn + g4 - row_groups < nrows;
+                        if (more) {
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                f[u] = fk[rn + u * row_groups];
+                                b[u] = M[(size_t)(rn + u * row_groups) * L + j];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; u++) store(r + u * row_groups, nv[u]);
+                        r = rn;
+                        if (!more) break;
+                    }
+                }
+                for (; r < nrows; r += row_groups) store(r, elim_val(fk[r], M[(size_t)r * L + j], pj, jk));
+            }
+        }
+        prev_p = p;
+        prev_inv = inv;
+        steps_done = k + 1;
+        if (k + 1 == L) break;
+        __syncthreads();  // column k+1 and the position table are up to date
+        publish(warp_candidate(M, L, nrows, r0, lpos, k + 1), (k + 1) & 1);
+        tc::cluster_arrive_release();
+    }
+    tc::cluster_sync_all();  // rows read in place by peers outlive their last step
+    if (steps_done < L) return;  // failure already recorded; X is undefined
+    leaf_finish(M, L, R, r0, nrows, rank, prev_p, prev_inv, lpos, piv, sigma, dst, ldd, info, leaf_index);
+}
+
+// ---------------------------------------------------------------------------
+// L <= 256: every CTA sends its candidate for the next column, and that
+// row, into every other CTA's shared memory, completing on the receiver's
+// slot barrier (mbarrier transaction bytes: no fence, no cluster barrier),
+// and the bulk of each step's elimination runs while the data is in flight.
+// Step k, after slot k & 1's barrier:
+//   winner -> A: column k+1 of every row of this CTA (the multipliers of
+//   step k+1) -> block barrier -> candidate for column k+1 -> B: that row's
+//   step-k update, into M and this CTA's own slot -> C: every other row,
+//   every column but k+1.
+// 256 compute threads own one column each (L <= 256); A gives rows to
+// threads, one each.  A ninth warp, the messenger, computes the candidate's
+// reciprocal pivot (a ~10-operation FP64 sequence) and sends the candidate
+// (st.async), then, once the compute threads have written the row in B
+// (named barrier: they arrive, it waits), one bulk copy of the row per peer
+// (copy engine), so that neither the reciprocal nor the sending holds up C.
+// A CTA sends step k+1's candidate only after it has received step k's from
+// every CTA, so no CTA runs more than one step ahead: two slots suffice (the
+// slot a sender overwrites was last read before the receiver sent its own
+// step-k candidate), and a copy's source row, rewritten two steps later, is
+// no longer being read.  A CTA without a candidate sends its slot's stale
+// row, so that every step delivers the same byte count.
+__device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src, int64_t lds,
+                                                  double* __restrict__ dst, int64_t ldd, int L, int R, int32_t* info,
+                                                  int leaf_index) {
+    const int C = (int)tc::cluster_nctarank();
+    const int rank = (int)tc::cluster_ctarank();
+    const int tid = threadIdx.x;
+    const int mt = tid - NT;  // messenger lane, if >= 0
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const LeafSmemLayout lay = leaf_layout(L, R, C, true, true);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + lay.bar_off);    // [2] slot barriers
+    double* M = reinterpret_cast<double*>(smem_raw + lay.m_off);             // [R][L] this CTA's rows
+    double* slots = reinterpret_cast<double*>(smem_raw + lay.prow_off);      // [2][C][L] candidate rows
+    double* fcol = reinterpret_cast<double*>(smem_raw + lay.fcol_off);       // [2][R] multipliers
+    Cand* infos = reinterpret_cast<Cand*>(smem_raw + lay.info_off);          // [2][C] candidates
+    int* phys_at = reinterpret_cast<int*>(smem_raw + lay.phys_off);
+    int* lpos = reinterpret_cast<int*>(smem_raw + lay.lpos_off);
+    int* piv = reinterpret_cast<int*>(smem_raw + lay.piv_off);
+    int* sigma = reinterpret_cast<int*>(smem_raw + lay.sig_off);
+
+    const int r0 = rank * R;
+    const int nrows = max(0, min(R, L - r0));
+    const int row_groups = NT / L;  // thread (tr, j): column j, rows tr, tr + row_groups, ...
+    const int j = tid % L, tr = tid / L;
+    const bool active = mt < 0 && tr < row_groups;
+    const int LS = slot_stride(L);
+    const uint32_t row_bytes = (uint32_t)(LS * sizeof(double));  // a multiple of 16
+    const uint32_t step_bytes = (uint32_t)(C - 1) * (uint32_t)(row_bytes + sizeof(Cand));
+
+    // Send this CTA's candidate row (already in its own slot, written and
+    // fenced for the copy engine by the compute threads before a barrier the
+    // messenger has passed) to the other CTAs' slot s: one bulk copy per
+    // peer, by the messenger lanes.
+    auto send_row = [&](int s) {
+        if (mt >= 0 && mt < C && mt != rank) {
+            const uint32_t src_row = tc::smem_u32(slots + ((size_t)s * C + rank) * LS);
+            tc::bulk_copy_to_peer(tc::mapa_u32(src_row, (uint32_t)mt), src_row, row_bytes,
+                                  tc::mapa_u32(tc::smem_u32(&bars[s]), (uint32_t)mt));
+        }
+    };
+    // Send this CTA's candidate to every CTA's slot s: messenger lanes.
+    auto send_info = [&](const Cand& c, int s) {
+        if (mt >= 0 && mt < C) {
+            const double inv = __drcp_rn(c.val);  // inf or NaN for no candidate: never used
+            if (mt == rank) {
+                Cand& mine = infos[s * C + rank];
+                mine.key = c.key;
+                mine.val = c.val;
+                mine.inv = inv;
+                mine.pos = c.pos;
+                mine.phys = c.phys;
+            } else {
+                const uint32_t a = tc::mapa_u32(tc::smem_u32(&infos[s * C + rank]), (uint32_t)mt);
+                const uint32_t b = tc::mapa_u32(tc::smem_u32(&bars[s]), (uint32_t)mt);
+                tc::st_async_v2_b64(a, c.key, (uint64_t)__double_as_longlong(c.val), b);
+                tc::st_async_v2_b64(a + 16, (uint64_t)__double_as_longlong(inv),
+                                    ((uint64_t)(uint32_t)c.phys << 32) | (uint32_t)c.pos, b);
+            }
+        }
+    };
+
+    if (mt < 0) {
+        for (size_t idx = tid; idx < (size_t)nrows * L; idx += NT) {
+            const int r = (int)(idx / L), jj = (int)(idx % L);
+            M[idx] = src[(size_t)(r0 + r) * lds + jj];
+        }
+        for (int r = tid; r < nrows; r += NT) fcol[r] = src[(size_t)(r0 + r) * lds];  // step 0's multipliers
+        for (int q = tid; q < L; q += NT) { phys_at[q] = q; lpos[q] = q; }
+    }
+    // slot s's barrier completes when the C - 1 other CTAs' candidates and
+    // rows for the step using that slot have landed; armed for steps 0 and 1
+    // here, re-armed for step k + 2 once step k's wait is over
+    if (tid == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        tc::fence_mbar_init();
+        tc::mbar_arrive_expect_tx(&bars[0], step_bytes);
+        tc::mbar_arrive_expect_tx(&bars[1], step_bytes);
+    }
+    __syncthreads();
+    tc::cluster_sync_all();  // every CTA runs, its barriers armed, before the first remote write
+    {
+        const Cand c = warp_candidate(M, L, nrows, r0, lpos, 0);
+        if (active && tr == 0 && c.phys >= 0) {
+            slots[(size_t)rank * LS + j] = M[(size_t)(c.phys - r0) * L + j];
+            tc::fence_proxy_async_smem();
+        }
+        __syncthreads();
+        send_row(0);
+        send_info(c, 0);
+    }
+
+    int steps_done = 0;
+    int prev_p = -1;
+    double prev_inv = 0.0;
+    for (int k = 0; k < L; k++) {
+        const int s = k & 1;
+        const bool ok = slot_wait(&bars[s], (uint32_t)(k >> 1) & 1u);
+        if (__syncthreads_or(!ok)) {  // also makes this CTA's own slot entries visible
+            if (tid == 0) record_failure(info, SPIN_ERR_TIMEOUT, leaf_index, k);
+            break;
+        }
+        if (tid == 0 && k + 2 < L) tc::mbar_arrive_expect_tx(&bars[s], step_bytes);
+        const Cand w = cluster_winner(infos + s * C, C);
+        if (bad_pivot(w)) {  // identical decision in every thread of every CTA: all leave together
+            if (rank == 0 && tid == 0) record_failure(info, SPIN_ERR_SINGULAR, leaf_index, k);
+            break;
+        }
+        apply_pivot(k, w, phys_at, lpos, piv);
+        const int p = w.phys, pl = p - r0;  // the pivot row stays raw
+        const double inv = w.inv;
+        const double* prow = slots + ((size_t)s * C + p / R) * LS;
+        const double* fk = fcol + s * R;
+        double* fn = fcol + (s ^ 1) * R;
+        const double pj = (j == k) ? inv : prow[j] * inv;
+        // the previous pivot row is scaled by its 1/pivot (its multiplier is
+        // already scaled); column k+1 is scaled in A by the thread that
+        // updates it
+        const int pr = prev_p - r0;
+        const double pinv = prev_inv;
+        if (active && prev_p >= 0 && pr >= 0 && pr < nrows && pr % row_groups == tr && j != k + 1) {
+            double* rp = M + (size_t)pr * L + j;
+            *rp = (j == k - 1) ? pinv : *rp * pinv;
+        }
+        prev_p = p;
+        prev_inv = inv;
+        steps_done = k + 1;
+        if (k + 1 == L) {  // last step: no next candidate
+            if (active) elim_column(M, L, j, fk, pj, j == k, tr, row_groups, nrows, pl, pl);
+            break;
+        }
+        // A: column k+1, one row per thread
+        if (tid < nrows) {
+            const double pjn = prow[k + 1] * inv;
+            if (tid == pl) {
+                fn[tid] = pjn;
+            } else {
+                double b = M[(size_t)tid * L + k + 1];
+                if (tid == pr) b *= pinv;
+                const double nv = elim_val(fk[tid], b, pjn, false);
+                M[(size_t)tid * L + k + 1] = nv;
+                fn[tid] = nv;
+            }
+        }
+        __syncthreads();  // column k+1 and the position table are up to date
+        const Cand c = warp_candidate(M, L, nrows, r0, lpos, k + 1);
+        if (mt >= 0) {  // the messenger: the candidate now, its row once B is done
+            send_info(c, s ^ 1);
+            asm volatile("bar.sync 1, %0;" ::"n"(NT + kMessengers) : "memory");
+            send_row(s ^ 1);
+            continue;
+        }
+        const int rc = c.phys - r0;  // this CTA's candidate row (never p or the previous pivot row)
+        // B: the candidate row's step-k update, into M and into this CTA's own slot
+        if (active && c.phys >= 0 && rc % row_groups == tr) {
+            double v = M[(size_t)rc * L + j];
+            if (j != k + 1) {
+                v = elim_val(fk[rc], v, pj, j == k);
+                M[(size_t)rc * L + j] = v;
+            }
+            slots[((size_t)(s ^ 1) * C + rank) * LS + j] = v;
+            tc::fence_proxy_async_smem();
+        }
+        asm volatile("bar.arrive 1, %0;" ::"n"(NT + kMessengers) : "memory");  // own slot row written
+
+        // C: every other row, every column but k+1
+        if (active && j != k + 1) elim_column(M, L, j, fk, pj, j == k, tr, row_groups, nrows, pl, rc);
+    }
+    __syncthreads();
+    if (steps_done < L) return;  // failure already recorded; X is undefined
+    leaf_finish(M, L, R, r0, nrows, rank, prev_p, prev_inv, lpos, piv, sigma, dst, ldd, info, leaf_index);
+}
+
+template <bool ROWS_IN_SMEM, bool PUSH>
+__device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int64_t lds, double* __restrict__ dst,
+                                             int64_t ldd, double* __restrict__ gwork, int L, int R, int32_t* info,
+                                             int leaf_index) {
+    if constexpr (PUSH)
+        leaf_gj_push_body(src, lds, dst, ldd, L, R, info, leaf_index);
+    else
+        leaf_gj_pull_body<ROWS_IN_SMEM>(src, lds, dst, ldd, gwork, L, R, info, leaf_index);
+}
+
+template <bool ROWS_IN_SMEM, bool PUSH>
+__global__ void __launch_bounds__(PUSH ? NT + kMessengers : NT, 1)
 leaf_gj_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__ dst, int64_t ldd,
                double* __restrict__ gwork, int L, int R, int32_t* info, int leaf_index) {
-    leaf_gj_body<ROWS_IN_SMEM>(src, lds, dst, ldd, gwork, L, R, info, leaf_index);
+    leaf_gj_body<ROWS_IN_SMEM, PUSH>(src, lds, dst, ldd, gwork, L, R, info, leaf_index);
 }
 
 // Batched form: cluster blockIdx.y inverts problem z = blockIdx.y.
-template <bool ROWS_IN_SMEM>
-__global__ void __launch_bounds__(NT, 1)
+template <bool ROWS_IN_SMEM, bool PUSH>
+__global__ void __launch_bounds__(PUSH ? NT + kMessengers : NT, 1)
 leaf_gj_batched_kernel(BatchView src, BatchView dst, double* __restrict__ gwork, int64_t gwork_stride, int L, int R,
                        int32_t* info, int leaf_index) {
     const int z = blockIdx.y;
     const int64_t lds = src.ld_of(z), ldd = dst.ld_of(z);
-    leaf_gj_body<ROWS_IN_SMEM>(src.ptr(z, lds), lds, const_cast<double*>(dst.ptr(z, ldd)), ldd,
-                               ROWS_IN_SMEM ? nullptr : gwork + (int64_t)z * gwork_stride, L, R,
-                               info + (int64_t)z * INFO_WORDS, leaf_index);
+    leaf_gj_body<ROWS_IN_SMEM, PUSH>(src.ptr(z, lds), lds, const_cast<double*>(dst.ptr(z, ldd)), ldd,
+                                     ROWS_IN_SMEM ? nullptr : gwork + (int64_t)z * gwork_stride, L, R,
+                                     info + (int64_t)z * INFO_WORDS, leaf_index);
 }
 
 struct LeafConfig {
     int C, R;
-    bool smem_rows;
+    bool smem_rows, push;
     size_t smem;
 };
 
@@ -288,7 +613,7 @@ int max_cluster_size() {
     static int cached = 0;
     if (cached) return cached;
     cached = 8;
-    auto kern = leaf_gj_kernel<true>;
+    auto kern = leaf_gj_kernel<true, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) != cudaSuccess ||
         cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
@@ -297,7 +622,7 @@ int max_cluster_size() {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16, 1, 1);
     cfg.blockDim = dim3(NT, 1, 1);
-    cfg.dynamicSmemBytes = leaf_layout(512, 32, true).total;
+    cfg.dynamicSmemBytes = leaf_layout(512, 32, 16, true, false).total;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 16;
@@ -311,41 +636,55 @@ int max_cluster_size() {
     return cached;
 }
 
-// Cluster shape.  A pivot step costs a few microseconds of latency
-// (barrier, DSMEM reads) plus R*L FMAs on each CTA at ~2 FP64 FMA/clock:
-// measured per-step times at L = 128 are 17.4 / 10.6 / 7.2 / 5.6 / 5.0 us for
-// 1 / 2 / 4 / 8 / 16 CTAs.  A single inversion waits on its leaves, so it
-// takes the widest cluster (latency); a batch runs many leaves side by side,
-// so it takes the narrowest that fits shared memory (SM time).
+size_t leaf_smem_bytes(int64_t L, int C, bool rows, bool push) {
+    return leaf_layout((int)L, (int)((L + C - 1) / C), C, rows, push).total;
+}
+
+// Cluster shape.  A pivot step costs a barrier's latency plus R*L FMAs on
+// each CTA at ~2 FP64 FMA/clock: measured per-step times at L = 128 are
+// 12.2 / 7.4 / 4.5 / 3.2 / 2.9 us on 1 / 2 / 4 / 8 / 16 CTAs, and 2.0 us at
+// L = 32 on 16.  A single inversion waits on its leaves,
+// so it takes the widest cluster (latency); a batch runs many leaves side
+// by side, so it takes the narrowest that fits shared memory (SM time).
+// Rows are pushed to every CTA when L <= 256 and the slots fit.
 LeafConfig leaf_config(int64_t L, bool have_scratch, bool batched = false) {
     LeafConfig c;
     const int cmax = max_cluster_size();
+    const bool push_ok = L <= kPushMaxL;
     c.C = 1;
     if (batched) {
-        while (c.C < cmax && leaf_layout((int)L, (int)((L + c.C - 1) / c.C), true).total > kSmemBudget) c.C <<= 1;
+        while (c.C < cmax && leaf_smem_bytes(L, c.C, true, push_ok) > kSmemBudget) c.C <<= 1;
     } else {
         while (c.C < cmax && c.C < L) c.C <<= 1;
     }
     c.R = (int)((L + c.C - 1) / c.C);
-    c.smem_rows = leaf_layout((int)L, c.R, true).total <= kSmemBudget;
+    c.push = push_ok && leaf_smem_bytes(L, c.C, true, true) <= kSmemBudget;
+    c.smem_rows = c.push || leaf_smem_bytes(L, c.C, true, false) <= kSmemBudget;
     if (!c.smem_rows && !have_scratch) c.smem_rows = true;  // rejected by the caller's size check
-    c.smem = leaf_layout((int)L, c.R, c.smem_rows).total;
+    c.smem = leaf_smem_bytes(L, c.C, c.smem_rows, c.push);
     return c;
 }
 
-template <bool S>
+template <typename K>
+int prepare_leaf_kernel(K kern) {
+    SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
+    SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    return SPIN_OK;
+}
+
+template <bool S, bool P>
 int launch_leaf_impl(const double* A, int64_t lda, double* X, int64_t ldx, const LeafConfig& c, int64_t L,
                      double* scratch, int32_t* info, int leaf_index, cudaStream_t s) {
-    static bool attr_done[2] = {false, false};
-    auto kern = leaf_gj_kernel<S>;
-    if (!attr_done[S ? 1 : 0]) {
-        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
-        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        attr_done[S ? 1 : 0] = true;
+    static bool attr_done = false;
+    auto kern = leaf_gj_kernel<S, P>;
+    if (!attr_done) {
+        const int rc = prepare_leaf_kernel(kern);
+        if (rc != SPIN_OK) return rc;
+        attr_done = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)c.C, 1, 1);
-    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.blockDim = dim3(P ? NT + kMessengers : NT, 1, 1);
     cfg.dynamicSmemBytes = c.smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -359,20 +698,20 @@ int launch_leaf_impl(const double* A, int64_t lda, double* X, int64_t ldx, const
     return SPIN_OK;
 }
 
-template <bool S>
+template <bool S, bool P>
 int launch_leaf_batched_impl(const BatchView& src, const BatchView& dst, const LeafConfig& c, int64_t L,
                              double* scratch, int64_t stride, int32_t* info, int leaf_index, int count,
                              cudaStream_t s) {
-    static bool attr_done[2] = {false, false};
-    auto kern = leaf_gj_batched_kernel<S>;
-    if (!attr_done[S ? 1 : 0]) {
-        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
-        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        attr_done[S ? 1 : 0] = true;
+    static bool attr_done = false;
+    auto kern = leaf_gj_batched_kernel<S, P>;
+    if (!attr_done) {
+        const int rc = prepare_leaf_kernel(kern);
+        if (rc != SPIN_OK) return rc;
+        attr_done = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)c.C, (unsigned)count, 1);
-    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.blockDim = dim3(P ? NT + kMessengers : NT, 1, 1);
     cfg.dynamicSmemBytes = c.smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -394,9 +733,11 @@ int launch_leaf_gj_batched(const BatchView& src, const BatchView& dst, int64_t L
     if (L > kMaxLeaf || count > 65535) return SPIN_ERR_INVALID_ARG;
     const LeafConfig c = leaf_config(L, scratch_base != nullptr, true);
     if (c.smem > kSmemBudget) return SPIN_ERR_INVALID_ARG;
+    if (c.push) return launch_leaf_batched_impl<true, true>(src, dst, c, L, nullptr, 0, info, leaf_index, count, s);
     if (c.smem_rows)
-        return launch_leaf_batched_impl<true>(src, dst, c, L, nullptr, 0, info, leaf_index, count, s);
-    return launch_leaf_batched_impl<false>(src, dst, c, L, scratch_base, scratch_stride, info, leaf_index, count, s);
+        return launch_leaf_batched_impl<true, false>(src, dst, c, L, nullptr, 0, info, leaf_index, count, s);
+    return launch_leaf_batched_impl<false, false>(src, dst, c, L, scratch_base, scratch_stride, info, leaf_index,
+                                                  count, s);
 }
 
 // Leaves above 256 may not fit shared memory on every cluster shape, so
@@ -409,8 +750,9 @@ int launch_leaf_gj(const double* A, int64_t lda, double* X, int64_t ldx, int64_t
     if (L > kMaxLeaf) return SPIN_ERR_INVALID_ARG;
     const LeafConfig c = leaf_config(L, scratch != nullptr);
     if (c.smem > kSmemBudget) return SPIN_ERR_INVALID_ARG;
-    if (c.smem_rows) return launch_leaf_impl<true>(A, lda, X, ldx, c, L, nullptr, info, leaf_index, s);
-    return launch_leaf_impl<false>(A, lda, X, ldx, c, L, scratch, info, leaf_index, s);
+    if (c.push) return launch_leaf_impl<true, true>(A, lda, X, ldx, c, L, nullptr, info, leaf_index, s);
+    if (c.smem_rows) return launch_leaf_impl<true, false>(A, lda, X, ldx, c, L, nullptr, info, leaf_index, s);
+    return launch_leaf_impl<false, false>(A, lda, X, ldx, c, L, scratch, info, leaf_index, s);
 }
 
 }  // namespace spin

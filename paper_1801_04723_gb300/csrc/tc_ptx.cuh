@@ -208,6 +208,55 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
 __device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
 }
+__device__ __forceinline__ void st_cluster_f64(uint32_t cluster_addr, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(cluster_addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u64(uint32_t cluster_addr, uint64_t v) {
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(cluster_addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_nctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// Store 8 bytes into a peer CTA's shared memory and complete them on the
+// peer's mbarrier (transaction bytes): the peer's wait on that barrier sees
+// the data, with no fence on the sending side.
+__device__ __forceinline__ void st_async_b64(uint32_t cluster_addr, uint64_t v, uint32_t cluster_bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(cluster_addr),
+                 "l"(v), "r"(cluster_bar)
+                 : "memory");
+}
+// 16 bytes (16-byte aligned), same completion.
+__device__ __forceinline__ void st_async_v2_b64(uint32_t cluster_addr, uint64_t v0, uint64_t v1, uint32_t cluster_bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b64 [%0], {%1, %2}, [%3];" ::"r"(
+                     cluster_addr),
+                 "l"(v0), "l"(v1), "r"(cluster_bar)
+                 : "memory");
+}
+// Bulk copy (copy engine) from this CTA's shared memory into a peer CTA's,
+// completing on the peer's mbarrier.  Addresses 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_copy_to_peer(uint32_t cluster_dst, uint32_t cta_src, uint32_t bytes,
+                                                  uint32_t cluster_bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            cluster_dst),
+        "r"(cta_src), "r"(bytes), "r"(cluster_bar)
+        : "memory");
+}
+// Make this thread's (and, after a barrier, its block's) ordinary shared
+// memory writes visible to the copy engine.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// The two halves of cluster_sync_all, for work between them.
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t cluster_addr) {
     uint32_t v;
     asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(cluster_addr) : "memory");
