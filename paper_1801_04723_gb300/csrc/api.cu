@@ -556,24 +556,28 @@ __global__ void synth_sdd_kernel(double* A, int64_t n, uint64_t seed) {
 // levels are too small to fill 152 SMs (left), and Gauss-Jordan leaves run on
 // one cluster of at most 16 SMs at the FP64 rate plus a per-pivot latency
 // (right).  Model, per recursion node: six products (n1, n2 split), each
-//   t = launch + max(ceil(tiles / 152) * 2 * 64 * 64 * k / P_sm, 2 m n k / P_gpu)
-// with 64 x 64 tiles and P_sm = 4 flops/clock at 2.07 GHz (P_gpu = 152 P_sm,
+//   t = launch + max(ceil(tiles / 152) * 2 * TM * TM * k / P_sm, 2 m n k / P_gpu)
+// with the product kernel's TM x TM tiles (64, 32 or 16) and P_sm = 4 flops/clock at 2.07 GHz (P_gpu = 152 P_sm,
 // 1.259 TFLOP/s, the measured DFMA rate); per leaf of order L on C = min(16,
 // 2^ceil(log2 L)) CTAs with R = ceil(L / C) rows each, L pivot steps of
 //   a + b L + R L / (2 FMA/clock)     (rows in shared memory)
 //   a + b L + R L g                   (rows in L2-resident global memory)
-// a = 0.65 us, b = 15.7 ns (the leaf microbenchmark's per-step times at
-// L = 128 ... 512 on 16 CTAs) and g = 0.45 ns per element (its times at L =
-// 640 ... 2048).  It reproduces the measured sweeps at n = 4096, 8192 and
-// 16384 (leaf 64 ... 2048) within 6 %.
+// with a = 1.55 us, b = 5 ns for L <= 256 (candidate rows pushed to every
+// CTA) and a = 1.8 us, b = 14 ns above (pivot row read from its owner), and
+// g = 0.55 ns per element: the leaf microbenchmark's per-step times on 16
+// CTAs (L = 32 ... 2048).  It reproduces the measured sweeps at n = 1024,
+// 4096 and 8192 (leaf 64 ... 2048) within 8 %.
 constexpr double kModelClock = 2.07e9;
 constexpr double kModelPsm = 4.0 * kModelClock;
 constexpr double kModelPgpu = 152.0 * kModelPsm;
-constexpr double kModelLaunch = 4e-6, kModelA = 0.65e-6, kModelB = 15.7e-9, kModelG = 0.45e-9;
+constexpr double kModelLaunch = 4e-6;
+constexpr double kModelAPush = 1.55e-6, kModelBPush = 5e-9, kModelAPull = 1.8e-6, kModelBPull = 14e-9;
+constexpr double kModelG = 0.55e-9;
 
 double model_gemm(int64_t m, int64_t n, int64_t k) {
-    const double tiles = (double)((m + 63) / 64) * (double)((n + 63) / 64);
-    const double wave = std::ceil(tiles / 152.0) * 2.0 * 64.0 * 64.0 * (double)k / kModelPsm;
+    const int64_t tm = gemm_f64_tile_size(m, n, 1);
+    const double tiles = (double)((m + tm - 1) / tm) * (double)((n + tm - 1) / tm);
+    const double wave = std::ceil(tiles / 152.0) * 2.0 * (double)(tm * tm) * (double)k / kModelPsm;
     return kModelLaunch + std::max(wave, 2.0 * (double)m * (double)n * (double)k / kModelPgpu);
 }
 
@@ -581,9 +585,10 @@ double model_leaf(int64_t L) {
     int64_t C = 1;
     while (C < 16 && C < L) C <<= 1;
     const int64_t R = (L + C - 1) / C;
-    const bool smem = L <= 256 || (double)R * L * 8 + 16.0 * R + 64.0 * C + 16.0 * L <= 200.0 * 1024;
-    const double work = smem ? (double)R * L / (2.0 * kModelClock) : (double)R * L * kModelG;
-    return (double)L * (kModelA + kModelB * (double)L + work);
+    const double fma_time = (double)R * L / (2.0 * kModelClock);
+    if (L <= 256) return (double)L * (kModelAPush + kModelBPush * (double)L + fma_time);
+    const bool smem = (double)R * L * 8 + 16.0 * R + 64.0 * C + 16.0 * L <= 200.0 * 1024;
+    return (double)L * (kModelAPull + kModelBPull * (double)L + (smem ? fma_time : (double)R * L * kModelG));
 }
 
 double model_fp64(int64_t n, int64_t leaf) {

@@ -6,55 +6,70 @@
 //
 // On GB300 the FP64 pipe retires about 2 FMA per clock per SM (DFMA measured
 // at ~1.2 TFLOP/s over 152 SMs; DMMA at ~1.05-1.10), so the kernel is
-// bounded by the FP64 pipe at any reasonable tiling.  A 64x64 output tile
-// per 256-thread CTA, 4x4 register tile per thread, k-step 16 staged through
-// double-buffered shared memory, gives 16 independent FMAs per thread per
-// k-slice and needs ~0.25 B of L2 traffic per FMA -- far under any memory
-// roof.  Operands are arbitrary strided views (no alignment beyond 8 B).
+// bounded by the FP64 pipe at any reasonable tiling, and a product runs at
+// the rate of the SMs it occupies.  A 64x64 output tile per 256-thread CTA,
+// 4x4 register tile per thread, k-step 16 staged through double-buffered
+// shared memory, gives 16 independent FMAs per thread per k-slice and needs
+// ~0.25 B of L2 traffic per FMA -- far under any memory roof.  Products too
+// small to give every SM a 64x64 tile (the deep recursion levels: at n =
+// 1024 the three levels have 64, 16 and 4 such tiles) take 32x32 or 16x16
+// tiles instead.  Every output is one FMA chain over k in order, whatever
+// the tile, so the tile size never changes a result bit.  Operands are
+// arbitrary strided views (no alignment beyond 8 B).
+#include <math.h>
+#include <stdlib.h>
+
+#include <cmath>
+
 #include "common.cuh"
 
 namespace spin {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
+// One TM x TM output tile per 256-thread CTA: thread (tx, ty) of a 16 x 16
+// grid owns a (TM/16) x (TM/16) register tile.
+template <int TM>
 __device__ __forceinline__ void gemm_f64_tile(int64_t m, int64_t n, int64_t k, double alpha,
                                               const double* __restrict__ A, int64_t lda,
                                               const double* __restrict__ B, int64_t ldb, double beta,
                                               const double* C, int64_t ldc, double* D, int64_t ldd) {
-    __shared__ double As[2][BK][BM + 1];
-    __shared__ double Bs[2][BK][BN];
+    constexpr int T = TM / 16;        // outputs per thread along each side
+    constexpr int BR = NT / TM;       // B tile rows loaded per pass
+    __shared__ double As[2][BK][TM + 1];
+    __shared__ double Bs[2][BK][TM];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+    const int64_t m0 = (int64_t)blockIdx.y * TM, n0 = (int64_t)blockIdx.x * TM;
 
-    // load mapping: A tile (BM x BK): row = ty + 16*i, kk = tx; B tile (BK x BN): kr = tid/64 + 4*i, col = tid%64
+    // load mapping: A tile (TM x BK): row = ty + 16*i, kk = tx; B tile (BK x TM): kr = tid/TM + BR*i, col = tid%TM
     const int a_kk = tx;
-    const int b_col = tid & 63, b_kr = tid >> 6;
-    double ra[4], rb[4];
+    const int b_col = tid % TM, b_kr = tid / TM;
+    double ra[T], rb[T];
 
     auto load_regs = [&](int64_t k0) {
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
+        for (int i = 0; i < T; i++) {
             const int64_t r = m0 + ty + 16 * i, c = k0 + a_kk;
             ra[i] = (r < m && c < k) ? A[r * lda + c] : 0.0;
-            const int64_t kr = k0 + b_kr + 4 * i, cc = n0 + b_col;
+            const int64_t kr = k0 + b_kr + BR * i, cc = n0 + b_col;
             rb[i] = (kr < k && cc < n) ? B[kr * ldb + cc] : 0.0;
         }
     };
     auto store_smem = [&](int buf) {
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
+        for (int i = 0; i < T; i++) {
             As[buf][a_kk][ty + 16 * i] = ra[i];
-            Bs[buf][b_kr + 4 * i][b_col] = rb[i];
+            Bs[buf][b_kr + BR * i][b_col] = rb[i];
         }
     };
 
-    double acc[4][4];
+    double acc[T][T];
 #pragma unroll
-    for (int i = 0; i < 4; i++)
+    for (int i = 0; i < T; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+        for (int j = 0; j < T; j++) acc[i][j] = 0.0;
 
     const int64_t ktiles = (k + BK - 1) / BK;
     if (ktiles > 0) {
@@ -67,15 +82,15 @@ __device__ __forceinline__ void gemm_f64_tile(int64_t m, int64_t n, int64_t k, d
         if (t + 1 < ktiles) load_regs((t + 1) * BK);
 #pragma unroll
         for (int kk = 0; kk < BK; kk++) {
-            double a[4], b[4];
+            double a[T], b[T];
 #pragma unroll
-            for (int i = 0; i < 4; i++) a[i] = As[buf][kk][ty + 16 * i];
+            for (int i = 0; i < T; i++) a[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; j++) b[j] = Bs[buf][kk][tx + 16 * j];
+            for (int j = 0; j < T; j++) b[j] = Bs[buf][kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; i++)
+            for (int i = 0; i < T; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < T; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         if (t + 1 < ktiles) {
             store_smem(buf ^ 1);
@@ -84,11 +99,11 @@ __device__ __forceinline__ void gemm_f64_tile(int64_t m, int64_t n, int64_t k, d
     }
 
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
+    for (int i = 0; i < T; i++) {
         const int64_t r = m0 + ty + 16 * i;
         if (r >= m) continue;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < T; j++) {
             const int64_t c = n0 + tx + 16 * j;
             if (c >= n) continue;
             double v = alpha * acc[i][j];
@@ -98,15 +113,17 @@ __device__ __forceinline__ void gemm_f64_tile(int64_t m, int64_t n, int64_t k, d
     }
 }
 
+template <int TM>
 __global__ void __launch_bounds__(NT, 2)
 gemm_f64_kernel(int64_t m, int64_t n, int64_t k, double alpha, const double* __restrict__ A, int64_t lda,
                 const double* __restrict__ B, int64_t ldb, double beta, const double* C, int64_t ldc,
                 double* D, int64_t ldd) {
-    gemm_f64_tile(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
+    gemm_f64_tile<TM>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
 }
 
 // Batched form: problem blockIdx.z uses the views described by the BatchView
 // operands (same shape for every problem, per-problem base and leading dim).
+template <int TM>
 __global__ void __launch_bounds__(NT, 2)
 gemm_f64_batched_kernel(int64_t m, int64_t n, int64_t k, double alpha, BatchView a, BatchView b, double beta,
                         BatchView c, BatchView d) {
@@ -120,17 +137,54 @@ gemm_f64_batched_kernel(int64_t m, int64_t n, int64_t k, double alpha, BatchView
         ldc = c.ld_of(z);
         C = c.ptr(z, ldc);
     }
-    gemm_f64_tile(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, const_cast<double*>(d.ptr(z, ldd)), ldd);
+    gemm_f64_tile<TM>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, const_cast<double*>(d.ptr(z, ldd)), ldd);
+}
+
+// SPIN_F64_TILE=64|32|16 forces a tile size (for measurement); read once.
+int forced_tile() {
+    static int t = -1;
+    if (t < 0) {
+        const char* e = getenv("SPIN_F64_TILE");
+        const int v = e ? atoi(e) : 0;
+        t = (v == 64 || v == 32 || v == 16) ? v : 0;
+    }
+    return t;
 }
 
 }  // namespace
 
+// Tile size for an m x n product (count of them side by side): the one
+// whose busiest SM has the fewest FMAs, ceil(tiles / 152) * TM^2 per
+// k, larger tiles preferred unless a smaller one is at least 1.25x better
+// (a smaller tile keeps fewer FMAs in flight per thread).
+int gemm_f64_tile_size(int64_t m, int64_t n, int64_t count) {
+    const int forced = forced_tile();
+    if (forced) return forced;
+    int best = 64;
+    double best_cost = 0.0;
+    for (int tm : {64, 32, 16}) {
+        const double tiles = (double)((m + tm - 1) / tm) * (double)((n + tm - 1) / tm) * (double)count;
+        const double cost = std::ceil(tiles / 152.0) * tm * tm;
+        if (tm == 64 || cost * 1.25 <= best_cost) {
+            best = tm;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
 int launch_gemm_f64_batched(int64_t m, int64_t n, int64_t k, double alpha, const BatchView& a, const BatchView& b,
                             double beta, const BatchView& c, const BatchView& d, int count, cudaStream_t s) {
     if (m <= 0 || n <= 0 || count <= 0) return SPIN_OK;
-    dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)count);
+    const int tm = gemm_f64_tile_size(m, n, count);
+    dim3 grid((unsigned)((n + tm - 1) / tm), (unsigned)((m + tm - 1) / tm), (unsigned)count);
     if (grid.y > 65535u || grid.z > 65535u) return SPIN_ERR_INVALID_ARG;
-    gemm_f64_batched_kernel<<<grid, NT, 0, s>>>(m, n, k, alpha, a, b, beta, c, d);
+    if (tm == 64)
+        gemm_f64_batched_kernel<64><<<grid, NT, 0, s>>>(m, n, k, alpha, a, b, beta, c, d);
+    else if (tm == 32)
+        gemm_f64_batched_kernel<32><<<grid, NT, 0, s>>>(m, n, k, alpha, a, b, beta, c, d);
+    else
+        gemm_f64_batched_kernel<16><<<grid, NT, 0, s>>>(m, n, k, alpha, a, b, beta, c, d);
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
 }
@@ -139,9 +193,15 @@ int launch_gemm_f64(int64_t m, int64_t n, int64_t k, double alpha, const double*
                     const double* B, int64_t ldb, double beta, const double* C, int64_t ldc, double* D,
                     int64_t ldd, cudaStream_t s) {
     if (m <= 0 || n <= 0) return SPIN_OK;
-    dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM));
+    const int tm = gemm_f64_tile_size(m, n, 1);
+    dim3 grid((unsigned)((n + tm - 1) / tm), (unsigned)((m + tm - 1) / tm));
     if (grid.y > 65535u) return SPIN_ERR_INVALID_ARG;
-    gemm_f64_kernel<<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
+    if (tm == 64)
+        gemm_f64_kernel<64><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
+    else if (tm == 32)
+        gemm_f64_kernel<32><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
+    else
+        gemm_f64_kernel<16><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
 }

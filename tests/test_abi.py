@@ -109,14 +109,17 @@ def test_pretransform_workspace(L):
 def test_cost_model_shape(L):
     """The model of the plain path (spin_model_seconds): never faster than the
     FP64 peak allows, U-shaped in the leaf order with the optimum of the
-    measured sweeps (256 at n = 8192 and 16384), growing like n^3, and the
-    untuned default leaf is its optimum."""
+    measured sweeps (a flat bottom at 64-128 at n = 4096 and 8192, within 1 %
+    of each other), growing like n^3, and the untuned default leaf is its
+    optimum."""
     peak = 152 * 4 * 2.07e9
     for n in (8192, 16384):
         t = {Lf: spin.model_seconds(n, Lf) for Lf in (64, 128, 256, 512, 1024, 2048)}
         assert all(v >= 2.0 * n ** 3 / peak for v in t.values())
-        assert t[64] > t[128] > t[256] < t[512] < t[1024] < t[2048]
-        assert spin.default_leaf(n) == 256
+        best = min(t, key=t.get)
+        assert best in (64, 128)
+        assert t[best] < t[256] < t[512] < t[1024] < t[2048]
+        assert spin.default_leaf(n) == best
     r = spin.model_seconds(16384, 256) / spin.model_seconds(8192, 256)
     assert 7.0 < r < 8.0
     assert spin.model_seconds(100, 64, precision="bf16x3") == -1.0
