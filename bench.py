@@ -691,7 +691,7 @@ def run_serve(args, w: dict):
         for tk in list(pending):
             got = srv.poll(tk, discard=True)
             if got is not None:
-                pending.pop(tk)
+                got[1]["n"] = pending.pop(tk)
                 done.append(got[1])
 
     with ClockSampler(local) as clk:
@@ -723,6 +723,12 @@ def run_serve(args, w: dict):
     srv.close()
     lat = sorted(r["latency_ms"] for r in done)
     bad = sum(1 for r in done if r["status"] != 0)
+    failed_status = {}
+    for r in done:
+        if r["status"] != 0:
+            failed_status[str(r["status"])] = failed_status.get(str(r["status"]), 0) + 1
+    failed_detail = [{k: r[k] for k in ("status", "n", "precision", "refine_iters", "rel_residual")}
+                     for r in done if r["status"] != 0][:20]
 
     def pct(q):
         return lat[min(len(lat) - 1, int(q * len(lat)))] if lat else None
@@ -740,7 +746,8 @@ def run_serve(args, w: dict):
         "offered_tflops": flops_done / args.serve_seconds / 1e12,
         "served_tflops": flops_done / makespan / 1e12,
         "drain_s_after_last_arrival": makespan - t_last_arrival,
-        "failed": bad, "shed": shed, "served": len(done), "peak_running": st["peak_running"],
+        "failed": bad, "failed_status": failed_status, "failed_detail": failed_detail,
+        "shed": shed, "served": len(done), "peak_running": st["peak_running"], "deferred": st["deferred"],
         "clocks": clk.summary(),
         "e2e": {"value": len(done) / makespan, "unit": "req/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                 "how": "requests submitted from device memory; results left on the device"},

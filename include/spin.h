@@ -221,6 +221,10 @@ typedef struct spin_serve_stats_t {
     int32_t running, peak_running;
     size_t bytes_in_use;
     uint64_t shed;            /* submits refused by max_queued_bytes                   */
+    uint64_t deferred;        /* admissions put back in the queue because device memory
+                                 could not be allocated (retried after another request
+                                 completed; a request fails with SPIN_ERR_OOM only when
+                                 it cannot be allocated while running alone)          */
 } spin_serve_stats_t;
 
 typedef struct spin_server spin_server;
@@ -245,7 +249,7 @@ int spin_serve_submit(spin_server* sv, const double* A, int64_t lda, int64_t n, 
 int spin_serve_poll(spin_server* sv, uint64_t ticket, double* X, int64_t ldx, spin_result* r);
 
 /* Counters: submitted, completed, rejected, queued, running, peak running,
- * bytes held, shed. */
+ * bytes held, shed, deferred. */
 int spin_serve_stats(spin_server* sv, spin_serve_stats_t* st);
 
 /* Stop the slots (running requests finish), free everything. */

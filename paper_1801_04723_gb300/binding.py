@@ -106,6 +106,7 @@ class ServeStats(ctypes.Structure):
         ("peak_running", ctypes.c_int32),
         ("bytes_in_use", ctypes.c_size_t),
         ("shed", ctypes.c_uint64),
+        ("deferred", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:

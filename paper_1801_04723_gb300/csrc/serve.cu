@@ -10,6 +10,7 @@
 // client polls it.  Memory comes from a stream-ordered pool
 // (cudaMallocAsync), so admission does not synchronise the device.
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <chrono>
@@ -46,6 +47,7 @@ struct Request {
     spin_info info{};
     int status = SPIN_ERR_BUSY;
     bool done = false;
+    int deferrals = 0;      // times put back in the queue for lack of device memory
 };
 
 }  // namespace
@@ -68,12 +70,26 @@ struct spin_server {
     std::vector<cudaStream_t> hi_streams;    // per slot, high priority (small requests)
     cudaStream_t copy_stream = nullptr;
     // counters
-    uint64_t submitted = 0, completed = 0, rejected = 0, shed = 0;
+    uint64_t submitted = 0, completed = 0, rejected = 0, shed = 0, deferred = 0;
+    // test hook (SPIN_SERVE_INJECT_OOM="ticket:count", read at creation): the
+    // first count allocation attempts of that ticket fail as if the device
+    // were out of memory
+    uint64_t inject_ticket = 0;
+    int inject_left = 0;
     int running = 0, peak_running = 0;
+    // a request whose memory could not be allocated waits at the head of the
+    // queue until another request completes (completed > retry_after)
+    uint64_t retry_after = 0;
+    bool retry_wait = false;
 };
 
 namespace spin {
 namespace {
+
+bool verbose() {
+    static const bool v = getenv("SPIN_VERBOSE") != nullptr;
+    return v;
+}
 
 size_t request_workspace(int64_t n, int precision, double tol) {
     spin_opts o = spin_opts_default();
@@ -91,12 +107,14 @@ void worker_loop(spin_server* sv, int slot) {
             sv->cv.wait(lk, [&] {
                 if (sv->stop) return true;
                 if (sv->queue.empty()) return false;
+                if (sv->retry_wait && sv->completed <= sv->retry_after && sv->running > 0) return false;
                 const auto& h = sv->queue.front();
                 return sv->in_use + h->footprint_run + h->footprint_keep <= sv->cfg.hbm_budget_bytes;
             });
             if (sv->stop) return;
             rq = sv->queue.front();
             sv->queue.pop_front();
+            sv->retry_wait = false;
             sv->queued_a_bytes -= (size_t)rq->n * (size_t)rq->n * sizeof(double);
             sv->in_use += rq->footprint_run + rq->footprint_keep;
             sv->running++;
@@ -110,16 +128,68 @@ void worker_loop(spin_server* sv, int slot) {
         const size_t ws_bytes = request_workspace(n, rq->precision, rq->tol);
         double* Ad = nullptr;
         void* ws = nullptr;
+        // The budget bounds what the server holds, but the device is shared
+        // (the client's own tensors, other processes, and blocks the pool
+        // keeps for reuse), so an allocation can still fail: release this
+        // request's blocks, return the pool's unused memory to the device and
+        // try once more; failing that, put the request back at the head of
+        // the queue until another request completes, and fail it only when
+        // nothing else is running.
+        auto alloc_all = [&]() -> bool {
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                if (rq->ticket == sv->inject_ticket && sv->inject_left > 0) {
+                    sv->inject_left--;
+                    return false;
+                }
+            }
+            if (cudaMallocFromPoolAsync((void**)&rq->X, nn, sv->pool, s) != cudaSuccess) return false;
+            if (ws_bytes && cudaMallocFromPoolAsync(&ws, ws_bytes, sv->pool, s) != cudaSuccess) return false;
+            if (!rq->a_on_device && cudaMallocFromPoolAsync((void**)&Ad, nn, sv->pool, s) != cudaSuccess) return false;
+            return true;
+        };
+        auto release_all = [&]() {
+            cudaGetLastError();
+            if (rq->X) cudaFreeAsync(rq->X, s);
+            if (ws) cudaFreeAsync(ws, s);
+            if (Ad) cudaFreeAsync(Ad, s);
+            rq->X = nullptr;
+            ws = nullptr;
+            Ad = nullptr;
+            cudaStreamSynchronize(s);
+        };
         int rc = SPIN_OK;
-        if (cudaMallocFromPoolAsync((void**)&rq->X, nn, sv->pool, s) != cudaSuccess) rc = SPIN_ERR_OOM;
-        if (rc == SPIN_OK && ws_bytes && cudaMallocFromPoolAsync(&ws, ws_bytes, sv->pool, s) != cudaSuccess)
-            rc = SPIN_ERR_OOM;
+        if (!alloc_all()) {
+            release_all();
+            cudaMemPoolTrimTo(sv->pool, 0);
+            if (!alloc_all()) {
+                release_all();
+                bool deferred = false;
+                {
+                    std::lock_guard<std::mutex> lk(sv->mu);
+                    if (sv->running > 1 && rq->deferrals < 1000) {
+                        rq->deferrals++;
+                        sv->deferred++;
+                        sv->in_use -= rq->footprint_run + rq->footprint_keep;
+                        sv->running--;
+                        sv->queued_a_bytes += nn;
+                        sv->queue.push_front(rq);
+                        sv->retry_wait = true;
+                        sv->retry_after = sv->completed;
+                        deferred = true;
+                    }
+                }
+                if (deferred) {
+                    sv->cv.notify_all();
+                    continue;
+                }
+                rc = SPIN_ERR_OOM;
+            }
+        }
         const double* Ause = rq->A;
         int64_t lda = rq->lda;
         if (rc == SPIN_OK && !rq->a_on_device) {
-            if (cudaMallocFromPoolAsync((void**)&Ad, nn, sv->pool, s) != cudaSuccess) rc = SPIN_ERR_OOM;
-            if (rc == SPIN_OK &&
-                cudaMemcpy2DAsync(Ad, n * sizeof(double), rq->A, rq->lda * sizeof(double), n * sizeof(double), n,
+            if (cudaMemcpy2DAsync(Ad, n * sizeof(double), rq->A, rq->lda * sizeof(double), n * sizeof(double), n,
                                   cudaMemcpyHostToDevice, s) != cudaSuccess)
                 rc = SPIN_ERR_CUDA;
             Ause = Ad;
@@ -135,6 +205,9 @@ void worker_loop(spin_server* sv, int slot) {
             rc = spin_invert_ex(Ause, lda, rq->X, n, n, &o, &rq->info, (spin_stream_t)s);
             if (rc == SPIN_OK || rc == SPIN_ERR_SINGULAR || rc == SPIN_ERR_NOT_CONVERGED) rc = rq->info.status;
         }
+        if ((rc == SPIN_ERR_CUDA || rc == SPIN_ERR_OOM) && verbose())
+            fprintf(stderr, "spin serve: request %llu (n = %lld) failed with status %d: %s\n",
+                    (unsigned long long)rq->ticket, (long long)n, rc, spin_last_error());
         if (Ad) cudaFreeAsync(Ad, s);
         if (ws) cudaFreeAsync(ws, s);
         cudaStreamSynchronize(s);
@@ -174,6 +247,14 @@ extern "C" int spin_serve_create(const spin_serve_cfg* cfg, spin_server** out) {
         cudaGetLastError();
         delete sv;
         return SPIN_ERR_CUDA;
+    }
+    if (const char* e = getenv("SPIN_SERVE_INJECT_OOM")) {
+        unsigned long long t = 0;
+        int c = 0;
+        if (sscanf(e, "%llu:%d", &t, &c) == 2) {
+            sv->inject_ticket = t;
+            sv->inject_left = c;
+        }
     }
     uint64_t keep = cfg->hbm_budget_bytes;  // keep freed blocks for reuse up to the budget
     cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
@@ -290,6 +371,7 @@ extern "C" int spin_serve_stats(spin_server* sv, spin_serve_stats_t* st) {
     st->peak_running = sv->peak_running;
     st->bytes_in_use = sv->in_use;
     st->shed = sv->shed;
+    st->deferred = sv->deferred;
     return SPIN_OK;
 }
 

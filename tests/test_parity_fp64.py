@@ -297,3 +297,44 @@ def test_cost_model_against_measured_sweep(spin):
     assert ms[pick] <= 1.05 * ms[best]
     for L in cands:
         assert abs(spin.model_seconds(n, L) * 1e3 / ms[L] - 1.0) < 0.25, (L, ms[L])
+
+
+TILE_SCRIPT = r"""
+import sys
+import numpy as np, torch
+import paper_1801_04723_gb300 as s
+from paper_1801_04723_gb300 import inputs
+s.lib()
+out = {}
+for n, leaf in [(700, 64), (1024, 128), (333, 32)]:
+    A = torch.from_numpy(inputs.sdd(n, seed=n)).to("cuda:0")
+    X, info = s.invert(A, leaf=leaf)
+    torch.cuda.synchronize()
+    assert info["status"] == 0
+    out[f"{n}_{leaf}"] = X.cpu().numpy()
+np.savez(sys.argv[1], **out)
+print("TILE-OK")
+"""
+
+
+def test_product_tile_size_changes_no_bit(spin, tmp_path):
+    """The FP64 products choose 64-, 32- or 16-row tiles by how well they
+    fill the SMs (SPIN_F64_TILE forces one, read once per process); every
+    output is one FMA chain over k in order, so inversions are bit-identical
+    whichever tile runs."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    results = {}
+    for tile in ("", "64", "32", "16"):
+        env = dict(os.environ, SPIN_F64_TILE=tile)
+        path = str(tmp_path / f"x{tile or 'auto'}.npz")
+        r = subprocess.run([sys.executable, "-c", TILE_SCRIPT, path], cwd=root, env=env, capture_output=True,
+                           text=True, timeout=600)
+        assert r.returncode == 0 and "TILE-OK" in r.stdout, r.stdout + r.stderr
+        results[tile] = dict(np.load(path))
+    for tile in ("64", "32", "16"):
+        for key, X in results[""].items():
+            np.testing.assert_array_equal(results[tile][key], X, err_msg=f"tile {tile}, {key}")

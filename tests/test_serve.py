@@ -110,3 +110,55 @@ def test_serve_load_shedding(spin):
     while srv.poll(tb, discard=True) is None:
         time.sleep(0.001)
     srv.close()
+
+
+DEFER_SCRIPT = r"""
+import time
+import numpy as np, torch
+import paper_1801_04723_gb300 as s
+from paper_1801_04723_gb300 import inputs
+s.lib()
+srv = s.Server(hbm_budget_bytes=4 << 30, max_slots=2)
+big = torch.from_numpy(inputs.sdd(4096, seed=1)).cuda()
+small = inputs.sdd(300, seed=2)
+torch.cuda.synchronize()
+t1 = srv.submit(big, precision="fp64")  # ticket 1: ~0.1 s of work
+for _ in range(5000):  # bounded wait until it runs
+    if srv.stats()["running"] == 1:
+        break
+    time.sleep(0.001)
+t2 = srv.submit(small, precision="fp64")  # ticket 2: its first two allocation attempts fail
+assert (t1, t2) == (1, 2)
+out = {}
+for t in (t1, t2):
+    for _ in range(600000):
+        got = srv.poll(t, discard=(t == t1))
+        if got is not None:
+            break
+        time.sleep(0.0005)
+    out[t] = got
+st = srv.stats()
+srv.close()
+assert out[t1][1]["status"] == 0 and out[t2][1]["status"] == 0, (out[t1][1], out[t2][1])
+assert st["deferred"] == 1, st
+alone, _ = s.invert(torch.from_numpy(small).cuda())
+np.testing.assert_array_equal(out[t2][0], alone.cpu().numpy())
+print("DEFER-OK")
+"""
+
+
+def test_serve_defers_on_allocation_failure(spin):
+    """A request whose device memory cannot be allocated while another one
+    runs is put back at the head of the queue and admitted again when that
+    one completes, instead of failing.  The allocation failures are made on
+    the host (SPIN_SERVE_INJECT_OOM=ticket:count makes the first count
+    attempts of that ticket fail); the result equals the request run alone."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SPIN_SERVE_INJECT_OOM="2:2")
+    r = subprocess.run([sys.executable, "-c", DEFER_SCRIPT], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and "DEFER-OK" in r.stdout, r.stdout + r.stderr
