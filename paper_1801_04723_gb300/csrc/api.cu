@@ -195,10 +195,22 @@ int leaf_prof(Run& r, int depth, const double* A, int64_t lda, double* X, int64_
 // (and for small products in mixed mode); in mixed mode bf16x3 on the
 // tensor cores, or FP64-class digit slices for the Schur complement of the
 // top fp64_levels levels.
+// Smallest m and n a mixed-mode product takes to the tensor cores
+// (SPIN_TC_MIN overrides it, for measurement; read once).
+int64_t tc_min() {
+    static int64_t v = -1;
+    if (v < 0) {
+        const char* e = getenv("SPIN_TC_MIN");
+        const long long x = e ? atoll(e) : 0;
+        v = x > 0 ? (int64_t)x : kTcMin;
+    }
+    return v;
+}
+
 int level_gemm(Run& r, int depth, bool schur, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
                int64_t lda, const double* B, int64_t ldb, double beta, const double* C, int64_t ldc, double* D,
                int64_t ldd) {
-    if (r.precision == SPIN_FP64 || m < kTcMin || n < kTcMin || k < 64)
+    if (r.precision == SPIN_FP64 || m < tc_min() || n < tc_min() || k < 64)
         return gemm_f64_prof(r, depth, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
     const double f = 2.0 * (double)m * (double)n * (double)k;
     SplitPlan sp;

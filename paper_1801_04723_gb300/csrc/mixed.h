@@ -10,7 +10,14 @@ namespace spin {
 
 constexpr int kSchurSlices = 7;  // digit slices of the FP64-class Schur complements
 constexpr int kLevelSlices = 4;  // digit slices of the level products in SPIN_MIXED_DIGITS
-constexpr int64_t kTcMin = 128;  // products smaller than this in m or n stay in FP64
+// Products smaller than this in m or n stay in FP64: below it a product has
+// a handful of 128 x 256 tiles and a short K, so the tensor-core path (two
+// operand splits and a launch that fills a few SMs) costs more than the FP64
+// kernel, whose small tiles fill the SMs.  Measured single inversions, bf16x3
+// to 1e-10: threshold 128 -> 384 took n = 512 / 1024 / 2048 / 4096 from
+// 3.29 / 6.10 / 13.1 / 30.0 ms to 1.82 / 4.57 / 10.4 / 24.7 ms (512 gives the
+// same times; 384 keeps orders like 777 on the tensor cores).
+constexpr int64_t kTcMin = 384;
 
 // Slice-pair schedules of the tensor-core product forms (fill pa, pb, pg,
 // num_pairs and the exactness fields of p).

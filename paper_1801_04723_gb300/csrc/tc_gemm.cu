@@ -925,13 +925,24 @@ __global__ void col_exp_kernel(Src src, int rows, int cols, int rows_per_block, 
     const int r0 = blockIdx.y * rows_per_block;
     const int r1 = min(rows, r0 + rows_per_block);
     int m = 0;
-    double ss = 0.0;
-    if (c < cols)
-        for (int r = r0; r < r1; r++) {
+    double ss4[4] = {0.0, 0.0, 0.0, 0.0};  // four FMA chains: an FP64 operation takes ~250 cycles here
+    if (c < cols) {
+        int r = r0;
+        for (; r + 3 < r1; r += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const double v = src.row(z, r + u)[c];
+                m = max(m, exp_field(v));
+                if (sumsq) ss4[u] = fma(v, v, ss4[u]);
+            }
+        }
+        for (; r < r1; r++) {
             const double v = src.row(z, r)[c];
             m = max(m, exp_field(v));
-            if (sumsq) ss = fma(v, v, ss);
+            if (sumsq) ss4[0] = fma(v, v, ss4[0]);
         }
+    }
+    double ss = (ss4[0] + ss4[1]) + (ss4[2] + ss4[3]);
     if (c < cols && m > 0) atomicMax(&ex[z * exs + c], m);
     if (sumsq) {
 #pragma unroll
@@ -1203,7 +1214,11 @@ int split_digits(Src src, int rows, int cols, bool transpose, int nslices, int* 
     } else {
         const int64_t plane = (int64_t)cols * ldd, dzs = nslices * plane, nex = (int64_t)cols * count;
         fill_int_kernel<<<(unsigned)((nex + 255) / 256), 256, 0, s>>>(ex, nex, 0);
-        const int rpb = 256;
+        // rows per block: enough blocks to cover the SMs at small orders,
+        // at most 256 (fewer atomics at large ones)
+        const int64_t col_blocks = (int64_t)((cols + 255) / 256) * count;
+        int rpb = (int)std::min<int64_t>(256, std::max<int64_t>(16, (int64_t)rows * col_blocks / 608));
+        rpb = (rpb + 7) & ~7;
         const dim3 g1((unsigned)((cols + 255) / 256), (unsigned)((rows + rpb - 1) / rpb), (unsigned)count);
         col_exp_kernel<Src><<<g1, 256, 0, s>>>(src, rows, cols, rpb, ex, cols, sumsq, sss);
         col_exp_finish_kernel<<<(unsigned)((nex + 255) / 256), 256, 0, s>>>(ex, nex);
