@@ -14,24 +14,25 @@
 // CTAs (C <= 16) whose rows stay put: every CTA owns R = ceil(L/C) rows in
 // shared memory when they fit (global memory, L2-resident, otherwise).  Row
 // interchanges are bookkeeping only (position <-> physical row tables
-// replicated in every CTA).  A pivot step is latency-bound at these sizes,
-// so each step has one cluster barrier, one block barrier and no remote
-// read on its critical path:
-//   wait (cluster barrier k) -> every warp reduces the C candidates that the
-//   CTAs pushed into its shared memory (redux.sync argmax) -> eliminate this
-//   CTA's rows with the pivot row -> block barrier -> every warp finds this
-//   CTA's candidate for column k+1 -> push it (and, for L <= 256, its whole
-//   row) into every peer's shared memory -> arrive (cluster barrier k+1).
-// For L > 256 the pushed rows would not fit, so the pivot row is read from
-// its owner (distributed shared memory or the L2-resident work rows).
-// Candidate and row slots alternate between two buffers: a CTA writes step
-// k+1's slot while a slower peer may still read step k's; the slot it
-// overwrites was last read in step k-1, which every CTA finished before it
-// arrived at barrier k.  The multipliers of step k+1 (column k+1 after step
-// k) are written to a second buffer by the threads that compute them, so no
-// thread reads a column while another overwrites it.  The pivot row of step
-// k is left raw; its scaling by 1/pivot is folded into step k+1's update of
-// that row.  No spin-wait anywhere: both barriers are hardware barriers.
+// replicated in every CTA).  A pivot step is latency-bound at these sizes
+// (an FP64 operation takes ~250 cycles on this part), so a step keeps
+// remote reads, fences and FP64 work off its critical path:
+//  - the pivot search compares the bit patterns of |a_ik| as integers
+//    (redux.sync argmax), and each candidate's reciprocal is computed once,
+//    by the CTA that publishes it;
+//  - every CTA publishes its candidate for the next column into every other
+//    CTA's shared memory, double-buffered by step parity (a CTA writes step
+//    k+1's slot while a slower one may still read step k's; the slot it
+//    overwrites was last read in step k-1);
+//  - the multipliers of step k+1 (column k+1 after step k) go to a second
+//    buffer, written by the threads that compute them;
+//  - the pivot row of step k is left raw; its scaling by 1/pivot is folded
+//    into step k+1's update of that row.
+// Two forms (leaf_gj_push_body, leaf_gj_pull_body below): for L <= 256 the
+// candidate rows travel with the candidates (st.async and bulk copies that
+// complete on per-slot mbarriers, with the bulk of each step overlapping the
+// exchange); above, the pivot row is read from its owner and a step ends at
+// a cluster barrier.
 #include <cooperative_groups.h>
 #include <limits.h>
 
