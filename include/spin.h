@@ -393,6 +393,14 @@ int spin_gemm_ozaki(int64_t m, int64_t n, int64_t k, double alpha,
  * bounded device-side wait gave up. */
 int spin_take_device_error(spin_stream_t stream);
 
+/* Test hook for the leaf's bounded exchange waits: inverts the identity of
+ * order L (2..256, the pushed-row leaf form on its widest cluster) with the
+ * CTA of rank mute_rank sending nothing and every wait limited to limit_ms
+ * (0 < limit_ms <= 4000).  The waits run out, the kernel leaves without a
+ * fault or a hang, and the leaf's status is returned: SPIN_ERR_TIMEOUT.
+ * SPIN_ERR_INVALID_ARG for a bad order, rank or limit. */
+int spin_test_leaf_timeout(int64_t L, int mute_rank, double limit_ms);
+
 /* ---------------------------------------------------------------------
  * Instrumentation: the paper times each method of the recursion
  * separately (Sec. 5, Table 3: leafNode, multiply, subtract, ...).  With

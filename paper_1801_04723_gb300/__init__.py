@@ -22,6 +22,7 @@ from .binding import (  # noqa: F401
     gemm_bf16x3,
     gemm_ozaki,
     take_device_error,
+    leaf_exchange_timeout,
     invert,
     invert_host,
     invert_noalloc,

@@ -194,6 +194,8 @@ def lib():
         L.spin_autotune_leaf.restype = ctypes.c_int
         L.spin_take_device_error.argtypes = [vp]
         L.spin_take_device_error.restype = ctypes.c_int
+        L.spin_test_leaf_timeout.argtypes = [i64, ctypes.c_int, ctypes.c_double]
+        L.spin_test_leaf_timeout.restype = ctypes.c_int
         L.spin_invert_noalloc.argtypes = [vp, vp, i64, i64, ctypes.c_int, vp]
         L.spin_invert_noalloc.restype = ctypes.c_int
         _lib = L
@@ -446,6 +448,11 @@ def gemm_ozaki(A, B, *, slices=7, alpha=1.0, beta=0.0, C=None, out=None, add_ide
 
 def take_device_error(stream=None) -> int:
     return int(lib().spin_take_device_error(_stream(stream)))
+
+
+def leaf_exchange_timeout(order: int, mute_rank: int, limit_ms: float) -> int:
+    """Status of a leaf whose CTA mute_rank sends nothing (spin_test_leaf_timeout)."""
+    return int(lib().spin_test_leaf_timeout(int(order), int(mute_rank), float(limit_ms)))
 
 
 def invert_noalloc(A, *, leaf: int = 0, out=None, stream=None):

@@ -36,6 +36,8 @@
 #include <cooperative_groups.h>
 #include <limits.h>
 
+#include <vector>
+
 #include "common.cuh"
 #include "tc_ptx.cuh"
 
@@ -131,12 +133,20 @@ __device__ __forceinline__ Cand warp_candidate(const double* M, int L, int nrows
 // Bounded wait for a slot barrier (a step takes microseconds; the limit
 // only turns a broken exchange into an error instead of a hang).
 constexpr uint64_t kLeafWaitLimitNs = 4000000000ull;
-__device__ __forceinline__ bool slot_wait(uint64_t* bar, uint32_t parity) {
+
+// Exchange settings of the pushed-row form: the wait limit, and (tests
+// only) a CTA that sends nothing, so that the others' waits run out.
+struct LeafWait {
+    uint64_t limit_ns = kLeafWaitLimitNs;
+    int mute_rank = -1;
+};
+
+__device__ __forceinline__ bool slot_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
     if (tc::mbar_try_wait_cluster(bar, parity)) return true;
     const uint64_t t0 = tc::globaltimer_ns();
     for (uint32_t spins = 1;; spins++) {
         if (tc::mbar_try_wait_cluster(bar, parity)) return true;
-        if ((spins & 63u) == 0 && tc::globaltimer_ns() - t0 > kLeafWaitLimitNs) return false;
+        if ((spins & 63u) == 0 && tc::globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -400,7 +410,7 @@ __device__ __forceinline__ void leaf_gj_pull_body(const double* __restrict__ src
 // row, so that every step delivers the same byte count.
 __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src, int64_t lds,
                                                   double* __restrict__ dst, int64_t ldd, int L, int R, int32_t* info,
-                                                  int leaf_index) {
+                                                  int leaf_index, LeafWait lw) {
     const int C = (int)tc::cluster_nctarank();
     const int rank = (int)tc::cluster_ctarank();
     const int tid = threadIdx.x;
@@ -431,8 +441,9 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
     // fenced for the copy engine by the compute threads before a barrier the
     // messenger has passed) to the other CTAs' slot s: one bulk copy per
     // peer, by the messenger lanes.
+    const bool muted = rank == lw.mute_rank;
     auto send_row = [&](int s) {
-        if (mt >= 0 && mt < C && mt != rank) {
+        if (mt >= 0 && mt < C && mt != rank && !muted) {
             const uint32_t src_row = tc::smem_u32(slots + ((size_t)s * C + rank) * LS);
             tc::bulk_copy_to_peer(tc::mapa_u32(src_row, (uint32_t)mt), src_row, row_bytes,
                                   tc::mapa_u32(tc::smem_u32(&bars[s]), (uint32_t)mt));
@@ -449,7 +460,7 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
                 mine.inv = inv;
                 mine.pos = c.pos;
                 mine.phys = c.phys;
-            } else {
+            } else if (!muted) {
                 const uint32_t a = tc::mapa_u32(tc::smem_u32(&infos[s * C + rank]), (uint32_t)mt);
                 const uint32_t b = tc::mapa_u32(tc::smem_u32(&bars[s]), (uint32_t)mt);
                 tc::st_async_v2_b64(a, c.key, (uint64_t)__double_as_longlong(c.val), b);
@@ -495,7 +506,7 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
     double prev_inv = 0.0;
     for (int k = 0; k < L; k++) {
         const int s = k & 1;
-        const bool ok = slot_wait(&bars[s], (uint32_t)(k >> 1) & 1u);
+        const bool ok = slot_wait(&bars[s], (uint32_t)(k >> 1) & 1u, lw.limit_ns);
         if (__syncthreads_or(!ok)) {  // also makes this CTA's own slot entries visible
             if (tid == 0) record_failure(info, SPIN_ERR_TIMEOUT, leaf_index, k);
             break;
@@ -574,9 +585,9 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
 template <bool ROWS_IN_SMEM, bool PUSH>
 __device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int64_t lds, double* __restrict__ dst,
                                              int64_t ldd, double* __restrict__ gwork, int L, int R, int32_t* info,
-                                             int leaf_index) {
+                                             int leaf_index, LeafWait lw) {
     if constexpr (PUSH)
-        leaf_gj_push_body(src, lds, dst, ldd, L, R, info, leaf_index);
+        leaf_gj_push_body(src, lds, dst, ldd, L, R, info, leaf_index, lw);
     else
         leaf_gj_pull_body<ROWS_IN_SMEM>(src, lds, dst, ldd, gwork, L, R, info, leaf_index);
 }
@@ -584,20 +595,20 @@ __device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int
 template <bool ROWS_IN_SMEM, bool PUSH>
 __global__ void __launch_bounds__(PUSH ? NT + kMessengers : NT, 1)
 leaf_gj_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__ dst, int64_t ldd,
-               double* __restrict__ gwork, int L, int R, int32_t* info, int leaf_index) {
-    leaf_gj_body<ROWS_IN_SMEM, PUSH>(src, lds, dst, ldd, gwork, L, R, info, leaf_index);
+               double* __restrict__ gwork, int L, int R, int32_t* info, int leaf_index, LeafWait lw) {
+    leaf_gj_body<ROWS_IN_SMEM, PUSH>(src, lds, dst, ldd, gwork, L, R, info, leaf_index, lw);
 }
 
 // Batched form: cluster blockIdx.y inverts problem z = blockIdx.y.
 template <bool ROWS_IN_SMEM, bool PUSH>
 __global__ void __launch_bounds__(PUSH ? NT + kMessengers : NT, 1)
 leaf_gj_batched_kernel(BatchView src, BatchView dst, double* __restrict__ gwork, int64_t gwork_stride, int L, int R,
-                       int32_t* info, int leaf_index) {
+                       int32_t* info, int leaf_index, LeafWait lw) {
     const int z = blockIdx.y;
     const int64_t lds = src.ld_of(z), ldd = dst.ld_of(z);
     leaf_gj_body<ROWS_IN_SMEM, PUSH>(src.ptr(z, lds), lds, const_cast<double*>(dst.ptr(z, ldd)), ldd,
                                      ROWS_IN_SMEM ? nullptr : gwork + (int64_t)z * gwork_stride, L, R,
-                                     info + (int64_t)z * INFO_WORDS, leaf_index);
+                                     info + (int64_t)z * INFO_WORDS, leaf_index, lw);
 }
 
 struct LeafConfig {
@@ -675,7 +686,7 @@ int prepare_leaf_kernel(K kern) {
 
 template <bool S, bool P>
 int launch_leaf_impl(const double* A, int64_t lda, double* X, int64_t ldx, const LeafConfig& c, int64_t L,
-                     double* scratch, int32_t* info, int leaf_index, cudaStream_t s) {
+                     double* scratch, int32_t* info, int leaf_index, cudaStream_t s, LeafWait lw = LeafWait()) {
     static bool attr_done = false;
     auto kern = leaf_gj_kernel<S, P>;
     if (!attr_done) {
@@ -695,7 +706,7 @@ int launch_leaf_impl(const double* A, int64_t lda, double* X, int64_t ldx, const
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    SPIN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, A, lda, X, ldx, scratch, (int)L, c.R, info, leaf_index));
+    SPIN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, A, lda, X, ldx, scratch, (int)L, c.R, info, leaf_index, lw));
     return SPIN_OK;
 }
 
@@ -722,7 +733,8 @@ int launch_leaf_batched_impl(const BatchView& src, const BatchView& dst, const L
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    SPIN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, src, dst, scratch, stride, (int)L, c.R, info, leaf_index));
+    SPIN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, src, dst, scratch, stride, (int)L, c.R, info, leaf_index,
+                                     LeafWait()));
     return SPIN_OK;
 }
 
@@ -757,3 +769,45 @@ int launch_leaf_gj(const double* A, int64_t lda, double* X, int64_t ldx, int64_t
 }
 
 }  // namespace spin
+
+// Test hook: the identity of order L (2 <= L <= 256, the pushed-row form, on
+// its widest cluster) with the CTA of rank mute_rank sending nothing and the
+// exchange waits limited to limit_ms.  The other CTAs' waits for step 0 run
+// out, the muted CTA's wait for step 1 does, every CTA leaves, and the info
+// record gets SPIN_ERR_TIMEOUT.  Remote writes happen only in the first
+// exchange, while every CTA still waits.  Returns the recorded status.
+extern "C" int spin_test_leaf_timeout(int64_t L, int mute_rank, double limit_ms) {
+    using namespace spin;
+    if (L < 2 || L > kPushMaxL || !(limit_ms > 0.0) || limit_ms > 4000.0) return SPIN_ERR_INVALID_ARG;
+    const LeafConfig c = leaf_config(L, false);
+    if (!c.push || mute_rank < 0 || mute_rank >= c.C) return SPIN_ERR_INVALID_ARG;
+    double* A = nullptr;
+    double* X = nullptr;
+    int32_t* info = nullptr;
+    const size_t bytes = (size_t)L * (size_t)L * sizeof(double);
+    if (cudaMalloc(&A, bytes) != cudaSuccess || cudaMalloc(&X, bytes) != cudaSuccess ||
+        cudaMalloc(&info, INFO_WORDS * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(A);
+        cudaFree(X);
+        return SPIN_ERR_OOM;
+    }
+    {  // the identity: the muted CTA gets past step 0 (a valid pivot) and waits at step 1
+        std::vector<double> I((size_t)L * (size_t)L, 0.0);
+        for (int64_t i = 0; i < L; i++) I[(size_t)i * (size_t)L + (size_t)i] = 1.0;
+        cudaMemcpy(A, I.data(), bytes, cudaMemcpyHostToDevice);
+    }
+    cudaMemset(info, 0, INFO_WORDS * sizeof(int32_t));
+    LeafWait lw;
+    lw.limit_ns = (uint64_t)(limit_ms * 1e6);
+    lw.mute_rank = mute_rank;
+    int rc = launch_leaf_impl<true, true>(A, L, X, L, c, L, nullptr, info, 0, 0, lw);
+    int32_t h[INFO_WORDS] = {0, 0, 0, 0};
+    if (rc == SPIN_OK) {
+        if (cudaMemcpy(h, info, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) rc = SPIN_ERR_CUDA;
+    }
+    cudaFree(A);
+    cudaFree(X);
+    cudaFree(info);
+    return rc == SPIN_OK ? h[INFO_STATUS] : rc;
+}

@@ -93,6 +93,12 @@ def test_invalid_arguments_rejected_on_host(L):
     assert L.spin_gemm_f64(4, 4, 4, 1.0, a, 4, a, 4, 1.0, None, 0, x, 4, None) == 1
     # leaf order above the supported maximum
     assert L.spin_leaf_inverse(a, 5000, x, 5000, 5000, None, None) == 1
+    # leaf exchange timeout hook: order outside 2..256, limit outside (0, 4000] ms
+    L.spin_test_leaf_timeout.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_double]
+    assert L.spin_test_leaf_timeout(1, 0, 50.0) == 1
+    assert L.spin_test_leaf_timeout(300, 0, 50.0) == 1
+    assert L.spin_test_leaf_timeout(128, 0, 0.0) == 1
+    assert L.spin_test_leaf_timeout(128, 0, 5000.0) == 1
 
 
 def test_pretransform_workspace(L):

@@ -132,6 +132,18 @@ def test_leaf_concurrent_streams_deterministic(spin, L):
     assert st == 0 and rel(first, G) <= tol(A)
 
 
+@pytest.mark.parametrize("L,mute", [(128, 0), (128, 7), (64, 15), (200, 3)])
+def test_leaf_exchange_timeout(spin, L, mute):
+    """A CTA of a pushed-row leaf that sends nothing: the other CTAs' bounded
+    waits (50 ms here) run out, every CTA leaves without a fault or a hang,
+    the status is SPIN_ERR_TIMEOUT, and the context stays usable (a leaf run
+    right after is right)."""
+    assert spin.leaf_exchange_timeout(L, mute, 50.0) == 6
+    A = np.random.default_rng(L).uniform(-1, 1, (L, L))
+    X = host(spin.leaf_inverse(dev(A)))
+    assert oracle.residual(A, X)[0] < 1e-13
+
+
 def test_leaf_singular_reports_column(spin):
     # a zero column c stays exactly zero under row operations, so the pivot
     # search fails exactly at step c (the oracle agrees)
