@@ -14,9 +14,11 @@
 // CTAs (C <= 16) whose rows stay put: every CTA owns R = ceil(L/C) rows in
 // shared memory when they fit (global memory, L2-resident, otherwise).  Row
 // interchanges are bookkeeping only (position <-> physical row tables
-// replicated in every CTA).  A pivot step is latency-bound at these sizes
-// (an FP64 operation takes ~250 cycles on this part), so a step keeps
-// remote reads, fences and FP64 work off its critical path:
+// replicated in every CTA).  A pivot step is latency-bound at these sizes:
+// each SM sub-partition's FP64 unit takes one warp instruction per 64
+// cycles, a dependent FP64 operation waits behind every one queued before
+// it (~250 cycles in a step), so a step keeps remote reads, fences and FP64
+// work off its critical path:
 //  - the pivot search compares the bit patterns of |a_ik| as integers
 //    (redux.sync argmax), and each candidate's reciprocal is computed once,
 //    by the CTA that publishes it;

@@ -925,7 +925,7 @@ __global__ void col_exp_kernel(Src src, int rows, int cols, int rows_per_block, 
     const int r0 = blockIdx.y * rows_per_block;
     const int r1 = min(rows, r0 + rows_per_block);
     int m = 0;
-    double ss4[4] = {0.0, 0.0, 0.0, 0.0};  // four FMA chains: an FP64 operation takes ~250 cycles here
+    double ss4[4] = {0.0, 0.0, 0.0, 0.0};  // four FMA chains: a dependent FP64 FMA takes 64+ cycles here
     if (c < cols) {
         int r = r0;
         for (; r + 3 < r1; r += 4) {
