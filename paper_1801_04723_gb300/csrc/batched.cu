@@ -173,10 +173,17 @@ int binv(BRun& r, BatchView A, BatchView X, const double* const* wbase, int64_t 
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-#ifndef SPIN_TC_MIN_BATCHED
-#define SPIN_TC_MIN_BATCHED 32
-#endif
-constexpr int64_t kTcMinBatched = SPIN_TC_MIN_BATCHED;
+// Smallest m, n and k a batched mixed product takes to the tensor cores
+// (SPIN_TC_MIN_BATCHED overrides it, for measurement; read once).
+int64_t tc_min_batched() {
+    static int64_t v = -1;
+    if (v < 0) {
+        const char* e = getenv("SPIN_TC_MIN_BATCHED");
+        const long long x = e ? atoll(e) : 0;
+        v = x > 0 ? (int64_t)x : 32;
+    }
+    return v;
+}
 
 // Split-plane bytes per matrix for a bucket of order n: the largest level
 // product (bf16x3 planes, or digit planes for the top Schur complements),
@@ -221,8 +228,10 @@ int bproduct(BMix& x, int depth, bool schur, int64_t m, int64_t n, int64_t k, do
     // The batch's products are small and numerous: on the tensor cores a
     // 128 x 256 tile that a 32 x 32 product fills to 1/32 still outruns the
     // FP64 pipe (GB300's BF16 rate is ~1500x its FP64 rate), so only products
-    // below 32 in some dimension stay in FP64.
-    if (m < kTcMinBatched || n < kTcMinBatched || k < kTcMinBatched) {
+    // below 32 in some dimension stay in FP64 (64 measures the same, 128 and
+    // 256 are 12 % and 72 % slower per batch).
+    const int64_t tcm = tc_min_batched();
+    if (m < tcm || n < tcm || k < tcm) {
         (*x.kernels)++;
         return launch_gemm_f64_batched(m, n, k, alpha, A, B, beta, C, D, x.count, x.s);
     }
