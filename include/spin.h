@@ -338,7 +338,7 @@ const char* spin_last_error(void);
 /*
  * spin_leaf_inverse: X = A^-1 for one leaf block by Gauss-Jordan with
  * partial pivoting (largest |a_ik|, lowest row position on ties), the
- * paper's direct leaf inversion (Alg. 1 "invert A in any approach";
+ * paper's direct leaf inversion (Alg. 1, which leaves the method open;
  * Alg. 2 locInverse).  A: device n x n (lda), X: device n x n (ldx).
  * info_dev: device int32[4] {status, leaf_index, column, 0}; the first
  * failure is recorded (status 0 -> SPIN_ERR_SINGULAR) and later ones are

@@ -1,7 +1,7 @@
 // Leaf inversion: Gauss-Jordan with partial pivoting on one leaf block.
 //
-// Algorithm 1 inverts a block directly once its order reaches the threshold
-// ("invert A in any approach"; Algorithm 2's locInverse).  This kernel
+// Algorithm 1 inverts a block directly, by a method it leaves open, once its
+// order reaches the threshold (Algorithm 2's locInverse).  This kernel
 // computes the same in-place Gauss-Jordan as the CPU oracle's leaf: at step
 // k choose the row (among positions >= k) with the largest |a_ik|, lowest
 // position on ties; scale it by 1/pivot with the pivot slot receiving
