@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--probes", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-json", default="", help="write per-launch records here")
+    ap.add_argument("--leaf-times", default="", help="comma-separated leaf orders: time one leaf inversion "
+                    "(spin_leaf_inverse on its default cluster) per order and print the per-pivot-step times")
     ap.add_argument("--leaf-sweep", default="", help="comma-separated orders: time every candidate leaf "
                     "(the U-shaped block-size sweep) with spin_autotune_leaf and print one JSON line")
     ap.add_argument("--gemm-probe", type=int, default=0, help="time one digit-slice (6 slices) and one bf16x3 "
@@ -805,8 +807,41 @@ def run_leaf_sweep(args):
     return 0
 
 
+def run_leaf_times(args):
+    """The leaf kernel alone: CUDA events around one spin_leaf_inverse launch
+    per order (best of 5 after 2 warm-ups), on a seeded diagonally dominant
+    matrix; per pivot step = time / L.  These are the per-step times the
+    cost model's leaf constants come from."""
+    import torch
+
+    import paper_1801_04723_gb300 as spin
+    from paper_1801_04723_gb300 import inputs
+
+    spin.build()
+    out = {"leaf_times": [], "how": "CUDA events around one spin_leaf_inverse launch, best of 5 after 2 warm-ups"}
+    for L in [int(v) for v in args.leaf_times.split(",") if v]:
+        A = torch.from_numpy(inputs.sdd(L, seed=inputs.SEED_BASE + L)).to("cuda:0")
+        X = torch.empty_like(A)
+        for _ in range(2):
+            spin.leaf_inverse(A, out=X)
+        best = float("inf")
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            spin.leaf_inverse(A, out=X)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out["leaf_times"].append({"L": L, "ms": best, "us_per_step": best * 1e3 / L})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.leaf_times:
+        return run_leaf_times(args)
     if args.leaf_sweep:
         return run_leaf_sweep(args)
     if args.gemm_probe:

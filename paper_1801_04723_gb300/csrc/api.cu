@@ -576,8 +576,8 @@ __global__ void synth_sdd_kernel(double* A, int64_t n, uint64_t seed) {
 //   a + b L + R L g                   (rows in L2-resident global memory)
 // with a = 1.55 us, b = 5 ns for L <= 256 (candidate rows pushed to every
 // CTA) and a = 1.8 us, b = 14 ns above (pivot row read from its owner), and
-// g = 0.55 ns per element: the leaf microbenchmark's per-step times on 16
-// CTAs (L = 32 ... 2048).  It reproduces the measured sweeps at n = 1024,
+// g = 0.55 ns per element: per-step times of one leaf on its 16-CTA cluster
+// (bench.py --leaf-times, L = 32 ... 2048).  It reproduces the measured sweeps at n = 1024,
 // 4096 and 8192 (leaf 64 ... 2048) within 8 %.
 constexpr double kModelClock = 2.07e9;
 constexpr double kModelPsm = 4.0 * kModelClock;
