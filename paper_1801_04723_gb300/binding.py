@@ -524,7 +524,10 @@ class Server:
     """Request server (spin_serve_*): submit matrices (host numpy arrays or
     CUDA tensors, kept alive by the caller until polled), poll results.
     With ``max_queued_bytes`` a submit that would overfill the queue is shed:
-    ``submit`` returns None."""
+    ``submit`` returns None.  With ``priority_order`` > 0, requests of order
+    up to it run on high-priority streams.  A request whose device memory
+    cannot be allocated while others run waits for one of them to finish
+    (``stats()["deferred"]``)."""
 
     def __init__(self, hbm_budget_bytes: int, max_slots: int = 4, max_queued_bytes: int = 0,
                  priority_order: int = 0):
