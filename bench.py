@@ -35,9 +35,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "2n³/t TFLOP/s vs FP64/BF16 peak at residual ≤1e-10; served req/s with p50/p99"
 
-# DRAM bytes per flop of gemm_f64_kernel from one ncu capture of a 4096^3
-# launch (profiles/gemm_f64_kernel_n8192_top_level.md); operand re-reads grow
-# with the flops of a launch, so per-launch traffic is scaled by flops.
+# DRAM bytes per flop of gemm_f64_kernel: one ncu capture of a 4096^3 launch
+# of the top recursion level at n = 8192 read and wrote 3.852e9 bytes
+# (dram__bytes_read.sum + dram__bytes_write.sum); operand re-reads grow with
+# the flops of a launch, so per-launch traffic is scaled by flops.
 GEMM_F64_DRAM_BYTES_PER_FLOP = 3.852e9 / (2.0 * 4096 ** 3)
 SEED_BASE = 0x5EED0000
 
@@ -90,6 +91,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--probes", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="plain_fp64: skip the mixed-precision sub-record")
+    ap.add_argument("--mixed-steps", type=int, default=3, help="plain_fp64: timed steps of the mixed sub-record "
+                    "(at most --steps)")
+    ap.add_argument("--mixed-warmup", type=int, default=2, help="plain_fp64: warm-up steps of the mixed sub-record "
+                    "(at most --warmup, at least 1)")
     ap.add_argument("--profile-json", default="", help="write per-launch records here")
     ap.add_argument("--leaf-times", default="", help="comma-separated leaf orders: time one leaf inversion "
                     "(spin_leaf_inverse on its default cluster) per order and print the per-pivot-step times")
@@ -251,9 +257,14 @@ def cpu_baseline(w: dict, seconds_hint: float = 15.0) -> dict:
     t0 = time.perf_counter()
     oracle.strassen_inv(A, leaf)
     dt = time.perf_counter() - t0
-    return {"value": 2.0 * n_s ** 3 / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
-            "kind": "oracle", "sample": f"one inversion, n={n_s}, leaf {leaf}, {w['family']} input, "
-                                        f"{dt:.1f} s on {oracle.num_threads()} threads"}
+    out = {"value": 2.0 * n_s ** 3 / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
+           "kind": "oracle", "sample": f"one inversion, n={n_s}, leaf {leaf}, {w['family']} input, "
+                                       f"{dt:.1f} s on {oracle.num_threads()} threads"}
+    if w["n"] > n_s:
+        # the method's work is 2 n^3 at any leaf: the full order's time by n^3
+        out["extrapolated"] = {"n": w["n"], "seconds": dt * (w["n"] / n_s) ** 3, "label": "extrapolated",
+                               "how": f"sample time x (n / {n_s})^3"}
+    return out
 
 
 def run_reference_serve(args, w: dict):
@@ -473,6 +484,78 @@ def replica_rate(ms_local: float, flops_local: float, world: int, device):
     return ms, float(f.item()) / (ms * 1e-3) / 1e12
 
 
+def time_work(spin, work, steps: int, warmup: int, stream, barrier, local: int) -> dict:
+    """Warm-up calls through host buffers (each one also an end-to-end
+    measurement: pinned host memory, H2D of the inputs and D2H of the results
+    inside), then exactly `steps` device-resident steps between CUDA events
+    on the launching stream, with launch records and nvidia-smi clock samples
+    taken over the timed region."""
+    import torch
+
+    e2e_times = []
+    for _ in range(warmup):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        work.e2e_step()
+        e2e_times.append(time.perf_counter() - t0)
+    if warmup == 0:
+        work.step()  # at least one warm call
+        work.finish()
+    with ClockSampler(local) as clk:
+        barrier()
+        spin.profile_start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            work.step()
+        e1.record(stream)
+        barrier()
+        recs = spin.profile_collect()
+        info = work.finish()
+    return {"ms_local": e0.elapsed_time(e1) / steps, "e2e_times": e2e_times, "recs": recs, "info": info,
+            "clocks": clk.summary()}
+
+
+def kernel_table(recs) -> dict:
+    by_kind: dict = {}
+    for r in recs:
+        d = by_kind.setdefault(r["kind"], {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 0})
+        d["ms"] += r["ms"]
+        d["flops"] += r["flops"]
+        d["bytes"] += r["bytes"]
+        d["launches"] += 1
+    return by_kind
+
+
+def tensor_peak(peaks: dict):
+    """Tensor-core kernels timed inside a long step: the sustained BF16 peak."""
+    peak = peaks.get("bf16_tflops_sustained")
+    if peak is None:
+        return 1700.0, "fallback 1.7 PFLOP/s sustained BF16 (of fallback)"
+    return peak, "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+
+
+def top_roofline(by_kind: dict, ms_step: float, steps: int, peaks: dict, peak_fp64: float):
+    if not by_kind:
+        return None
+    top = max(by_kind, key=lambda k: by_kind[k]["ms"])
+    d = by_kind[top]
+    achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+    if top in ("gemm_tc", "residual", "update"):
+        peak, src = tensor_peak(peaks)
+        return {"kernel": top, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "flops_counted": "BF16 tensor-core products actually issued (slice pairs x 2mnk)",
+                "launches": d["launches"], "share_of_step": d["ms"] / (ms_step * steps)}
+    traffic = GEMM_F64_DRAM_BYTES_PER_FLOP * d["flops"] / d["launches"] if top == "gemm_f64" else None
+    return {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+            "frac": achieved / peak_fp64, "traffic": traffic,
+            "traffic_note": "bytes per launch: ncu dram read+write of a 4096^3 launch, scaled by flops",
+            "peak_source": "FP64 FMA rate measured live by spin_probe_fp64_peak on this GPU",
+            "launches": d["launches"], "share_of_step": d["ms"] / (ms_step * steps)}
+
+
 def run_ours(args, w: dict, n: int, leaf: int):
     import torch
 
@@ -502,33 +585,24 @@ def run_ours(args, w: dict, n: int, leaf: int):
     stream = torch.cuda.current_stream()
     flops = work.flops
 
-    # warm-up through host buffers: each is also an end-to-end measurement
-    # (pinned host memory, H2D of the inputs and D2H of the results inside)
-    e2e_times = []
-    for i in range(args.warmup):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        work.e2e_step()
-        e2e_times.append(time.perf_counter() - t0)
-    if args.warmup == 0:
-        work.step()  # at least one warm call
-        work.finish()
-    peak_fp64 = spin.probe_fp64_peak()
-
-    with ClockSampler(local) as clk:
-        barrier()
-        spin.profile_start()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            work.step()
-        e1.record(stream)
-        barrier()
-        recs = spin.profile_collect()
-        info = work.finish()
-    ms, value = replica_rate(e0.elapsed_time(e1) / args.steps, flops, world, device)
+    # FP64 peak, live: the DFMA probe (the plain path's roofline denominator)
+    # and the DMMA probe beside it, with the SM clock sampled meanwhile
+    with ClockSampler(local) as pclk:
+        dfma = [spin.probe_fp64_peak() for _ in range(3)]
+        dmma = [spin.probe_fp64_mma_peak() for _ in range(3)]
+    peak_fp64 = max(dfma)
+    probe = {"dfma_tflops": max(dfma), "dmma_tflops": max(dmma), "clocks": pclk.summary(),
+             "how": "spin_probe_fp64_peak (8 DFMA chains per thread) and spin_probe_fp64_mma_peak (8 mma.sync "
+                    "m8n8k4 f64 chains per warp), 4 x 256 threads per SM, best of 3 launches, 3 calls each"}
+    t = time_work(spin, work, args.steps, args.warmup, stream, barrier, local)
+    recs, info = t["recs"], t["info"]
+    ms, value = replica_rate(t["ms_local"], flops, world, device)
     acc = work.accuracy(args.probes)
+
+    mixed = None
+    if args.workload == "plain_fp64" and not args.no_mixed:
+        mixed = mixed_subrecord(args, spin, work, n, ms, device, stream, barrier, local, world, peak_fp64)
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -537,16 +611,9 @@ def run_ours(args, w: dict, n: int, leaf: int):
         return 0
 
     # roofline of the dominant kernel, from the in-region launch records
-    by_kind: dict = {}
-    for r in recs:
-        d = by_kind.setdefault(r["kind"], {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 0})
-        d["ms"] += r["ms"]
-        d["flops"] += r["flops"]
-        d["bytes"] += r["bytes"]
-        d["launches"] += 1
-    top = max(by_kind, key=lambda k: by_kind[k]["ms"]) if by_kind else None
-    roof = None
+    by_kind = kernel_table(recs)
     peaks = measured_peaks()
+    roof = None
     if isinstance(work, BatchWork) and work.precision == "fp64":
         # the batch replays one CUDA graph: no per-launch events; the whole
         # graph is FP64-pipe bound (batched products and leaves)
@@ -560,26 +627,10 @@ def run_ours(args, w: dict, n: int, leaf: int):
                 "achieved": value / world, "peak": peak_fp64, "unit": "TFLOP/s", "frac": value / world / peak_fp64,
                 "traffic": None, "peak_source": "FP64 FMA rate measured live by spin_probe_fp64_peak on this GPU",
                 "note": "effective 2n^3/t over the FP64 peak (above 1 means the tensor-core form beats FP64)"}
-    if top is not None:
-        d = by_kind[top]
-        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        if top in ("gemm_tc", "residual", "update"):
-            # tensor-core kernels timed inside a long step: the sustained BF16 peak
-            peak = peaks.get("bf16_tflops_sustained")
-            src = "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
-            if peak is None:
-                peak, src = 1700.0, "fallback 1.7 PFLOP/s sustained BF16 (of fallback)"
-            roof = {"kernel": top, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "peak_source": src,
-                    "flops_counted": "BF16 tensor-core products actually issued (slice pairs x 2mnk)",
-                    "launches": d["launches"], "share_of_step": d["ms"] / (ms * args.steps)}
-        else:
-            traffic = GEMM_F64_DRAM_BYTES_PER_FLOP * d["flops"] / d["launches"] if top == "gemm_f64" else None
-            roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-                    "frac": achieved / peak_fp64, "traffic": traffic,
-                    "traffic_note": "bytes per launch: ncu dram read+write of a 4096^3 launch, scaled by flops",
-                    "peak_source": "FP64 FMA rate measured live by spin_probe_fp64_peak on this GPU",
-                    "launches": d["launches"], "share_of_step": d["ms"] / (ms * args.steps)}
+    top_roof = top_roofline(by_kind, ms, args.steps, peaks, peak_fp64)
+    if top_roof is not None:
+        roof = top_roof
+    e2e_times = t["e2e_times"]
     e2e_ok = e2e_times[1:] if len(e2e_times) > 1 else e2e_times
     e2e_t = statistics.median(e2e_ok) if e2e_ok else None
     batch = isinstance(work, BatchWork)
@@ -599,19 +650,20 @@ def run_ours(args, w: dict, n: int, leaf: int):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if w["precision"] == "fp64" else ("bf16x3+f64" if w["precision"] == "bf16x3" else "bf16-digits+f64"), "data": "synthetic",
         "config": config,
-        "clocks": clk.summary(),
+        "clocks": t["clocks"],
         "e2e": {"value": flops / e2e_t / 1e12 if e2e_t else None, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": work.h2d, "d2h_bytes_per_step": work.d2h,
                 "how": "host buffers (pinned), copies inside the timed call, warm-up steps 2..W, host wall clock"},
         "cold": {"first_call_ms": e2e_times[0] * 1e3 if e2e_times else None,
                  "how": "the first end-to-end call of the process: workspace allocation, module load and "
                         "copies included"},
-        "gpu_launches": work.launches(recs, args.steps),
+        "gpu_launches": work.launches(recs, args.steps) + (mixed["gpu_launches"] if mixed else 0),
         "roofline": roof,
         "status": info["status"],
         "refine_iters": info.get("refine_iters"),
         "rel_residual_lib": info.get("rel_residual"),
         "fp64_peak_tflops": peak_fp64,
+        "fp64_probe": probe,
         "frac_of_fp64_peak": value / world / peak_fp64,
         "bf16_peak_tflops": peaks.get("bf16_tflops"),
         "frac_of_bf16_peak": value / world / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
@@ -619,6 +671,8 @@ def run_ours(args, w: dict, n: int, leaf: int):
                     for k, v in by_kind.items()},
     }
     line.update(acc)
+    if mixed is not None:
+        line["mixed"] = mixed
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if args.profile_json:
@@ -630,6 +684,60 @@ def run_ours(args, w: dict, n: int, leaf: int):
 
         dist.destroy_process_group()
     return 0
+
+
+def mixed_subrecord(args, spin, plain_work, n: int, plain_ms: float, device, stream, barrier, local: int,
+                    world: int, peak_fp64: float) -> dict:
+    """The mixed-precision form on the same GPU in the same process: one SPD
+    matrix of order n with known inverse (A = Q diag(d) Q^T, 64 Householder
+    reflectors, d log-uniform in [1, 1e3]), BF16x3 tensor-core level
+    products, FP64 leaves, FP64-class top-two Schur complements and residual,
+    Newton-Schulz to residual <= 1e-10; timed like the plain form (CUDA events
+    over the steps, e2e through spin_invert_host) and compared with it."""
+    import gc
+
+    import torch
+
+    # the plain form's buffers (A, X, pinned host copies) are not needed any more
+    for name in ("A", "X", "Ah", "Xh"):
+        if hasattr(plain_work, name):
+            setattr(plain_work, name, None)
+    gc.collect()
+    torch.cuda.empty_cache()
+    wm = dict(WORKLOADS["mixed_bf16x3"])
+    wm["n"] = n
+    leaf_m = wm["leaf"]
+    steps = max(1, min(args.steps, args.mixed_steps))
+    warmup = max(1, min(args.warmup, args.mixed_warmup))
+    work = SingleWork(spin, wm, n, leaf_m, device, 0, args.fp64_levels)
+    t = time_work(spin, work, steps, warmup, stream, barrier, local)
+    ms, value = replica_rate(t["ms_local"], work.flops, world, device)
+    acc = work.accuracy(args.probes)
+    by_kind = kernel_table(t["recs"])
+    roof = top_roofline(by_kind, ms, steps, measured_peaks(), peak_fp64)
+    e2e_times = t["e2e_times"]
+    e2e_ok = e2e_times[1:] if len(e2e_times) > 1 else e2e_times
+    e2e_t = statistics.median(e2e_ok) if e2e_ok else None
+    info = t["info"]
+    return {
+        "workload": "mixed_bf16x3", "desc": wm["desc"], "n": n, "leaf": leaf_m, "precision": "bf16x3",
+        "fp64_levels": args.fp64_levels, "tol": 1e-10, "steps": steps, "warmup": warmup,
+        "value": value, "unit": "TFLOP/s", "ms_per_step": ms,
+        "speedup_vs_plain": plain_ms / ms,
+        "status": info["status"], "refine_iters": info.get("refine_iters"),
+        "rel_residual_lib": info.get("rel_residual"),
+        **acc,
+        "clocks": t["clocks"],
+        "e2e": {"value": work.flops / e2e_t / 1e12 if e2e_t else None, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": work.h2d, "d2h_bytes_per_step": work.d2h,
+                "how": "spin_invert_host on pinned host buffers, copies inside the timed call, warm-up steps "
+                       "2..W (step 1 if W = 1), host wall clock"},
+        "cold": {"first_call_ms": e2e_times[0] * 1e3 if e2e_times else None},
+        "roofline": roof,
+        "gpu_launches": len(t["recs"]),
+        "kernels": {k: {"launches": v["launches"], "ms": v["ms"], "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9}
+                    for k, v in by_kind.items()},
+    }
 
 
 def run_serve(args, w: dict):

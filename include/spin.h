@@ -63,7 +63,7 @@ typedef enum {
     SPIN_FP64 = 0,         /* every product in FP64 (plain method)                           */
     SPIN_MIXED_BF16X3 = 1, /* products on BF16 tensor cores with 3-term splits, FP32 accumulate,
                               then Newton-Schulz refinement to opts.tol                       */
-    SPIN_MIXED_TF32 = 2,   /* reserved: TF32 operands (returns SPIN_ERR_NOT_IMPLEMENTED)      */
+    /* 2 is not a precision (a call passing it gets SPIN_ERR_INVALID_ARG)                     */
     SPIN_MIXED_DIGITS = 3  /* products on BF16 tensor cores as 4-slice fixed-point digit
                               products with exact FP32 runs (~2^-30 relative), then the same
                               refinement -- which usually stops at its first, certifying
@@ -112,8 +112,8 @@ spin_opts spin_opts_default(void);
 
 /*
  * spin_invert: X = A^-1 by the plain method (Algorithm 1, every product in
- * FP64; leaves by Gauss-Jordan with partial pivoting, the paper's "any
- * approach" leaf, Alg. 1 / Alg. 2 "locInverse").
+ * FP64; leaves by Gauss-Jordan with partial pivoting, the direct leaf
+ * inversion that Alg. 1 and Alg. 2 leave open).
  *   A    device, n x n, leading dimension lda >= n, read only.
  *   X    device, n x n, leading dimension n, written.
  *   n    order, >= 1.
@@ -267,12 +267,19 @@ int spin_serve_destroy(spin_server* sv);
  * workspace fits it (n <= 1024 at any leaf <= 512; larger n, or a leaf whose
  * scratch does not fit, returns SPIN_ERR_INVALID_ARG before any work).
  *   A, X, n, lda, leaf, stream: as spin_invert (X has leading dimension n).
- * Blocking: returns the numerical status after the stream has finished.
+ * Blocking: the call synchronises `stream`, copies the 16-byte status
+ * record into a host variable and returns the numerical status.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the one array:
- * calls that may overlap on the GPU (other streams, other threads) race and
- * must be serialised by the caller.
+ * before any stream capture.  CUDA loads a library's device code lazily, so
+ * that first call is also when the driver places this library's kernels and
+ * the 8 MB array on the device: a caller whose device memory will later be
+ * reserved by another allocator makes one call (any small n) before that
+ * happens; later calls add nothing to the device's memory use.  All calls on
+ * a device share the one array, which keeps the previous call's contents
+ * (each call clears the status record itself): calls that may overlap on the
+ * GPU (other streams, other threads) race and must be serialised by the
+ * caller.
  */
 int spin_invert_noalloc(const double* A, double* X, int64_t n, int64_t lda, int leaf, spin_stream_t stream);
 
@@ -437,6 +444,13 @@ int spin_profile_stop(spin_stream_t stream, spin_prof_record* out, int max, int*
 /* Measure the FP64 FMA throughput of this GPU with a DFMA-bound kernel on
  * every SM (about 0.1 s); *tflops receives 2 * FMAs / s / 1e12. */
 int spin_probe_fp64_peak(double* tflops, spin_stream_t stream);
+
+/* The same measurement on the FP64 tensor path: every warp issues
+ * independent mma.sync m8n8k4 f64 (DMMA) chains on every SM (about 0.1 s);
+ * *tflops receives 2 * FMAs / s / 1e12.  Sec. 4 prices the method by its
+ * products, so the faster of the two FP64 forms is the one the plain path's
+ * level products use (on GB300: DFMA, which this lets anyone re-check). */
+int spin_probe_fp64_mma_peak(double* tflops, spin_stream_t stream);
 
 #ifdef __cplusplus
 }

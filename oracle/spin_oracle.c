@@ -13,8 +13,8 @@
  *        VI = V^-1, C12 = III.VI, C21 = VI.II, VII = III.C21,
  *        C11 = I - VII, C22 = -VI,
  *     recursing until the block order reaches the leaf size, where the block
- *     is inverted directly (Algorithm 1 leaves the leaf method open: "LU, QR,
- *     SVD"; this oracle uses Gauss-Jordan with partial pivoting, below).
+ *     is inverted directly (Algorithm 1 leaves the direct leaf method open,
+ *     Sec. 3.1; this oracle uses Gauss-Jordan with partial pivoting, below).
  *   - oracle_gj_inv: Gauss-Jordan inversion with partial pivoting on the full
  *     matrix (the plain definition X = A^-1), used at the leaves and as an
  *     independent second oracle.
@@ -24,8 +24,9 @@
  *   - oracle_freivalds: ||(A X - I) v|| for given probe vectors v, O(k n^2).
  *
  * Readings of the paper taken here (each also listed in the design notes):
- *   - leaf test: a block is a leaf when its order n <= leaf (Alg 1 says
- *     "n = threshold", Alg 2 "size/blockSize = 1"; both agree on powers of 2);
+ *   - leaf test: a block is a leaf when its order n <= leaf (Alg. 1 stops when
+ *     the order equals the threshold, Alg. 2 when one block of that order is
+ *     left; the two agree on powers of 2);
  *   - split point for any n (the paper treats n = 2^p only, Sec. 4):
  *     n1 = 32*ceil(n/64) when n > 64, else ceil(n/2); n2 = n - n1;
  *   - leaf pivoting: the row with the largest |a_ik|, i >= k, lowest index on

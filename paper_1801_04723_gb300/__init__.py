@@ -9,7 +9,7 @@ There is no CPU fallback: every entry point raises if the library is absent.
 from .binding import (  # noqa: F401
     SPIN_FP64,
     SPIN_MIXED_BF16X3,
-    SPIN_MIXED_TF32,
+    SPIN_MIXED_DIGITS,
     SpinError,
     Server,
     Info,
@@ -36,6 +36,7 @@ from .binding import (  # noqa: F401
     profile_start,
     profile_collect,
     probe_fp64_peak,
+    probe_fp64_mma_peak,
     workspace_bytes,
 )
 from .build import build  # noqa: F401

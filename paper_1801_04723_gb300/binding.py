@@ -21,10 +21,9 @@ SPIN_ERR_NOT_IMPLEMENTED = 8
 
 SPIN_FP64 = 0
 SPIN_MIXED_BF16X3 = 1
-SPIN_MIXED_TF32 = 2
 SPIN_MIXED_DIGITS = 3
 
-PRECISIONS = {"fp64": SPIN_FP64, "bf16x3": SPIN_MIXED_BF16X3, "tf32": SPIN_MIXED_TF32, "digits": SPIN_MIXED_DIGITS}
+PRECISIONS = {"fp64": SPIN_FP64, "bf16x3": SPIN_MIXED_BF16X3, "digits": SPIN_MIXED_DIGITS}
 
 
 class Opts(ctypes.Structure):
@@ -169,6 +168,8 @@ def lib():
         L.spin_profile_stop.restype = ctypes.c_int
         L.spin_probe_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
         L.spin_probe_fp64_peak.restype = ctypes.c_int
+        L.spin_probe_fp64_mma_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+        L.spin_probe_fp64_mma_peak.restype = ctypes.c_int
         L.spin_gemm_bf16x3.argtypes = [i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp, i64, vp]
         L.spin_gemm_bf16x3.restype = ctypes.c_int
         L.spin_gemm_ozaki.argtypes = [i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp, i64, ctypes.c_int,
@@ -404,6 +405,15 @@ def probe_fp64_peak(stream=None) -> float:
     rc = lib().spin_probe_fp64_peak(ctypes.byref(v), _stream(stream))
     if rc != SPIN_OK:
         raise SpinError(rc, "spin_probe_fp64_peak")
+    return v.value
+
+
+def probe_fp64_mma_peak(stream=None) -> float:
+    """FP64 throughput of this GPU through mma.sync f64 (DMMA) in TFLOP/s."""
+    v = ctypes.c_double(0.0)
+    rc = lib().spin_probe_fp64_mma_peak(ctypes.byref(v), _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_probe_fp64_mma_peak")
     return v.value
 
 

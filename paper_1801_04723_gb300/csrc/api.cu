@@ -511,7 +511,7 @@ int enqueue(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, con
             StreamState* st, cudaStream_t s) {
     const int64_t leaf = resolve_leaf(n, o.leaf, o.precision);
     RET(check_common(A, lda, X, ldx, n, leaf));
-    if (o.precision == SPIN_MIXED_TF32) return SPIN_ERR_NOT_IMPLEMENTED;
+    if (!valid_precision(o.precision)) return SPIN_ERR_INVALID_ARG;
     const bool mixed = o.precision != SPIN_FP64;
     if (mixed && (o.residual_slices < 0 || o.residual_slices > 7 || o.max_refine < 0 || !(o.tol > 0.0)))
         return SPIN_ERR_INVALID_ARG;
@@ -691,8 +691,7 @@ int spin_default_leaf(int64_t n, int precision) {
 int spin_autotune_leaf(int64_t n, int precision, const int* candidates, int ncand, int* leaf_out, double* ms_out,
                        spin_stream_t stream) {
     if (n < 2 || ncand < 1 || candidates == nullptr || leaf_out == nullptr) return SPIN_ERR_INVALID_ARG;
-    if (precision < SPIN_FP64 || precision > SPIN_MIXED_DIGITS || precision == SPIN_MIXED_TF32)
-        return SPIN_ERR_INVALID_ARG;
+    if (!valid_precision(precision)) return SPIN_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     StreamState* st = nullptr;
     RET(get_state(s, &st));
@@ -758,7 +757,7 @@ int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t
                    spin_info* info, spin_stream_t stream) {
     cudaStream_t s = (cudaStream_t)stream;
     spin_opts o = opts ? *opts : spin_opts_default();
-    if (o.precision < SPIN_FP64 || o.precision > SPIN_MIXED_DIGITS) return SPIN_ERR_INVALID_ARG;
+    if (!valid_precision(o.precision)) return SPIN_ERR_INVALID_ARG;
     RET(check_common(A, lda, X, ldx, n, n >= 1 ? resolve_leaf(n, o.leaf, o.precision) : 1));
     StreamState* st = nullptr;
     RET(get_state(s, &st));

@@ -4,6 +4,8 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
+
 #include "../../include/spin.h"
 
 namespace spin {
@@ -25,6 +27,30 @@ enum { INFO_STATUS = 0, INFO_LEAF = 1, INFO_COL = 2, INFO_WORDS = 4 };
     } while (0)
 
 void record_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// One-time set-up per device (cudaFuncSetAttribute applies to the current
+// device only): run(f) calls f once for each device it is used on; threads
+// that race on a new device may both call f, which is harmless for attribute
+// setting.  Devices beyond 64 run f every time.
+struct PerDeviceOnce {
+    std::atomic<unsigned long long> done{0};
+    template <class F>
+    int run(F&& f) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            return f();
+        }
+        const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+        if (bit && (done.load(std::memory_order_acquire) & bit)) return 0;
+        const int rc = f();
+        if (rc == 0 && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+        return rc;
+    }
+};
+
+// The precisions of spin_precision (0, 1 and 3).
+inline bool valid_precision(int p) { return p == SPIN_FP64 || p == SPIN_MIXED_BF16X3 || p == SPIN_MIXED_DIGITS; }
 
 // First failure wins: status 0 -> code, then leaf and column are recorded.
 __device__ __forceinline__ void record_failure(int32_t* info, int code, int leaf, int col) {

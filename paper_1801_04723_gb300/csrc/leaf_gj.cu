@@ -689,12 +689,11 @@ int prepare_leaf_kernel(K kern) {
 template <bool S, bool P>
 int launch_leaf_impl(const double* A, int64_t lda, double* X, int64_t ldx, const LeafConfig& c, int64_t L,
                      double* scratch, int32_t* info, int leaf_index, cudaStream_t s, LeafWait lw = LeafWait()) {
-    static bool attr_done = false;
+    static PerDeviceOnce attrs;
     auto kern = leaf_gj_kernel<S, P>;
-    if (!attr_done) {
-        const int rc = prepare_leaf_kernel(kern);
+    {
+        const int rc = attrs.run([&] { return prepare_leaf_kernel(kern); });
         if (rc != SPIN_OK) return rc;
-        attr_done = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)c.C, 1, 1);
@@ -716,12 +715,11 @@ template <bool S, bool P>
 int launch_leaf_batched_impl(const BatchView& src, const BatchView& dst, const LeafConfig& c, int64_t L,
                              double* scratch, int64_t stride, int32_t* info, int leaf_index, int count,
                              cudaStream_t s) {
-    static bool attr_done = false;
+    static PerDeviceOnce attrs;
     auto kern = leaf_gj_batched_kernel<S, P>;
-    if (!attr_done) {
-        const int rc = prepare_leaf_kernel(kern);
+    {
+        const int rc = attrs.run([&] { return prepare_leaf_kernel(kern); });
         if (rc != SPIN_OK) return rc;
-        attr_done = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)c.C, (unsigned)count, 1);

@@ -273,7 +273,7 @@ extern "C" int spin_serve_create(const spin_serve_cfg* cfg, spin_server** out) {
 extern "C" int spin_serve_submit(spin_server* sv, const double* A, int64_t lda, int64_t n, int precision, double tol,
                                  uint64_t* ticket) {
     if (sv == nullptr || A == nullptr || ticket == nullptr || n < 1 || lda < n) return SPIN_ERR_INVALID_ARG;
-    if (precision < SPIN_FP64 || precision > SPIN_MIXED_DIGITS || precision == SPIN_MIXED_TF32 || !(tol > 0.0))
+    if (!valid_precision(precision) || !(tol > 0.0))
         return SPIN_ERR_INVALID_ARG;
     cudaPointerAttributes at;
     bool on_dev = false;

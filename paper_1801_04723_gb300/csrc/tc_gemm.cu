@@ -1081,12 +1081,14 @@ int launch_impl(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, c
     if (rc) return rc;
     rc = make_map(&tb, b.base, p.K, (int64_t)b.rows * b.slices * nz, b.ld, BN);
     if (rc) return rc;
-    static bool attr = false;
+    static PerDeviceOnce attrs;
     auto kern = tc_gemm_kernel<BN, EXACT, EPI_WARPS>;
-    if (!attr) {
-        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<BN, EXACT ? (BN >= 256 ? 1 : KSUB_EXACT) : KSUB_FLOAT>::SMEM_BYTES));
-        attr = true;
-    }
+    rc = attrs.run([&]() -> int {
+        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)Cfg<BN, EXACT ? (BN >= 256 ? 1 : KSUB_EXACT) : KSUB_FLOAT>::SMEM_BYTES));
+        return SPIN_OK;
+    });
+    if (rc) return rc;
     const int64_t tiles = (int64_t)((p.N + BN - 1) / BN) * ((p.M + BM - 1) / BM);
     if (tiles > INT32_MAX) return SPIN_ERR_INVALID_ARG;
     kern<<<dim3((unsigned)tiles, (unsigned)nz), Epi<EPI_WARPS>::THREADS,
@@ -1104,12 +1106,13 @@ int launch_pair(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, c
     if (rc) return rc;
     rc = make_map(&tb, b.base, p.K, (int64_t)b.rows * b.slices * nz, b.ld, C::BNH);
     if (rc) return rc;
-    static bool attr = false;
+    static PerDeviceOnce attrs;
     auto kern = tc_gemm_pair_kernel<PBN, EPI_WARPS>;
-    if (!attr) {
+    rc = attrs.run([&]() -> int {
         SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES));
-        attr = true;
-    }
+        return SPIN_OK;
+    });
+    if (rc) return rc;
     const int64_t tiles = (int64_t)((p.N + PBN - 1) / PBN) * ((p.M + 2 * BM - 1) / (2 * BM));
     if (2 * tiles > INT32_MAX) return SPIN_ERR_INVALID_ARG;
     kern<<<dim3((unsigned)(2 * tiles), (unsigned)nz), Epi<EPI_WARPS>::THREADS, C::SMEM_BYTES, s>>>(ta, tb, p);

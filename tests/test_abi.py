@@ -88,6 +88,8 @@ def test_invalid_arguments_rejected_on_host(L):
     o.leaf = 0
     o.precision = 9
     assert L.spin_invert_ex(a, 4, x, 4, 4, ctypes.byref(o), ctypes.byref(info), None) == 1
+    o.precision = 2  # not a precision of spin_precision
+    assert L.spin_invert_ex(a, 4, x, 4, 4, ctypes.byref(o), ctypes.byref(info), None) == 1
     # gemm: alpha/beta outside {+-1} x {0,1}
     assert L.spin_gemm_f64(4, 4, 4, 2.0, a, 4, a, 4, 0.0, None, 0, x, 4, None) == 1
     assert L.spin_gemm_f64(4, 4, 4, 1.0, a, 4, a, 4, 1.0, None, 0, x, 4, None) == 1

@@ -4,6 +4,7 @@ result compared with the oracle's Algorithm 1 at the same leaf size."""
 import numpy as np
 import pytest
 
+import bounds
 import oracle
 from paper_1801_04723_gb300 import inputs
 
@@ -31,6 +32,7 @@ def check(A, X, leaf):
     n = A.shape[0]
     tol = 64 * n * np.linalg.cond(A) * U
     assert np.linalg.norm(X - ref) / np.linalg.norm(ref) <= tol
+    assert bounds.elementwise_ok(X, ref, A)
     assert oracle.residual(A, X)[0] <= 1e-13
 
 

@@ -16,6 +16,7 @@ from fractions import Fraction
 import numpy as np
 import pytest
 
+import bounds
 import oracle
 from paper_1801_04723_gb300 import inputs
 
@@ -220,6 +221,29 @@ def test_matches_lapack(n, leaf):
     assert rel_err(X, np.linalg.inv(A)) < 1e-14
     G, _ = oracle.gj_inv(A)
     assert rel_err(G, np.linalg.inv(A)) < 1e-14
+
+
+@pytest.mark.parametrize("n,leaf,family", [(65, 8, "sdd"), (257, 64, "spd"), (777, 100, "sdd"), (1100, 600, "spd")])
+def test_matches_lapack_elementwise(n, leaf, family):
+    """Element by element, within the componentwise bound the GPU parity
+    tests use (|X - X_ref|_ij <= 4 n u (|X_ref||A||X_ref|)_ij)."""
+    A = inputs.sdd(n, seed=11 + n) if family == "sdd" else inputs.spd_gram(n, seed=13 + n)
+    X, _ = oracle.strassen_inv(A, leaf)
+    assert bounds.elementwise_ok(X, np.linalg.inv(A), A)
+
+
+def test_elementwise_bound_sees_a_local_error():
+    """One deep leaf's block of the result off by 1e-11 relative: the
+    Frobenius comparison of the parity tests (64 n kappa u) lets it through,
+    the element-wise bound does not."""
+    n, leaf = 1024, 128
+    A = inputs.sdd(n, seed=inputs.SEED_BASE)
+    ref, _ = oracle.strassen_inv(A, leaf)
+    bad = ref.copy()
+    bad[:32, :32] *= 1.0 + 1e-11  # inside the first leaf's block
+    assert rel_err(bad, ref) <= 64 * n * np.linalg.cond(A) * U
+    assert bounds.elementwise_ok(ref, np.linalg.inv(A), A)
+    assert not bounds.elementwise_ok(bad, np.linalg.inv(A), A)
 
 
 def test_transpose_and_leaf_invariance():

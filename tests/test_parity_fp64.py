@@ -8,15 +8,19 @@ and FMA contraction (the oracle never contracts).  For an inversion with
 condition number kappa a perturbation of relative size ~u per operation
 moves the result by ~c * n * kappa * u in relative norm; the tests use
     ||X_gpu - X_oracle||_F / ||X_oracle||_F <= 64 * n * kappa * u,  u = 2^-53
-(about 1e-11 at n = 1024, kappa = 1.5), and on top of it the method's own
-target: relative residual ||AX - I||_F / (||A||_F ||X||_F) <= 1e-13,
-measured by the oracle's compensated residual.  Results that are exact in
+(about 1e-11 at n = 1024, kappa = 1.5); element by element (tests/bounds.py)
+    |X_gpu - X_oracle|_ij <= 4 n u (|X_oracle| |A| |X_oracle|)_ij,
+so that an error confined to one small block cannot hide under the norm;
+and on top of both the method's own target: relative residual
+||AX - I||_F / (||A||_F ||X||_F) <= 1e-13, measured by the oracle's
+compensated residual.  Results that are exact in
 floating point (permutations, power-of-two diagonals, block-diagonal and
 2^k-scaled inputs) are compared bit for bit.
 """
 import numpy as np
 import pytest
 
+import bounds
 import oracle
 from paper_1801_04723_gb300 import inputs
 
@@ -79,6 +83,14 @@ def test_gemm_f64_in_place_and_strided(spin):
     got = host(D)
     want = Cref - host(A) @ host(B)
     assert np.max(np.abs(got - want)) < 1e-13
+
+
+def test_fp64_probes(spin):
+    """Both FP64 forms of this GPU measured live: the DFMA probe (the plain
+    path's roofline denominator) and the DMMA (mma.sync f64) probe."""
+    dfma = spin.probe_fp64_peak()
+    dmma = spin.probe_fp64_mma_peak()
+    assert 0.3 < dfma < 100.0 and 0.3 < dmma < 100.0
 
 
 # ------------------------------------------------------------- leaf (GJ) --
@@ -169,6 +181,7 @@ def test_config0_n1024_leaf128(spin):
     assert info["status"] == 0
     assert rel(X, ref) <= tol(A)
     assert np.max(np.abs(X - ref)) <= 64 * 1024 * U * np.max(np.abs(ref))
+    assert bounds.elementwise_ok(X, ref, A)
     assert oracle.residual(A, X)[0] <= 1e-13
 
 
@@ -182,6 +195,7 @@ def test_invert_ragged(spin, n, leaf, family):
     ref, _ = oracle.strassen_inv(A, leaf)
     assert info["status"] == 0
     assert rel(X, ref) <= tol(A)
+    assert bounds.elementwise_ok(X, ref, A)
     assert oracle.residual(A, X)[0] <= 1e-13
 
 
@@ -260,6 +274,7 @@ def test_leading_dimensions_and_transpose(spin):
     X = host(Xview)
     ref, _ = oracle.strassen_inv(A, 64)
     assert rel(X, ref) <= tol(A)
+    assert bounds.elementwise_ok(X, ref, A)
     # the frame around the output view is untouched
     ob = host(outbig)
     assert np.all(ob[:3] == 7.0) and np.all(ob[260:] == 7.0) and np.all(ob[:, :11] == 7.0)
@@ -273,6 +288,7 @@ def test_host_buffers_and_caller_workspace(spin):
     Xh, info = spin.invert_host(A, leaf=128)
     ref, _ = oracle.strassen_inv(A, 128)
     assert rel(Xh, ref) <= tol(A)
+    assert bounds.elementwise_ok(Xh, ref, A)
     ws = torch.empty(spin.workspace_bytes(600, leaf=128) // 8 + 1, dtype=torch.float64, device="cuda:0")
     Xd = host(spin.invert(dev(A), leaf=128, workspace=ws)[0])
     np.testing.assert_array_equal(Xd, Xh)
