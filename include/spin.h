@@ -130,10 +130,13 @@ int spin_invert(const double* A, double* X, int64_t n, int64_t lda, int leaf, sp
  * opts may be NULL (defaults).  With opts->blocking, or when info is not
  * NULL, the call synchronises the stream and fills *info; otherwise it
  * returns once the work is enqueued and spin_sync() reads the status later.
- * Mixed precisions refine until opts->tol or opts->max_refine; they read the
- * residual norm back after every refinement step, so they synchronise the
- * stream during the call whatever opts->blocking says.  The caller-provided
- * workspace (opts->workspace) must be 256-byte aligned.
+ * Mixed precisions refine until opts->tol or opts->max_refine: rounds
+ * 0 .. max_refine of Newton-Schulz are all enqueued and the stopping
+ * decision is taken on the device after each residual (a converged matrix
+ * skips the remaining rounds' work), so they do not synchronise the stream
+ * unless blocking or info asks for it; pretransform = 2 waits once for the
+ * first attempt's status.  The caller-provided workspace (opts->workspace)
+ * must be 256-byte aligned.
  */
 int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n,
                    const spin_opts* opts, spin_info* info, spin_stream_t stream);
@@ -158,10 +161,11 @@ int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t
  * on streams forked from `stream`.  The launch sequence is captured into a
  * CUDA graph on the first call and replayed while the arguments (pointers,
  * orders, leading dimensions, options) stay the same; the
- * workspace is library-owned.  The mixed form reads residual norms on the
- * host between refinement steps, so it returns when the batch is done (its
- * refinement launches are not part of the graph).  count <= 65535,
- * n[i] <= 65536.
+ * workspace is library-owned.  The mixed form's refinement is part of the
+ * graph: each matrix's stopping decision is taken on the device, so the
+ * result of a matrix does not depend on the others in the batch, and the
+ * call returns once the graph is enqueued (with opts->blocking, once it has
+ * run).  count <= 65535, n[i] <= 65536.
  */
 int spin_invert_batched(const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
                         int count, const spin_opts* opts, int* info_dev, spin_stream_t stream);
@@ -177,9 +181,10 @@ int spin_rbt_diagonals(uint64_t seed, int64_t n, int depth, double* out_dev, spi
  * kernel launches per call and order buckets.  SPIN_ERR_INVALID_ARG if none. */
 int spin_batched_stats(spin_stream_t stream, int* kernels, int* buckets);
 
-/* Mixed-form refinement of the latest spin_invert_batched on `stream`:
- * Newton-Schulz steps taken (the most over the buckets) and the largest
- * ||A X - I||_F / (||A||_F ||X||_F) over the batch; -1 for a plain batch. */
+/* Mixed-form refinement of the latest spin_invert_batched on `stream`
+ * (synchronises the stream): Newton-Schulz steps taken (the most over the
+ * matrices) and the largest ||A X - I||_F / (||A||_F ||X||_F) over the
+ * batch; -1 for a plain batch. */
 int spin_batched_refine_info(spin_stream_t stream, int* refine_iters, double* worst_rel);
 
 /* ---------------------------------------------------------------------

@@ -63,6 +63,7 @@ namespace {
 struct ProfEntry {
     spin_prof_record rec;
     cudaEvent_t start, stop;
+    int gate_slot;  // >= 0: the launch ran only if flags[gate_slot] != 0
 };
 
 struct Profiler {
@@ -70,6 +71,11 @@ struct Profiler {
     int max_records = 0;
     std::vector<ProfEntry> entries;
     std::vector<cudaEvent_t> pool;
+    // Refinement launches are gated on the device by a matrix's active flag;
+    // a copy of the flag taken just before each gated launch (device int per
+    // record) tells profile_stop which ones did the work they describe.
+    int* flags = nullptr;
+    int flags_cap = 0;
 
     cudaEvent_t event() {
         if (!pool.empty()) {
@@ -83,21 +89,27 @@ struct Profiler {
     }
 };
 
+// Device status block of a stream (32 bytes, pinned mirror on the host):
+// int32 info record [status, leaf, column, spare], then the refinement's
+// active flag, iteration count and last relative residual.
+constexpr int CTL_ACTIVE = INFO_WORDS, CTL_ITERS = INFO_WORDS + 1, CTL_REL = INFO_WORDS + 2;  // int32 offsets
+constexpr size_t CTL_BYTES = 32;
+
 struct StreamState {
     Profiler prof;
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    int32_t* info_dev = nullptr;   // INFO_WORDS ints
+    int32_t* info_dev = nullptr;   // CTL_BYTES: info record + refinement control
     int32_t* info_host = nullptr;  // pinned mirror
     double* hostA = nullptr;       // device staging for spin_invert_host
     double* hostX = nullptr;
     size_t host_elems = 0;
-    double* norms_host = nullptr;  // pinned: ||A||^2, ||X||^2, ||R||^2 of the refinement
     int* err_dev = nullptr;        // device: tensor-core bounded-wait failures
-    int last_refine_iters = 0;     // host: result of the latest mixed-precision call
-    double last_rel = -1.0;
-    int last_host_status = 0;      // host-detected status (e.g. not converged)
+    int last_mixed = 0;            // host: the latest call refined (mixed precision)
     int last_pretransformed = 0;   // host: the latest call went through the butterfly transform
+    int* active() { return (int*)(info_dev + CTL_ACTIVE); }
+    int* iters() { return (int*)(info_dev + CTL_ITERS); }
+    double* rel() { return (double*)(info_dev + CTL_REL); }
 };
 
 std::mutex g_mu;
@@ -109,9 +121,9 @@ int get_state(cudaStream_t s, StreamState** out) {
     std::lock_guard<std::mutex> lk(g_mu);
     StreamState& st = g_states[std::make_pair(dev, s)];
     if (st.info_dev == nullptr) {
-        SPIN_CUDA_TRY(cudaMalloc(&st.info_dev, INFO_WORDS * sizeof(int32_t)));
-        SPIN_CUDA_TRY(cudaMallocHost(&st.info_host, INFO_WORDS * sizeof(int32_t)));
-        SPIN_CUDA_TRY(cudaMallocHost(&st.norms_host, 4 * sizeof(double)));
+        SPIN_CUDA_TRY(cudaMalloc(&st.info_dev, CTL_BYTES));
+        SPIN_CUDA_TRY(cudaMemset(st.info_dev, 0, CTL_BYTES));
+        SPIN_CUDA_TRY(cudaMallocHost(&st.info_host, CTL_BYTES));
         SPIN_CUDA_TRY(cudaMalloc(&st.err_dev, sizeof(int)));
         SPIN_CUDA_TRY(cudaMemset(st.err_dev, 0, sizeof(int)));
     }
@@ -150,17 +162,25 @@ struct Run {
 };
 
 
-// Bracket one launch with events when the stream's profiler is on.
+// Bracket one launch with events when the stream's profiler is on.  gate
+// (optional, device int): the launch is gated on it; its value just before
+// the launch is kept so that profile_stop can drop the flops and bytes of a
+// launch that did nothing.
 struct ProfScope {
     Profiler* p;
     cudaStream_t s;
     ProfEntry e;
     bool active;
     ProfScope(Profiler* prof, cudaStream_t st, int kind, int depth, int64_t m, int64_t n, int64_t k, double flops,
-              double bytes)
+              double bytes, const int* gate = nullptr)
         : p(prof), s(st), active(prof != nullptr && prof->on && (int)prof->entries.size() < prof->max_records) {
         if (!active) return;
         e.rec = spin_prof_record{kind, depth, m, n, k, flops, bytes, 0.0};
+        e.gate_slot = -1;
+        if (gate != nullptr && p->flags != nullptr && (int)p->entries.size() < p->flags_cap) {
+            e.gate_slot = (int)p->entries.size();
+            cudaMemcpyAsync(p->flags + e.gate_slot, gate, sizeof(int), cudaMemcpyDeviceToDevice, s);
+        }
         e.start = p->event();
         e.stop = p->event();
         cudaEventRecord(e.start, s);
@@ -176,7 +196,7 @@ int gemm_f64_prof(Run& r, int depth, int64_t m, int64_t n, int64_t k, double alp
                   const double* B, int64_t ldb, double beta, const double* C, int64_t ldc, double* D, int64_t ldd) {
     const double flops = 2.0 * (double)m * (double)n * (double)k;
     const double bytes = 8.0 * ((double)m * k + (double)k * n + (double)m * n * (beta != 0.0 ? 2.0 : 1.0));
-    ProfScope ps(r.prof, r.s, SPIN_KERNEL_GEMM_F64, depth, m, n, k, flops, bytes);
+    ProfScope ps(r.prof, r.s, SPIN_KERNEL_GEMM_F64, depth, m, n, k, flops, bytes, nullptr);
     return launch_gemm_f64(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, r.s);
 }
 
@@ -299,17 +319,17 @@ int check_common(const void* A, int64_t lda, const void* X, int64_t ldx, int64_t
 }
 
 int read_info(StreamState* st, cudaStream_t s, spin_info* info) {
-    SPIN_CUDA_TRY(cudaMemcpyAsync(st->info_host, st->info_dev, INFO_WORDS * sizeof(int32_t),
-                                  cudaMemcpyDeviceToHost, s));
+    SPIN_CUDA_TRY(cudaMemcpyAsync(st->info_host, st->info_dev, CTL_BYTES, cudaMemcpyDeviceToHost, s));
     SPIN_CUDA_TRY(cudaStreamSynchronize(s));
     const int32_t* h = st->info_host;
-    int status = h[INFO_STATUS] ? h[INFO_STATUS] : st->last_host_status;
+    const int status = h[INFO_STATUS];
     if (info) {
+        // a leaf's failure records the leaf and column; a refinement status -1, -1
         info->status = status;
-        info->refine_iters = st->last_refine_iters;
-        info->fail_leaf = h[INFO_STATUS] ? h[INFO_LEAF] : -1;
-        info->fail_col = h[INFO_STATUS] ? h[INFO_COL] : -1;
-        info->rel_residual = st->last_rel;
+        info->refine_iters = st->last_mixed ? h[CTL_ITERS] : 0;
+        info->fail_leaf = status ? h[INFO_LEAF] : -1;
+        info->fail_col = status ? h[INFO_COL] : -1;
+        info->rel_residual = st->last_mixed ? *(const double*)(h + CTL_REL) : -1.0;
         info->pretransformed = st->last_pretransformed;
         info->reserved = 0;
     }
@@ -388,65 +408,61 @@ size_t workspace_bytes_for(int64_t n, int64_t leaf, const spin_opts& o) {
 // in full: after a step the true residual is dominated by the previous
 // residual's own rounding error, which an update of the form R - A (dX)
 // cannot see.  Stops when ||AX - I||_F / (||A||_F ||X||_F) <= tol.
+//
+// The stopping decision is taken on the device (refine.cu): rounds
+// 0 .. max_refine are all enqueued, each gated on the stream's active flag,
+// so the call never waits for the host between steps.
 int refine(Run& r, StreamState* st, const double* A, int64_t lda, double* X, int64_t ldx, int64_t n,
            const spin_opts& o, const MixLayout& L, unsigned char* ws) {
     cudaStream_t s = r.s;
     double* R = (double*)ws;
     double* norms = (double*)(ws + L.off_norms);
+    int* act = st->active();
     const int64_t ld = tc_ld(n);
     OzakiCachedA ca{(uint16_t*)(ws + L.off_apl), (int*)(ws + L.off_apl + (size_t)L.sr * n * ld * 2)};
     void* scratch = ws + L.off_scratch;
+    // a leaf that failed leaves the matrix switched off: nothing below runs
+    RET(launch_refine_init(st->info_dev, 1, act, st->rel(), st->iters(), s));
     SPIN_CUDA_TRY(cudaMemsetAsync(norms, 0, 3 * sizeof(double), s));
     {
-        ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 8.0 * n * n + 2.0 * L.sr * n * n);
-        RET(ozaki_split_a(A, lda, n, n, L.sr, &ca, &norms[0], s));
+        ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 8.0 * n * n + 2.0 * L.sr * n * n, act);
+        RET(ozaki_split_a(A, lda, n, n, L.sr, &ca, &norms[0], s, act));
     }
     const double f = 2.0 * (double)n * n * n;
-    st->last_refine_iters = 0;
-    st->last_rel = -1.0;
-    const bool verbose = getenv("SPIN_VERBOSE") != nullptr;
-    for (int it = 0;; it++) {
-        const int sr = L.sr;
-        const int pairs = sr * (sr + 1) / 2;
+    const int sr = L.sr;
+    const int pairs = sr * (sr + 1) / 2;
+    for (int it = 0; it <= o.max_refine; it++) {
         SPIN_CUDA_TRY(cudaMemsetAsync(norms + 1, 0, 2 * sizeof(double), s));
         SplitPlan sp;
         RET(plan_ozaki(0, n, n, sr, scratch, L.scratch, &sp));
         sp.a = ca.planes;
         sp.ea = ca.exps;
         {
-            ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 8.0 * n * n + 2.0 * sr * n * n);
-            RET(split_b_ozaki(sp, X, ldx, n, n, &norms[1], s));
+            ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 8.0 * n * n + 2.0 * sr * n * n, act);
+            RET(split_b_ozaki(sp, X, ldx, n, n, &norms[1], s, act));
         }
         {
-            ProfScope ps(r.prof, s, SPIN_KERNEL_RESIDUAL, -1, n, n, n, pairs * f,
-                         2.0 * sr * 2.0 * n * n + 8.0 * n * n);
-            RET(product_ozaki(sp, n, n, n, -1.0, 0.0, nullptr, 0, R, n, 1, &norms[2], r.err, s));
+            ProfScope ps(r.prof, s, SPIN_KERNEL_RESIDUAL, -1, n, n, n, pairs * f, 2.0 * sr * 2.0 * n * n + 8.0 * n * n,
+                         act);
+            RET(product_ozaki(sp, n, n, n, -1.0, 0.0, nullptr, 0, R, n, 1, &norms[2], r.err, s, act));
         }
-        SPIN_CUDA_TRY(cudaMemcpyAsync(st->norms_host, norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        SPIN_CUDA_TRY(cudaStreamSynchronize(s));
-        const double* h = st->norms_host;
-        const double rel = std::sqrt(h[2]) / (std::sqrt(h[0]) * std::sqrt(h[1]));
-        if (verbose) fprintf(stderr, "[spin] refine it=%d slices=%d rel=%.3e\n", it, sr, rel);
-        st->last_rel = rel;
-        st->last_refine_iters = it;
-        if (rel <= o.tol) return SPIN_OK;
-        if (!(rel == rel) || it >= o.max_refine) {
-            st->last_host_status = SPIN_ERR_NOT_CONVERGED;
-            return SPIN_OK;
-        }
+        RET(launch_refine_decide(norms, norms + 1, norms + 2, 1, o.tol, it, o.max_refine, act, st->rel(),
+                                 st->iters(), st->info_dev, s));
+        if (it == o.max_refine) break;
         // X <- X + X R with three-plane BF16 splits and six products (~2^-22
         // relative): the correction's own error enters the next residual
         // amplified by ~kappa * rel, so it needs more than bf16x3's ~2^-16.
         SplitPlan up;
         RET(plan_bf16x6(n, n, n, scratch, L.scratch, &up));
         {
-            ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 28.0 * n * n);
-            RET(split_a_bf16x6(up, X, ldx, n, n, s));
-            RET(split_b_bf16x6(up, R, n, n, n, s));
+            ProfScope ps(r.prof, s, SPIN_KERNEL_SPLIT, -1, n, n, 0, 0.0, 28.0 * n * n, act);
+            RET(split_a_bf16x6(up, X, ldx, n, n, s, act));
+            RET(split_b_bf16x6(up, R, n, n, n, s, act));
         }
-        ProfScope ps(r.prof, s, SPIN_KERNEL_UPDATE, -1, n, n, n, 6.0 * f, 12.0 * n * n + 16.0 * n * n);
-        RET(product_bf16x6(up, n, n, n, 1.0, 1.0, X, ldx, X, ldx, r.err, s));
+        ProfScope ps(r.prof, s, SPIN_KERNEL_UPDATE, -1, n, n, n, 6.0 * f, 12.0 * n * n + 16.0 * n * n, act);
+        RET(product_bf16x6(up, n, n, n, 1.0, 1.0, X, ldx, X, ldx, r.err, s, act));
     }
+    return launch_refine_finish(r.err, st->info_dev, 1, s);
 }
 
 // One attempt: the recursion on A (pretransform 0) or on U^T A V with the
@@ -455,9 +471,7 @@ int refine(Run& r, StreamState* st, const double* A, int64_t lda, double* X, int
 int enqueue_once(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, int64_t leaf, const spin_opts& o,
                  bool rbt, StreamState* st, cudaStream_t s, unsigned char* ws) {
     const bool mixed = o.precision != SPIN_FP64;
-    st->last_host_status = 0;
-    st->last_refine_iters = 0;
-    st->last_rel = -1.0;
+    st->last_mixed = mixed ? 1 : 0;
     st->last_pretransformed = rbt ? 1 : 0;
     SPIN_CUDA_TRY(cudaMemsetAsync(st->info_dev, 0, INFO_WORDS * sizeof(int32_t), s));
     Run r{s, st->info_dev, 0, leaf, st->prof.on ? &st->prof : nullptr};
@@ -494,17 +508,8 @@ int enqueue_once(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n
     SPIN_CUDA_TRY(cudaMemsetAsync(st->err_dev, 0, sizeof(int), s));
     RET(inv_rec(r, 0, Ain, lda_in, Xout, ldx_out, n_in, (double*)inner));
     if (rbt) RET(launch_rbt_backward(Xout, R.np, kRbtDepth, (const double*)ws, X, ldx, n, s));
-    // a singular leaf makes the refinement meaningless: stop here
-    SPIN_CUDA_TRY(cudaMemcpyAsync(st->info_host, st->info_dev, INFO_WORDS * sizeof(int32_t),
-                                  cudaMemcpyDeviceToHost, s));
-    SPIN_CUDA_TRY(cudaStreamSynchronize(s));
-    if (st->info_host[INFO_STATUS] != 0) return SPIN_OK;
     // the refinement's layout for order n fits in the recursion's (order >= n)
-    RET(refine(r, st, A, lda, X, ldx, n, o, mix_layout(n, leaf, o), inner));
-    int err = 0;
-    SPIN_CUDA_TRY(cudaMemcpy(&err, st->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) st->last_host_status = err;
-    return SPIN_OK;
+    return refine(r, st, A, lda, X, ldx, n, o, mix_layout(n, leaf, o), inner);
 }
 
 int enqueue(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, const spin_opts& o,
@@ -859,6 +864,17 @@ int spin_profile_start(spin_stream_t stream, int max_records) {
     }
     p.entries.clear();
     p.max_records = max_records;
+    // one device int per possible record for the gate copies (grown here,
+    // outside the timed region of a caller that profiles)
+    if (p.flags_cap < max_records) {
+        if (p.flags) cudaFree(p.flags);
+        p.flags = nullptr;
+        p.flags_cap = 0;
+        if (max_records > 0) {
+            SPIN_CUDA_TRY(cudaMalloc(&p.flags, (size_t)max_records * sizeof(int)));
+            p.flags_cap = max_records;
+        }
+    }
     p.on = true;
     return SPIN_OK;
 }
@@ -870,11 +886,22 @@ int spin_profile_stop(spin_stream_t stream, spin_prof_record* out, int max, int*
     Profiler& p = st->prof;
     p.on = false;
     SPIN_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<int> gates;
+    if (p.flags != nullptr && !p.entries.empty()) {
+        gates.resize(std::min<size_t>(p.entries.size(), (size_t)p.flags_cap));
+        SPIN_CUDA_TRY(cudaMemcpy(gates.data(), p.flags, gates.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    }
     int c = 0;
     for (auto& e : p.entries) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e.start, e.stop);
         e.rec.ms = ms;
+        if (e.gate_slot >= 0 && e.gate_slot < (int)gates.size() && gates[e.gate_slot] == 0) {
+            // gated off on the device: the launch returned at once
+            e.rec.kind = SPIN_KERNEL_OTHER;
+            e.rec.flops = 0.0;
+            e.rec.bytes = 0.0;
+        }
         if (out != nullptr && c < max) out[c] = e.rec;
         c++;
         p.pool.push_back(e.start);

@@ -16,9 +16,10 @@
 // per split and per product; the digit or BF16 planes of every matrix of the
 // bucket sit in one arena, one problem after the other), FP64-class Schur
 // complements at the top fp64_levels levels, then Newton-Schulz refinement
-// of every matrix with FP64-class residuals (cached digit planes of A).
-// The refinement reads the residual norms on the host between iterations,
-// so a mixed call returns when the batch is done.
+// of every matrix with FP64-class residuals (cached digit planes of A).  The
+// refinement's stopping decisions are taken per matrix on the device
+// (refine.cu): every round is part of the captured graph and a matrix that
+// has converged is switched off, so a mixed batch is one graph replay too.
 #include <stdio.h>
 #include <string.h>
 
@@ -72,10 +73,10 @@ struct BatchPlan {
     unsigned char* arena = nullptr;
     size_t arena_bytes = 0;
     double* norms = nullptr;       // device: [3][count] sums of squares of A, X, R (sorted order)
-    double* norms_host = nullptr;  // pinned copy
+    int* active = nullptr;         // device: [count] refinement still running
+    double* rel = nullptr;         // device: [count] latest relative residual
+    int* iters = nullptr;          // device: [count] refinement steps taken
     int* err = nullptr;            // device: SPIN_ERR_TIMEOUT from a bounded wait
-    int refine_iters = 0;
-    double worst_rel = -1.0;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;  // private stream the launch sequence is captured on
     cudaStream_t streams[kStreams] = {};
@@ -89,12 +90,16 @@ void free_plan(BatchPlan& p) {
     if (p.exec) cudaGraphExecDestroy(p.exec);
     cudaFree(p.arena);
     cudaFree(p.norms);
+    cudaFree(p.active);
+    cudaFree(p.rel);
+    cudaFree(p.iters);
     cudaFree(p.err);
-    if (p.norms_host) cudaFreeHost(p.norms_host);
     p.arena = nullptr;
     p.arena_bytes = 0;
     p.norms = nullptr;
-    p.norms_host = nullptr;
+    p.active = nullptr;
+    p.rel = nullptr;
+    p.iters = nullptr;
     p.err = nullptr;
     cudaFree((void*)p.a_base);
     cudaFree(p.a_ld);
@@ -306,126 +311,77 @@ int binv_mixed(BRun& r, BMix& x, int depth, BatchView A, BatchView X, const doub
     return SPIN_OK;
 }
 
-// Refinement of every matrix: residuals R(z) = I - A(z) X(z) FP64-class
-// (digit planes, A's cached), X(z) <- X(z) + X(z) R(z) in the six-product
-// BF16 form, until every ||R||_F / (||A||_F ||X||_F) <= tol.  R lives in
-// each matrix's workspace.  Statuses go to the records (sorted order).
-int brefine(BatchPlan& p) {
+// Refinement of the matrices of one bucket, enqueued on s: residuals
+// R(z) = I - A(z) X(z) FP64-class (digit planes, A's cached), X(z) <- X(z) +
+// X(z) R(z) in the six-product BF16 form, rounds 0 .. max_refine all
+// enqueued; each matrix's decision is taken on the device and a matrix that
+// has converged (or failed) is switched off, its launches returning at once.
+// R lives in each matrix's workspace.  Statuses go to the records (sorted
+// order): SPIN_ERR_NOT_CONVERGED when the cap is reached above tol.
+int bucket_refine(BatchPlan& p, const Bucket& b, cudaStream_t s) {
     const int count = p.count;
-    double* nA = p.norms;
-    double* nX = p.norms + count;
-    double* nR = p.norms + 2 * count;
     const int sr = p.sr;
-    std::vector<int> active(p.buckets.size(), 1);
-    auto views = [&](const Bucket& b, BatchView& Av, BatchView& Xv, BatchView& Rv) {
-        Av = BatchView{p.a_base + b.first, p.a_ld + b.first, 0, 0, 0};
-        Xv = BatchView{(const double* const*)(p.x_base + b.first), nullptr, b.n, 0, 0};
-        Rv = BatchView{(const double* const*)(p.w_base + b.first), nullptr, b.n, 0, 0};
-    };
-    for (size_t bi = 0; bi < p.buckets.size(); bi++) {  // cached digit planes of A and ||A||
-        const Bucket& b = p.buckets[bi];
-        BatchView Av, Xv, Rv;
-        views(b, Av, Xv, Rv);
-        unsigned char* cache = p.arena + b.arena_offset + (size_t)b.count * b.scratch_per;
-        const int64_t ld = tc_ld(b.n);
-        uint16_t* planes = (uint16_t*)cache;
-        int* ex = after<int>(planes, (size_t)b.count * sr * b.n * ld * 2);
-        cudaStream_t s = p.streams[b.stream];
-        SPIN_CUDA_TRY(cudaMemsetAsync(nA + b.first, 0, b.count * sizeof(double), s));
+    BatchView Av{p.a_base + b.first, p.a_ld + b.first, 0, 0, 0};
+    BatchView Xv{(const double* const*)(p.x_base + b.first), nullptr, b.n, 0, 0};
+    BatchView Rv{(const double* const*)(p.w_base + b.first), nullptr, b.n, 0, 0};
+    int* act = p.active + b.first;
+    double* nA = p.norms + b.first;
+    double* nX = p.norms + count + b.first;
+    double* nR = p.norms + 2 * count + b.first;
+    int32_t* rec = p.records + (int64_t)b.first * INFO_WORDS;
+    const int64_t ld = tc_ld(b.n);
+    unsigned char* scratch = p.arena + b.arena_offset;
+    unsigned char* cache = scratch + (size_t)b.count * b.scratch_per;
+    uint16_t* aplanes = (uint16_t*)cache;
+    int* aex = after<int>(aplanes, (size_t)b.count * sr * b.n * ld * 2);
+    uint16_t* xplanes = (uint16_t*)scratch;
+    int* xex = after<int>(xplanes, (size_t)b.count * sr * b.n * ld * 2);
+    uint16_t* xp = (uint16_t*)scratch;  // update: three planes of X, then of R
+    uint16_t* rp = xp + (int64_t)b.count * 3 * b.n * ld;
+    BRET(launch_refine_init(rec, b.count, act, p.rel + b.first, p.iters + b.first, s));
+    SPIN_CUDA_TRY(cudaMemsetAsync(nA, 0, b.count * sizeof(double), s));
+    p.kernels += 3;
+    BRET(launch_ozaki_split_batched(Av, (int)b.n, (int)b.n, false, sr, aex, aplanes, ld, nA, b.count, s, act));
+    for (int it = 0; it <= p.max_refine; it++) {
+        SPIN_CUDA_TRY(cudaMemsetAsync(nX, 0, b.count * sizeof(double), s));
+        SPIN_CUDA_TRY(cudaMemsetAsync(nR, 0, b.count * sizeof(double), s));
+        BRET(launch_ozaki_split_batched(Xv, (int)b.n, (int)b.n, true, sr, xex, xplanes, ld, nX, b.count, s, act));
+        TcGemmParams q = {};
+        q.M = q.N = q.K = (int)b.n;
+        tc_pairs_ozaki(q, sr);
+        q.alpha = -1.0;
+        q.beta = 0.0;
+        q.add_identity = 1;
+        q.sumsq = nR;
+        q.err = p.err;
+        q.active = act;
+        q.row_exp = aex;
+        q.col_exp = xex;
+        q.batch = b.count;
+        q.d_base = p.w_base + b.first;
+        q.d_ld = b.n;
+        BRET(launch_tc_gemm(TcOperand{aplanes, (int)b.n, sr, ld}, TcOperand{xplanes, (int)b.n, sr, ld}, q, s));
+        BRET(launch_refine_decide(nA, nX, nR, b.count, p.tol, it, p.max_refine, act, p.rel + b.first,
+                                  p.iters + b.first, rec, s));
+        p.kernels += 6;
+        if (it == p.max_refine) break;
+        BRET(launch_split_planes_batched(Xv, (int)b.n, (int)b.n, false, 3, xp, ld, b.count, s, act));
+        BRET(launch_split_planes_batched(Rv, (int)b.n, (int)b.n, true, 3, rp, ld, b.count, s, act));
+        TcGemmParams u = {};
+        u.M = u.N = u.K = (int)b.n;
+        tc_pairs_bf16x6(u);
+        u.alpha = 1.0;
+        u.beta = 1.0;
+        u.err = p.err;
+        u.active = act;
+        u.batch = b.count;
+        u.c_base = Xv.base;
+        u.c_ld = b.n;
+        u.d_base = p.x_base + b.first;
+        u.d_ld = b.n;
         p.kernels += 3;
-        BRET(launch_ozaki_split_batched(Av, (int)b.n, (int)b.n, false, sr, ex, planes, ld, nA + b.first, b.count, s));
+        BRET(launch_tc_gemm(TcOperand{xp, (int)b.n, 3, ld}, TcOperand{rp, (int)b.n, 3, ld}, u, s));
     }
-    std::vector<double> rel(count, -1.0);
-    for (int it = 0;; it++) {
-        for (size_t bi = 0; bi < p.buckets.size(); bi++) {
-            if (!active[bi]) continue;
-            const Bucket& b = p.buckets[bi];
-            BatchView Av, Xv, Rv;
-            views(b, Av, Xv, Rv);
-            const int64_t ld = tc_ld(b.n);
-            unsigned char* scratch = p.arena + b.arena_offset;
-            unsigned char* cache = scratch + (size_t)b.count * b.scratch_per;
-            uint16_t* aplanes = (uint16_t*)cache;
-            int* aex = after<int>(aplanes, (size_t)b.count * sr * b.n * ld * 2);
-            uint16_t* xplanes = (uint16_t*)scratch;
-            int* xex = after<int>(xplanes, (size_t)b.count * sr * b.n * ld * 2);
-            cudaStream_t s = p.streams[b.stream];
-            SPIN_CUDA_TRY(cudaMemsetAsync(nX + b.first, 0, b.count * sizeof(double), s));
-            SPIN_CUDA_TRY(cudaMemsetAsync(nR + b.first, 0, b.count * sizeof(double), s));
-            BRET(launch_ozaki_split_batched(Xv, (int)b.n, (int)b.n, true, sr, xex, xplanes, ld, nX + b.first,
-                                            b.count, s));
-            TcGemmParams q = {};
-            q.M = q.N = q.K = (int)b.n;
-            tc_pairs_ozaki(q, sr);
-            q.alpha = -1.0;
-            q.beta = 0.0;
-            q.add_identity = 1;
-            q.sumsq = nR + b.first;
-            q.err = p.err;
-            q.row_exp = aex;
-            q.col_exp = xex;
-            q.batch = b.count;
-            q.d_base = p.w_base + b.first;
-            q.d_ld = b.n;
-            p.kernels += 5;
-            BRET(launch_tc_gemm(TcOperand{aplanes, (int)b.n, sr, ld}, TcOperand{xplanes, (int)b.n, sr, ld}, q, s));
-        }
-        for (int i = 0; i < kStreams; i++) SPIN_CUDA_TRY(cudaStreamSynchronize(p.streams[i]));
-        SPIN_CUDA_TRY(cudaMemcpy(p.norms_host, p.norms, 3 * (size_t)count * sizeof(double), cudaMemcpyDeviceToHost));
-        bool all_done = true;
-        for (size_t bi = 0; bi < p.buckets.size(); bi++) {
-            const Bucket& b = p.buckets[bi];
-            if (!active[bi]) continue;
-            bool bucket_done = true;
-            for (int z = b.first; z < b.first + b.count; z++) {
-                const double* h = p.norms_host;
-                rel[z] = std::sqrt(h[2 * count + z]) / (std::sqrt(h[z]) * std::sqrt(h[count + z]));
-                if (!(rel[z] <= p.tol) && rel[z] == rel[z]) bucket_done = false;  // NaN: a singular leaf
-            }
-            if (bucket_done) active[bi] = 0;
-            all_done = all_done && bucket_done;
-        }
-        p.refine_iters = it;
-        if (all_done || it >= p.max_refine) break;
-        for (size_t bi = 0; bi < p.buckets.size(); bi++) {  // X <- X + X R
-            if (!active[bi]) continue;
-            const Bucket& b = p.buckets[bi];
-            BatchView Av, Xv, Rv;
-            views(b, Av, Xv, Rv);
-            const int64_t ld = tc_ld(b.n);
-            uint16_t* xp = (uint16_t*)(p.arena + b.arena_offset);
-            uint16_t* rp = xp + (int64_t)b.count * 3 * b.n * ld;
-            cudaStream_t s = p.streams[b.stream];
-            BRET(launch_split_planes_batched(Xv, (int)b.n, (int)b.n, false, 3, xp, ld, b.count, s));
-            BRET(launch_split_planes_batched(Rv, (int)b.n, (int)b.n, true, 3, rp, ld, b.count, s));
-            TcGemmParams q = {};
-            q.M = q.N = q.K = (int)b.n;
-            tc_pairs_bf16x6(q);
-            q.alpha = 1.0;
-            q.beta = 1.0;
-            q.err = p.err;
-            q.batch = b.count;
-            q.c_base = Xv.base;
-            q.c_ld = b.n;
-            q.d_base = p.x_base + b.first;
-            q.d_ld = b.n;
-            p.kernels += 3;
-            BRET(launch_tc_gemm(TcOperand{xp, (int)b.n, 3, ld}, TcOperand{rp, (int)b.n, 3, ld}, q, s));
-        }
-    }
-    // statuses: a failed leaf stays SPIN_ERR_SINGULAR; else converged or not
-    std::vector<int32_t> rec((size_t)count * INFO_WORDS);
-    SPIN_CUDA_TRY(cudaMemcpy(rec.data(), p.records, rec.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    int herr = 0;
-    SPIN_CUDA_TRY(cudaMemcpy(&herr, p.err, sizeof(int), cudaMemcpyDeviceToHost));
-    p.worst_rel = 0.0;
-    for (int z = 0; z < count; z++) {
-        int32_t& st = rec[(size_t)z * INFO_WORDS + INFO_STATUS];
-        if (st == 0 && herr) st = herr;
-        if (st == 0 && !(rel[z] <= p.tol)) st = SPIN_ERR_NOT_CONVERGED;
-        if (rel[z] == rel[z]) p.worst_rel = std::max(p.worst_rel, rel[z]);
-    }
-    SPIN_CUDA_TRY(cudaMemcpy(p.records, rec.data(), rec.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     return SPIN_OK;
 }
 
@@ -446,8 +402,6 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
     p.max_refine = o.max_refine;
     p.fp64_levels = o.fp64_levels;
     p.sr = o.residual_slices > 0 ? o.residual_slices : (o.tol >= 1e-11 ? 6 : 7);
-    p.refine_iters = 0;
-    p.worst_rel = -1.0;
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] < n[b]; });
@@ -487,7 +441,9 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
             return SPIN_ERR_OOM;
         }
         SPIN_CUDA_TRY(cudaMalloc(&p.norms, 3 * (size_t)count * sizeof(double)));
-        SPIN_CUDA_TRY(cudaMallocHost(&p.norms_host, 3 * (size_t)count * sizeof(double)));
+        SPIN_CUDA_TRY(cudaMalloc(&p.active, (size_t)count * sizeof(int)));
+        SPIN_CUDA_TRY(cudaMalloc(&p.rel, (size_t)count * sizeof(double)));
+        SPIN_CUDA_TRY(cudaMalloc(&p.iters, (size_t)count * sizeof(int)));
         SPIN_CUDA_TRY(cudaMalloc(&p.err, sizeof(int)));
     }
     p.ws_bytes = ws_total * sizeof(double);
@@ -554,6 +510,7 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
         if (mixed) {
             BMix x{p.arena + b.arena_offset, b.count, p.fp64_levels, p.err, &p.kernels, p.streams[si]};
             rc = binv_mixed(r, x, 0, Av, Xv, (const double* const*)(p.w_base + b.first), 0, b.n);
+            if (rc == SPIN_OK) rc = bucket_refine(p, b, p.streams[si]);
         } else {
             rc = binv(r, Av, Xv, (const double* const*)(p.w_base + b.first), 0, b.n);
         }
@@ -565,6 +522,10 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
             record_cuda_error(e2, "batched join", __FILE__, __LINE__);
             rc = SPIN_ERR_CUDA;
         }
+    }
+    if (rc == SPIN_OK && mixed) {
+        p.kernels++;
+        rc = launch_refine_finish(p.err, p.records, count, s);
     }
     cudaError_t ec = cudaStreamEndCapture(s, &graph);
     if (rc != SPIN_OK) {
@@ -640,14 +601,7 @@ extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, d
         p.key = key;
     }
     SPIN_CUDA_TRY(cudaGraphLaunch(p.exec, s));
-    if (mixed) {
-        SPIN_CUDA_TRY(cudaStreamSynchronize(s));
-        p.kernels = p.graph_kernels;
-        int rc = brefine(p);
-        if (rc != SPIN_OK) return rc;
-    } else {
-        p.kernels = p.graph_kernels;
-    }
+    p.kernels = p.graph_kernels;
     // statuses go to the caller's array outside the graph, so that a new
     // info_dev does not force a new capture
     if (info_dev != nullptr) {
@@ -655,7 +609,7 @@ extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, d
         scatter_status_kernel<<<(count + 255) / 256, 256, 0, s>>>(p.records, p.user_index, count, info_dev);
         SPIN_CUDA_TRY(cudaGetLastError());
     }
-    if (o.blocking || mixed) SPIN_CUDA_TRY(cudaStreamSynchronize(s));
+    if (o.blocking) SPIN_CUDA_TRY(cudaStreamSynchronize(s));
     return SPIN_OK;
 }
 
@@ -663,8 +617,23 @@ extern "C" int spin_batched_refine_info(spin_stream_t stream, int* refine_iters,
     std::lock_guard<std::mutex> lk(g_bmu);
     auto it = g_plans.find((cudaStream_t)stream);
     if (it == g_plans.end() || it->second.exec == nullptr) return SPIN_ERR_INVALID_ARG;
-    if (refine_iters) *refine_iters = it->second.refine_iters;
-    if (worst_rel) *worst_rel = it->second.worst_rel;
+    const BatchPlan& p = it->second;
+    int most = 0;
+    double worst = -1.0;
+    if (p.precision != SPIN_FP64 && p.count > 0) {
+        SPIN_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+        std::vector<double> rel(p.count);
+        std::vector<int> its(p.count);
+        SPIN_CUDA_TRY(cudaMemcpy(rel.data(), p.rel, p.count * sizeof(double), cudaMemcpyDeviceToHost));
+        SPIN_CUDA_TRY(cudaMemcpy(its.data(), p.iters, p.count * sizeof(int), cudaMemcpyDeviceToHost));
+        worst = 0.0;
+        for (int z = 0; z < p.count; z++) {
+            most = std::max(most, its[z]);
+            if (rel[z] == rel[z]) worst = std::max(worst, rel[z]);  // NaN: a matrix whose leaf failed
+        }
+    }
+    if (refine_iters) *refine_iters = most;
+    if (worst_rel) *worst_rel = worst;
     return SPIN_OK;
 }
 

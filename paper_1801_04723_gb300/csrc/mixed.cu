@@ -117,8 +117,8 @@ int split_a_ozaki(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, 
     return launch_ozaki_split(A, lda, (int)m, (int)k, false, sp.slices, sp.ea, sp.a, sp.ld, sumsq, s);
 }
 int split_b_ozaki(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, double* sumsq,
-                  cudaStream_t s) {
-    return launch_ozaki_split(B, ldb, (int)k, (int)n, true, sp.slices, sp.eb, sp.b, sp.ld, sumsq, s);
+                  cudaStream_t s, const int* active) {
+    return launch_ozaki_split(B, ldb, (int)k, (int)n, true, sp.slices, sp.eb, sp.b, sp.ld, sumsq, s, active);
 }
 
 int product_bf16x3(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
@@ -149,15 +149,17 @@ int plan_bf16x6(int64_t m, int64_t n, int64_t k, void* scratch, size_t bytes, Sp
     return SPIN_OK;
 }
 
-int split_a_bf16x6(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, int64_t k, cudaStream_t s) {
-    return launch_split_bf16x3p(A, lda, (int)m, (int)k, false, sp.a, sp.ld, s);
+int split_a_bf16x6(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, int64_t k, cudaStream_t s,
+                   const int* active) {
+    return launch_split_bf16x3p(A, lda, (int)m, (int)k, false, sp.a, sp.ld, s, active);
 }
-int split_b_bf16x6(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, cudaStream_t s) {
-    return launch_split_bf16x3p(B, ldb, (int)k, (int)n, true, sp.b, sp.ld, s);
+int split_b_bf16x6(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, cudaStream_t s,
+                   const int* active) {
+    return launch_split_bf16x3p(B, ldb, (int)k, (int)n, true, sp.b, sp.ld, s, active);
 }
 
 int product_bf16x6(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
-                   int64_t ldc, double* D, int64_t ldd, int* err, cudaStream_t s) {
+                   int64_t ldc, double* D, int64_t ldd, int* err, cudaStream_t s, const int* active) {
     TcGemmParams p = {};
     p.M = (int)m;
     p.N = (int)n;
@@ -170,12 +172,14 @@ int product_bf16x6(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double 
     p.D = D;
     p.ldd = ldd;
     p.err = err;
+    p.active = active;
     TcOperand oa{sp.a, (int)m, 3, sp.ld}, ob{sp.b, (int)n, 3, sp.ld};
     return launch_tc_gemm(oa, ob, p, s);
 }
 
 int product_ozaki(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
-                  int64_t ldc, double* D, int64_t ldd, int add_identity, double* sumsq, int* err, cudaStream_t s) {
+                  int64_t ldc, double* D, int64_t ldd, int add_identity, double* sumsq, int* err, cudaStream_t s,
+                  const int* active) {
     const int slices = sp.slices;
     TcGemmParams p = {};
     p.M = (int)m;
@@ -193,6 +197,7 @@ int product_ozaki(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double a
     p.add_identity = add_identity;
     p.sumsq = sumsq;
     p.err = err;
+    p.active = active;
     TcOperand oa{sp.a, (int)m, slices, sp.ld}, ob{sp.b, (int)n, slices, sp.ld};
     return launch_tc_gemm(oa, ob, p, s);
 }
@@ -230,9 +235,9 @@ int gemm_ozaki(int64_t m, int64_t n, int64_t k, double alpha, const double* A, i
 }
 
 int ozaki_split_a(const double* A, int64_t lda, int64_t m, int64_t k, int slices, OzakiCachedA* out,
-                  double* sumsq, cudaStream_t s) {
+                  double* sumsq, cudaStream_t s, const int* active) {
     const int64_t ld = tc_ld(k);
-    return launch_ozaki_split(A, lda, (int)m, (int)k, false, slices, out->exps, out->planes, ld, sumsq, s);
+    return launch_ozaki_split(A, lda, (int)m, (int)k, false, slices, out->exps, out->planes, ld, sumsq, s, active);
 }
 
 }  // namespace spin

@@ -65,22 +65,39 @@ int plan_bf16x3(int64_t m, int64_t n, int64_t k, void* scratch, size_t bytes, Sp
 int plan_ozaki(int64_t m, int64_t n, int64_t k, int slices, void* scratch, size_t bytes, SplitPlan* sp);
 int split_a_bf16x3(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, int64_t k, cudaStream_t s);
 int split_b_bf16x3(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, cudaStream_t s);
+// active (optional, device int): the split / product runs only while *active != 0.
 int split_a_ozaki(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, int64_t k, double* sumsq,
                   cudaStream_t s);
 int split_b_ozaki(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, double* sumsq,
-                  cudaStream_t s);
+                  cudaStream_t s, const int* active = nullptr);
 int product_bf16x3(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
                    int64_t ldc, double* D, int64_t ldd, int* err, cudaStream_t s);
 // Three-plane form (hi, mid, lo) with the six products of weight <= 2^-16.
 int plan_bf16x6(int64_t m, int64_t n, int64_t k, void* scratch, size_t bytes, SplitPlan* sp);
-int split_a_bf16x6(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, int64_t k, cudaStream_t s);
-int split_b_bf16x6(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, cudaStream_t s);
+int split_a_bf16x6(const SplitPlan& sp, const double* A, int64_t lda, int64_t m, int64_t k, cudaStream_t s,
+                   const int* active = nullptr);
+int split_b_bf16x6(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k, int64_t n, cudaStream_t s,
+                   const int* active = nullptr);
 int product_bf16x6(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
-                   int64_t ldc, double* D, int64_t ldd, int* err, cudaStream_t s);
+                   int64_t ldc, double* D, int64_t ldd, int* err, cudaStream_t s, const int* active = nullptr);
 int product_ozaki(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
-                  int64_t ldc, double* D, int64_t ldd, int add_identity, double* sumsq, int* err, cudaStream_t s);
+                  int64_t ldc, double* D, int64_t ldd, int add_identity, double* sumsq, int* err, cudaStream_t s,
+                  const int* active = nullptr);
 
 int ozaki_split_a(const double* A, int64_t lda, int64_t m, int64_t k, int slices, OzakiCachedA* out,
-                  double* sumsq, cudaStream_t s);
+                  double* sumsq, cudaStream_t s, const int* active = nullptr);
+
+// Device-side Newton-Schulz control (refine.cu) for `count` matrices whose
+// info records (INFO_WORDS int32 each) start at `records`:
+//   init    active[z] = (status of z == 0), rel[z] = -1, iters[z] = 0;
+//   decide  for every active z: rel[z] = sqrt(nR[z]) / (sqrt(nA[z]) sqrt(nX[z])),
+//           iters[z] = it; off when rel <= tol, or (recording
+//           SPIN_ERR_NOT_CONVERGED) when rel is not finite or it >= max_refine;
+//   finish  a nonzero *err (a bounded wait that gave up) becomes the status of
+//           every matrix still at SPIN_OK.
+int launch_refine_init(const int32_t* records, int count, int* active, double* rel, int* iters, cudaStream_t s);
+int launch_refine_decide(const double* nA, const double* nX, const double* nR, int count, double tol, int it,
+                         int max_refine, int* active, double* rel, int* iters, int32_t* records, cudaStream_t s);
+int launch_refine_finish(const int* err, int32_t* records, int count, cudaStream_t s);
 
 }  // namespace spin

@@ -316,6 +316,9 @@ template <int BN, bool EXACT, int EPI_WARPS>
 __global__ void __maxnreg__(Epi<EPI_WARPS>::MAXREG)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const TcGemmParams p) {
+    // a problem switched off by its active flag does nothing (every thread
+    // of the CTA reads the same flag, before any barrier or TMEM is set up)
+    if (p.active != nullptr && p.active[p.batch ? blockIdx.y : 0] == 0) return;
     // k-blocks per stage (256-wide exact tiles: one, for a 4-stage ring)
     constexpr int KS = EXACT ? (BN >= 256 ? 1 : KSUB_EXACT) : KSUB_FLOAT;
     // exact mode keeps the FP64 running sums in TMEM when they fit beside the
@@ -574,6 +577,8 @@ template <int PBN, int EPI_WARPS>
 __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(Epi<EPI_WARPS>::MAXREG)
 tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const TcGemmParams p) {
+    // both CTAs of the pair read the same flag: the pair leaves together
+    if (p.active != nullptr && p.active[p.batch ? blockIdx.y : 0] == 0) return;
     using C = PairCfg<PBN>;
     constexpr int HALF = PBN / (EPI_WARPS / 4);
     static_assert(EPI_WARPS % 4 == 0 && PBN % (EPI_WARPS / 4) == 0 && HALF % 16 == 0, "epilogue split");
@@ -778,17 +783,22 @@ __device__ __forceinline__ void split3(double a, uint16_t& hi, uint16_t& mid, ui
 }
 
 // Operand source of a split: one FP64 view, or problem z's view of a batch.
+// act (optional): problem z is split only while act[z] != 0.
 struct SrcOne {
     const double* p;
     int64_t ld;
+    const int* act;
     __device__ __forceinline__ const double* row(int, int r) const { return p + (int64_t)r * ld; }
+    __device__ __forceinline__ bool on(int) const { return act == nullptr || act[0] != 0; }
 };
 struct SrcMany {
     BatchView v;
+    const int* act;
     __device__ __forceinline__ const double* row(int z, int r) const {
         const int64_t l = v.ld_of(z);
         return v.base[z] + (v.r0 + r) * l + v.c0;
     }
+    __device__ __forceinline__ bool on(int z) const { return act == nullptr || act[z] != 0; }
 };
 
 // Every split kernel handles problem z = blockIdx.z: its planes start at
@@ -799,6 +809,7 @@ template <class Src>
 __global__ void split_bf16x3p_rows_kernel(Src src, int rows, int cols, uint16_t* __restrict__ dst, int64_t ldd,
                                           int64_t plane, int64_t dzs) {
     const int z = blockIdx.z;
+    if (!src.on(z)) return;
     dst += z * dzs;
     const int64_t total = (int64_t)rows * cols;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -818,6 +829,7 @@ __global__ void split_bf16x3p_cols_kernel(Src src, int rows, int cols, uint16_t*
                                           int64_t plane, int64_t dzs) {
     __shared__ double tile[32][33];
     const int z = blockIdx.z;
+    if (!src.on(z)) return;
     dst += z * dzs;
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -843,6 +855,7 @@ template <class Src>
 __global__ void split_bf16x2_rows_kernel(Src src, int rows, int cols, uint16_t* __restrict__ dst, int64_t ldd,
                                          int64_t plane, int64_t dzs) {
     const int z = blockIdx.z;
+    if (!src.on(z)) return;
     dst += z * dzs;
     const int64_t total = (int64_t)rows * cols;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -861,6 +874,7 @@ __global__ void split_bf16x2_cols_kernel(Src src, int rows, int cols, uint16_t* 
                                          int64_t plane, int64_t dzs) {
     __shared__ double tile[32][33];
     const int z = blockIdx.z;
+    if (!src.on(z)) return;
     dst += z * dzs;
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -892,6 +906,7 @@ template <class Src>
 __global__ void row_exp_kernel(Src src, int rows, int cols, int* __restrict__ ex, int64_t exs, double* sumsq,
                                int64_t sss) {
     const int z = blockIdx.z;
+    if (!src.on(z)) return;
     const int warps = blockDim.x >> 5;
     const int r = blockIdx.x * warps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -921,6 +936,7 @@ template <class Src>
 __global__ void col_exp_kernel(Src src, int rows, int cols, int rows_per_block, int* __restrict__ ex, int64_t exs,
                                double* sumsq, int64_t sss) {
     const int z = blockIdx.z;
+    if (!src.on(z)) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int r0 = blockIdx.y * rows_per_block;
     const int r1 = min(rows, r0 + rows_per_block);
@@ -1009,6 +1025,7 @@ template <class Src>
 __global__ void ozaki_rows_kernel(Src src, int rows, int cols, const int* __restrict__ ex, int64_t exs, int nslices,
                                   uint16_t* __restrict__ dst, int64_t ldd, int64_t plane, int64_t dzs) {
     const int z = blockIdx.z;
+    if (!src.on(z)) return;
     dst += z * dzs;
     ex += z * exs;
     const int64_t total = (int64_t)rows * cols;
@@ -1026,6 +1043,7 @@ __global__ void ozaki_cols_kernel(Src src, int rows, int cols, const int* __rest
                                   uint16_t* __restrict__ dst, int64_t ldd, int64_t plane, int64_t dzs) {
     __shared__ double tile[32][33];
     const int z = blockIdx.z;
+    if (!src.on(z)) return;
     dst += z * dzs;
     ex += z * exs;
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -1236,28 +1254,29 @@ int split_digits(Src src, int rows, int cols, bool transpose, int nslices, int* 
 
 int launch_split_bf16x2(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
                         int64_t ldd, cudaStream_t s) {
-    return split_planes(SrcOne{src, lds}, rows, cols, transpose, 2, dst, ldd, 1, s);
+    return split_planes(SrcOne{src, lds, nullptr}, rows, cols, transpose, 2, dst, ldd, 1, s);
 }
 
 int launch_split_bf16x3p(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
-                         int64_t ldd, cudaStream_t s) {
-    return split_planes(SrcOne{src, lds}, rows, cols, transpose, 3, dst, ldd, 1, s);
+                         int64_t ldd, cudaStream_t s, const int* active) {
+    return split_planes(SrcOne{src, lds, active}, rows, cols, transpose, 3, dst, ldd, 1, s);
 }
 
 int launch_ozaki_split(const double* src, int64_t lds, int rows, int cols, bool transpose, int nslices, int* ex,
-                       uint16_t* dst, int64_t ldd, double* sumsq, cudaStream_t s) {
-    return split_digits(SrcOne{src, lds}, rows, cols, transpose, nslices, ex, dst, ldd, sumsq, 0, 1, s);
+                       uint16_t* dst, int64_t ldd, double* sumsq, cudaStream_t s, const int* active) {
+    return split_digits(SrcOne{src, lds, active}, rows, cols, transpose, nslices, ex, dst, ldd, sumsq, 0, 1, s);
 }
 
 int launch_split_planes_batched(const BatchView& src, int rows, int cols, bool transpose, int planes,
-                                uint16_t* dst, int64_t ldd, int count, cudaStream_t s) {
+                                uint16_t* dst, int64_t ldd, int count, cudaStream_t s, const int* active) {
     if (planes != 2 && planes != 3) return SPIN_ERR_INVALID_ARG;
-    return split_planes(SrcMany{src}, rows, cols, transpose, planes, dst, ldd, count, s);
+    return split_planes(SrcMany{src, active}, rows, cols, transpose, planes, dst, ldd, count, s);
 }
 
 int launch_ozaki_split_batched(const BatchView& src, int rows, int cols, bool transpose, int nslices, int* ex,
-                               uint16_t* dst, int64_t ldd, double* sumsq, int count, cudaStream_t s) {
-    return split_digits(SrcMany{src}, rows, cols, transpose, nslices, ex, dst, ldd, sumsq, 1, count, s);
+                               uint16_t* dst, int64_t ldd, double* sumsq, int count, cudaStream_t s,
+                               const int* active) {
+    return split_digits(SrcMany{src, active}, rows, cols, transpose, nslices, ex, dst, ldd, sumsq, 1, count, s);
 }
 
 }  // namespace spin

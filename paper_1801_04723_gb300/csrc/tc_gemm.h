@@ -40,6 +40,7 @@ struct TcGemmParams {
     int add_identity;
     double* sumsq;           // if set: += sum of squares of the final D values
     int* err;                // set to SPIN_ERR_TIMEOUT if a bounded wait gives up
+    const int* active;       // if set: problem z runs only while active[z] != 0 (batch = 0: active[0])
     // Batched launches (batch > 0): problem z = blockIdx.y.  The operand
     // planes of problem z follow those of problem z - 1 in the slice stack
     // (a_zrows = slices * rows of one problem, filled by launch_tc_gemm);
@@ -60,23 +61,26 @@ struct TcGemmParams {
 int64_t tc_ld(int64_t k);
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, cudaStream_t s);
 // FP64 view -> (hi, mid, lo) BF16 planes; transpose=true writes the cols x rows transpose.
+// active (optional, device): split only while *active != 0.
 int launch_split_bf16x3p(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
-                         int64_t ldd, cudaStream_t s);
+                         int64_t ldd, cudaStream_t s, const int* active = nullptr);
 // FP64 view -> (hi, lo) BF16 planes; transpose=true writes the cols x rows transpose.
 int launch_split_bf16x2(const double* src, int64_t lds, int rows, int cols, bool transpose, uint16_t* dst,
                         int64_t ldd, cudaStream_t s);
 // FP64 view -> nslices fixed-point digit planes plus per-row (or, transposed,
 // per-column) exponents in ex; sumsq (optional) += sum of squares of src.
 int launch_ozaki_split(const double* src, int64_t lds, int rows, int cols, bool transpose, int nslices, int* ex,
-                       uint16_t* dst, int64_t ldd, double* sumsq, cudaStream_t s);
+                       uint16_t* dst, int64_t ldd, double* sumsq, cudaStream_t s, const int* active = nullptr);
 
 // Batched forms: problem z's FP64 view is src(z); its planes start at
 // dst + z * planes * (transpose ? cols : rows) * ldd (the slice stack a
 // batched product expects), its exponents at ex + z * (rows or cols) and its
-// sum of squares at sumsq[z] (sumsq optional).
+// sum of squares at sumsq[z] (sumsq optional); problem z is split only while
+// active[z] != 0 (active optional, device).
 int launch_split_planes_batched(const BatchView& src, int rows, int cols, bool transpose, int planes,
-                                uint16_t* dst, int64_t ldd, int count, cudaStream_t s);
+                                uint16_t* dst, int64_t ldd, int count, cudaStream_t s, const int* active = nullptr);
 int launch_ozaki_split_batched(const BatchView& src, int rows, int cols, bool transpose, int nslices, int* ex,
-                               uint16_t* dst, int64_t ldd, double* sumsq, int count, cudaStream_t s);
+                               uint16_t* dst, int64_t ldd, double* sumsq, int count, cudaStream_t s,
+                               const int* active = nullptr);
 
 }  // namespace spin
