@@ -106,6 +106,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: arrival window (s)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: Poisson arrival rate (req/s)")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-max-batch", type=int, default=0,
+                    help="serving: requests per batched launch group (0: the library default, 64; 1: off)")
     ap.add_argument("--serve-priority-order", type=int, default=1024,
                     help="serving: requests of order <= this run on high-priority streams (0: off)")
     ap.add_argument("--fp64-levels", type=int, default=2,
@@ -741,10 +743,22 @@ def mixed_subrecord(args, spin, plain_work, n: int, plain_ms: float, device, str
 
 
 def run_serve(args, w: dict):
-    """Serving benchmark: replay a Poisson arrival trace against spin_serve_*."""
+    """Serving benchmark: replay a Poisson arrival trace against spin_serve_*.
+
+    A producer thread generates every request's matrix on the device ahead
+    of its arrival time (a bounded look-ahead in bytes); the main thread
+    submits each at its arrival time and polls finished requests.  Every
+    arrival of the trace is accounted for: submitted (then served or failed),
+    shed by the server's queue bound, or not generated (a generation failure,
+    reported, never silently dropped).  Latency is taken from the arrival
+    time in the trace (the server's own submit-to-finish latency is reported
+    beside it)."""
     import queue
     import threading
 
+    # many distinct matrix sizes come and go: let the caching allocator grow
+    # and shrink segments instead of fragmenting fixed ones
+    os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
     import torch
 
     import paper_1801_04723_gb300 as spin
@@ -760,22 +774,55 @@ def run_serve(args, w: dict):
     gen_stream = torch.cuda.Stream(device)
 
     def make(j, n, alpha):
+        # G G^T / n on the TF32 tensor cores (input preparation only: the
+        # product's rounding is far below alpha >= 0.1, so A stays SPD), then
+        # symmetrised in FP64
         with torch.cuda.stream(gen_stream):
-            G = inputs.normal_torch(w["seed"] + 7919 * (j + 1), n, n, 0, device, torch.float32)
-            A = (G @ G.T).double() / float(n)
+            prev = torch.backends.cuda.matmul.allow_tf32
+            torch.backends.cuda.matmul.allow_tf32 = True
+            try:
+                G = inputs.normal_torch(w["seed"] + 7919 * (j + 1), n, n, 0, device, torch.float32)
+                A = (G @ G.T).double() / float(n)
+            finally:
+                torch.backends.cuda.matmul.allow_tf32 = prev
             A = 0.5 * (A + A.T)
             A.diagonal().add_(alpha)
+            del G
             ev = torch.cuda.Event()
             ev.record(gen_stream)
         return A, ev
 
-    ready = queue.Queue(maxsize=32)  # bounded look-ahead of generated inputs
+    lookahead_bytes = 4 << 30
+    ready = queue.Queue()
+    cond = threading.Condition()
+    state = {"ahead": 0, "gen_retries": 0, "gen_failed": [], "error": None}
 
     def producer():
         try:
             for j, (t, n, alpha, mixed) in enumerate(trace):
-                A, ev = make(j, n, alpha)
+                nb = 8 * n * n
+                with cond:  # bounded look-ahead in bytes
+                    while state["ahead"] > 0 and state["ahead"] + nb > lookahead_bytes:
+                        cond.wait(timeout=0.05)
+                A = ev = None
+                for attempt in range(200):
+                    try:
+                        A, ev = make(j, n, alpha)
+                        break
+                    except torch.OutOfMemoryError:
+                        # the client's memory frees as results are polled: wait, then retry
+                        state["gen_retries"] += 1
+                        torch.cuda.empty_cache()
+                        time.sleep(0.05)
+                if A is None:
+                    state["gen_failed"].append(j)
+                    ready.put((j, t, n, mixed, None, None))
+                    continue
+                with cond:
+                    state["ahead"] += nb
                 ready.put((j, t, n, mixed, A, ev))
+        except BaseException as e:  # reported by the main loop, which then stops
+            state["error"] = repr(e)
         finally:
             ready.put(None)
 
@@ -783,47 +830,63 @@ def run_serve(args, w: dict):
     # whose A would take the queued bytes above 48 GB are shed (the A of
     # queued requests stays in the client's device memory).
     srv = spin.Server(hbm_budget_bytes=150 << 30, max_slots=args.serve_slots, max_queued_bytes=48 << 30,
-                      priority_order=args.serve_priority_order)
+                      priority_order=args.serve_priority_order, max_batch=args.serve_max_batch)
     pending = {}
     done = []
     shed = 0
-    # warm the kernels once (both paths) outside the measured window
-    for prec, tol in (("bf16x3", 1e-10), ("fp64", 1e-13)):
-        Aw, ev = make(10 ** 6, 256, 0.5)
-        ev.synchronize()
-        spin.invert(Aw, precision=prec, tol=tol)
+    submit_lag = {}
+    # warm the kernels once (both paths, batched and single) outside the measured window
+    for prec, tol in (("bf16x3", 1e-10), ("fp64", 1e-13), ("bf16x3", 1e-13)):
+        for nw in (256, 1536):
+            Aw, ev = make(10 ** 6, nw, 0.5)
+            ev.synchronize()
+            tk = srv.submit(Aw, precision=prec, tol=tol)
+            while srv.poll(tk, discard=True) is None:
+                time.sleep(0.001)
+    st0 = srv.stats()
     th = threading.Thread(target=producer, daemon=True)
     th.start()
     t0 = time.perf_counter()
-    flops_done = 0.0
 
     def collect():
         for tk in list(pending):
             got = srv.poll(tk, discard=True)
             if got is not None:
-                got[1]["n"] = pending.pop(tk)
-                done.append(got[1])
+                j, n, t_arr = pending.pop(tk)
+                r = got[1]
+                r["n"] = n
+                r["latency_from_arrival_ms"] = r["latency_ms"] + submit_lag[tk]
+                done.append(r)
 
+    submitted = 0
     with ClockSampler(local) as clk:
         while True:
             item = ready.get(timeout=600)
             if item is None:
                 break
             j, t_arr, n, mixed, A, ev = item
+            if A is None:
+                continue  # counted as not generated
             while time.perf_counter() - t0 < t_arr:
                 collect()  # poll finished requests while waiting for the next arrival
                 time.sleep(0.0005)
             ev.synchronize()
             if mixed:
-                tk = srv.submit(A, precision="bf16x3", tol=1e-10)
+                prec, tol = "bf16x3", 1e-10
             else:
-                prec = "bf16x3" if args.serve_fp64_path == "mixed" else "fp64"
-                tk = srv.submit(A, precision=prec, tol=1e-13)
+                prec, tol = ("bf16x3" if args.serve_fp64_path == "mixed" else "fp64"), 1e-13
+            t_sub = time.perf_counter() - t0
+            tk = srv.submit(A, precision=prec, tol=tol)
+            with cond:
+                state["ahead"] -= 8 * n * n
+                cond.notify_all()
+            del A
             if tk is None:
                 shed += 1
                 continue
-            pending[tk] = n
-            flops_done += 2.0 * float(n) ** 3
+            submitted += 1
+            submit_lag[tk] = (t_sub - t_arr) * 1e3
+            pending[tk] = (j, n, t_arr)
         t_last_arrival = time.perf_counter() - t0
         while pending:
             collect()
@@ -831,7 +894,14 @@ def run_serve(args, w: dict):
         makespan = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
-    lat = sorted(r["latency_ms"] for r in done)
+    if state["error"] is not None:
+        raise RuntimeError(f"input generation failed: {state['error']}")
+    arrivals = len(trace)
+    not_generated = len(state["gen_failed"])
+    assert arrivals == submitted + shed + not_generated, (arrivals, submitted, shed, not_generated)
+    assert len(done) == submitted
+    lat = sorted(r["latency_from_arrival_ms"] for r in done)
+    lat_srv = sorted(r["latency_ms"] for r in done)
     bad = sum(1 for r in done if r["status"] != 0)
     failed_status = {}
     for r in done:
@@ -840,26 +910,37 @@ def run_serve(args, w: dict):
     failed_detail = [{k: r[k] for k in ("status", "n", "precision", "refine_iters", "rel_residual")}
                      for r in done if r["status"] != 0][:20]
 
-    def pct(q):
-        return lat[min(len(lat) - 1, int(q * len(lat)))] if lat else None
+    def pct(v, q):
+        return v[min(len(v) - 1, int(q * len(v)))] if v else None
 
+    flops_trace = sum(2.0 * float(n) ** 3 for _, n, _, _ in trace)
+    flops_done = sum(2.0 * float(r["n"]) ** 3 for r in done if r["status"] == 0)
+    served_ok = sum(1 for r in done if r["status"] == 0)
     line = {
-        "metric": METRIC, "value": len(done) / makespan, "unit": "req/s", "n_gpus": world,
+        "metric": METRIC, "value": served_ok / makespan, "unit": "req/s", "n_gpus": world,
         "steps": 1, "warmup": 1, "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
         "config": {"workload": "serve", "rate_req_s": args.serve_rate, "arrival_window_s": args.serve_seconds,
-                   "requests": len(trace), "n_range": [64, min(8192, w["n"])], "slots": args.serve_slots,
-                   "priority_order": args.serve_priority_order,
-                   "hbm_budget_gb": 150, "fp64_class_path": args.serve_fp64_path, "desc": w["desc"]},
-        "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat[-1] if lat else None,
-        "offered_req_s": len(trace) / args.serve_seconds,
-        "offered_tflops": flops_done / args.serve_seconds / 1e12,
+                   "requests": arrivals, "n_range": [64, min(8192, w["n"])], "slots": args.serve_slots,
+                   "priority_order": args.serve_priority_order, "max_batch": args.serve_max_batch,
+                   "hbm_budget_gb": 150, "fp64_class_path": args.serve_fp64_path, "desc": w["desc"],
+                   "inputs": "A = G G^T / n + alpha I generated on the device ahead of arrival (G G^T on TF32 "
+                             "tensor cores, symmetrised in FP64), at most 4 GB ahead"},
+        "arrivals": arrivals, "submitted": submitted, "served": served_ok, "failed": bad, "shed": shed,
+        "not_generated": not_generated, "generation_retries": state["gen_retries"],
+        "p50_ms": pct(lat, 0.50), "p99_ms": pct(lat, 0.99), "max_ms": lat[-1] if lat else None,
+        "latency_from": "arrival time in the trace (p50_ms, p99_ms, max_ms)",
+        "server_p50_ms": pct(lat_srv, 0.50), "server_p99_ms": pct(lat_srv, 0.99),
+        "offered_req_s": arrivals / args.serve_seconds,
+        "offered_tflops": flops_trace / args.serve_seconds / 1e12,
         "served_tflops": flops_done / makespan / 1e12,
         "drain_s_after_last_arrival": makespan - t_last_arrival,
-        "failed": bad, "failed_status": failed_status, "failed_detail": failed_detail,
-        "shed": shed, "served": len(done), "peak_running": st["peak_running"], "deferred": st["deferred"],
+        "failed_status": failed_status, "failed_detail": failed_detail,
+        "peak_running": st["peak_running"], "deferred": st["deferred"] - st0["deferred"],
+        "batching": {"groups": st["groups"] - st0["groups"], "requests_in_groups": st["grouped"] - st0["grouped"],
+                     "largest_group": st["max_group"]},
         "clocks": clk.summary(),
-        "e2e": {"value": len(done) / makespan, "unit": "req/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+        "e2e": {"value": served_ok / makespan, "unit": "req/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                 "how": "requests submitted from device memory; results left on the device"},
         "gpu_launches": None,
     }

@@ -196,6 +196,15 @@ int spin_batched_refine_info(spin_stream_t stream, int* refine_iters, double* wo
  * host memory, the result X, the workspace) fits hbm_budget_bytes; it then
  * runs on that slot's stream while other requests run on theirs.  The
  * result stays on the device, counted against the budget, until polled.
+ * Continuous batching (the many-block parallelism of Alg. 2, Sec. 3.3, over
+ * requests): a request of order n <= batch_max_order (precision SPIN_FP64
+ * or SPIN_MIXED_BF16X3) is padded with the identity to the next multiple of
+ * 32, and the slot that takes it also takes every queued request of the same
+ * padded order, precision and tolerance (up to max_batch, within the
+ * budget); the group runs as one lockstep batched recursion (one launch per
+ * product and per leaf for all of it).  Such a request takes this path even
+ * alone, and every decision in it is per matrix, so its result is the same
+ * bit for bit whatever it is batched with.
  * ------------------------------------------------------------------- */
 typedef struct spin_serve_cfg {
     size_t hbm_budget_bytes;  /* device memory the server may hold for requests       */
@@ -208,13 +217,18 @@ typedef struct spin_serve_cfg {
                                  queued, not yet admitted, requests above this is
                                  refused with SPIN_ERR_BUSY and counted as shed (an
                                  empty queue accepts any request)                    */
+    int32_t max_batch;        /* requests per batched launch group: 0 = 64; 1 = no
+                                 batching (every request alone on the single path)  */
+    int32_t batch_max_order;  /* orders above this are never batched: 0 = 1024; at most
+                                 4096                                                 */
 } spin_serve_cfg;
 
 typedef struct spin_result {
     int32_t status;           /* spin_status of the inversion                          */
     int32_t refine_iters;
     int32_t precision;        /* spin_precision the request asked for                  */
-    int32_t reserved;
+    int32_t batch;            /* requests in the batched launch group it ran in (1: a
+                                 group of its own); 0: the single-matrix path         */
     double rel_residual;      /* -1 for SPIN_FP64 (not computed)                       */
     double queue_ms;          /* submit -> admitted                                    */
     double run_ms;            /* admitted -> finished                                  */
@@ -230,6 +244,10 @@ typedef struct spin_serve_stats_t {
                                  could not be allocated (retried after another request
                                  completed; a request fails with SPIN_ERR_OOM only when
                                  it cannot be allocated while running alone)          */
+    uint64_t groups;          /* batched launch groups run                             */
+    uint64_t grouped;         /* requests those groups held                            */
+    int32_t max_group;        /* largest group                                         */
+    int32_t reserved;
 } spin_serve_stats_t;
 
 typedef struct spin_server spin_server;
@@ -254,7 +272,7 @@ int spin_serve_submit(spin_server* sv, const double* A, int64_t lda, int64_t n, 
 int spin_serve_poll(spin_server* sv, uint64_t ticket, double* X, int64_t ldx, spin_result* r);
 
 /* Counters: submitted, completed, rejected, queued, running, peak running,
- * bytes held, shed, deferred. */
+ * bytes held, shed, deferred, batched groups, requests in them, largest. */
 int spin_serve_stats(spin_server* sv, spin_serve_stats_t* st);
 
 /* Stop the slots (running requests finish), free everything. */

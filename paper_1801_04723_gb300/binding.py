@@ -76,7 +76,8 @@ KERNEL_KINDS = {0: "leaf_gj", 1: "gemm_f64", 2: "gemm_tc", 3: "split", 4: "resid
 
 class ServeCfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("priority_order", ctypes.c_int32),
-                ("max_queued_bytes", ctypes.c_size_t)]
+                ("max_queued_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int32),
+                ("batch_max_order", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -84,7 +85,7 @@ class Result(ctypes.Structure):
         ("status", ctypes.c_int32),
         ("refine_iters", ctypes.c_int32),
         ("precision", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("batch", ctypes.c_int32),
         ("rel_residual", ctypes.c_double),
         ("queue_ms", ctypes.c_double),
         ("run_ms", ctypes.c_double),
@@ -106,10 +107,14 @@ class ServeStats(ctypes.Structure):
         ("bytes_in_use", ctypes.c_size_t),
         ("shed", ctypes.c_uint64),
         ("deferred", ctypes.c_uint64),
+        ("groups", ctypes.c_uint64),
+        ("grouped", ctypes.c_uint64),
+        ("max_group", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class SpinError(RuntimeError):
@@ -493,7 +498,9 @@ def invert_batched(As, *, leaf: int = 0, outs=None, stream=None, blocking: bool 
                    tol: float = 1e-10, max_refine: int = 6, fp64_levels: int = 2):
     """X_i = A_i^-1 for a list of square float64 CUDA tensors of any orders
     (spin_invert_batched).  Returns (list of X, int32 CUDA tensor of statuses).
-    precision "bf16x3" runs the mixed form (returns when done)."""
+    precision "bf16x3" runs the mixed form (its refinement is part of the
+    captured graph).  With ``blocking=False`` the call returns once the work
+    is enqueued on the stream."""
     import torch
 
     count = len(As)
@@ -537,11 +544,15 @@ class Server:
     ``submit`` returns None.  With ``priority_order`` > 0, requests of order
     up to it run on high-priority streams.  A request whose device memory
     cannot be allocated while others run waits for one of them to finish
-    (``stats()["deferred"]``)."""
+    (``stats()["deferred"]``).  Requests of order <= ``batch_max_order``
+    (0: 1024) with the same padded order, precision and tolerance run
+    together in batched launch groups of up to ``max_batch`` (0: 64; 1:
+    off); each result carries the size of its group (``batch``)."""
 
     def __init__(self, hbm_budget_bytes: int, max_slots: int = 4, max_queued_bytes: int = 0,
-                 priority_order: int = 0):
-        cfg = ServeCfg(int(hbm_budget_bytes), int(max_slots), int(priority_order), int(max_queued_bytes))
+                 priority_order: int = 0, max_batch: int = 0, batch_max_order: int = 0):
+        cfg = ServeCfg(int(hbm_budget_bytes), int(max_slots), int(priority_order), int(max_queued_bytes),
+                       int(max_batch), int(batch_max_order))
         h = ctypes.c_void_p()
         rc = lib().spin_serve_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != SPIN_OK:

@@ -77,6 +77,7 @@ struct BatchPlan {
     double* rel = nullptr;         // device: [count] latest relative residual
     int* iters = nullptr;          // device: [count] refinement steps taken
     int* err = nullptr;            // device: SPIN_ERR_TIMEOUT from a bounded wait
+    const int* nvalid = nullptr;   // device, optional: [count] order of the matrix inside its identity padding
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;  // private stream the launch sequence is captured on
     cudaStream_t streams[kStreams] = {};
@@ -341,11 +342,12 @@ int bucket_refine(BatchPlan& p, const Bucket& b, cudaStream_t s) {
     BRET(launch_refine_init(rec, b.count, act, p.rel + b.first, p.iters + b.first, s));
     SPIN_CUDA_TRY(cudaMemsetAsync(nA, 0, b.count * sizeof(double), s));
     p.kernels += 3;
-    BRET(launch_ozaki_split_batched(Av, (int)b.n, (int)b.n, false, sr, aex, aplanes, ld, nA, b.count, s, act));
+    const int* nv = p.nvalid ? p.nvalid + b.first : nullptr;  // norms over the unpadded block
+    BRET(launch_ozaki_split_batched(Av, (int)b.n, (int)b.n, false, sr, aex, aplanes, ld, nA, b.count, s, act, nv));
     for (int it = 0; it <= p.max_refine; it++) {
         SPIN_CUDA_TRY(cudaMemsetAsync(nX, 0, b.count * sizeof(double), s));
         SPIN_CUDA_TRY(cudaMemsetAsync(nR, 0, b.count * sizeof(double), s));
-        BRET(launch_ozaki_split_batched(Xv, (int)b.n, (int)b.n, true, sr, xex, xplanes, ld, nX, b.count, s, act));
+        BRET(launch_ozaki_split_batched(Xv, (int)b.n, (int)b.n, true, sr, xex, xplanes, ld, nX, b.count, s, act, nv));
         TcGemmParams q = {};
         q.M = q.N = q.K = (int)b.n;
         tc_pairs_ozaki(q, sr);
@@ -355,6 +357,7 @@ int bucket_refine(BatchPlan& p, const Bucket& b, cudaStream_t s) {
         q.sumsq = nR;
         q.err = p.err;
         q.active = act;
+        q.sum_order = nv;
         q.row_exp = aex;
         q.col_exp = xex;
         q.batch = b.count;
@@ -565,7 +568,162 @@ std::vector<uint64_t> make_key(const double* const* A, const int64_t* lda, doubl
     return k;
 }
 
+// Identity padding: Ap = [[A, 0], [0, I]] of order np >= n.
+__global__ void pad_identity_kernel(const double* A, int64_t lda, int64_t n, double* Ap, int64_t np) {
+    const int64_t total = np * np;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / np, c = i % np;
+        Ap[i] = (r < n && c < n) ? A[r * lda + c] : (r == c ? 1.0 : 0.0);
+    }
+}
+
+// Device layout of one bucket run directly (run_bucket), every part 256-byte
+// aligned: upload block (a_base, a_ld, x_base, w_base: count 8-byte words
+// each; nvalid: count ints), records, refinement control (active, rel,
+// iters, norms [3][count], err), FP64 workspaces, mixed arena.
+struct DirectLayout {
+    size_t upload, records, active, rel, iters, norms, err, ws, arena, total;
+    size_t ws_elems, scratch_per, cache_per;
+    int64_t leaf;
+    int sr;
+};
+
+DirectLayout direct_layout(int64_t n, int count, const spin_opts& o) {
+    DirectLayout L;
+    const bool mixed = o.precision != SPIN_FP64;
+    const size_t c = (size_t)count;
+    L.leaf = batched_leaf(n, o.leaf);
+    L.sr = o.residual_slices > 0 ? o.residual_slices : (o.tol >= 1e-11 ? 6 : 7);
+    L.ws_elems = std::max<size_t>(fp64_workspace_elems(n, L.leaf), 1);
+    if (mixed) L.ws_elems = std::max<size_t>(L.ws_elems, (size_t)n * (size_t)n);  // holds R
+    L.scratch_per = mixed ? mixed_scratch_per(n, L.leaf, o.fp64_levels, L.sr) : 0;
+    L.cache_per = mixed ? mixed_cache_per(n, L.sr) : 0;
+    size_t off = 0;
+    L.upload = off;
+    off = align256(off + 32 * c + 4 * c);
+    L.records = off;
+    off = align256(off + c * INFO_WORDS * 4);
+    L.active = off;
+    off = align256(off + 4 * c);
+    L.rel = off;
+    off = align256(off + 8 * c);
+    L.iters = off;
+    off = align256(off + 4 * c);
+    L.norms = off;
+    off = align256(off + 24 * c);
+    L.err = off;
+    off = align256(off + 4);
+    L.ws = off;
+    off = align256(off + L.ws_elems * 8 * c);
+    L.arena = off;
+    off = align256(off + c * (L.scratch_per + L.cache_per));
+    L.total = off;
+    return L;
+}
+
 }  // namespace
+
+size_t bucket_bytes(int64_t n, int count, const spin_opts& o) {
+    if (n < 1 || count < 1) return 0;
+    return direct_layout(n, count, o).total;
+}
+
+// Pinned host staging: upload block (36 bytes per matrix, padded to 40 so
+// that the results start 8-byte aligned), then records, rel, iters.
+size_t bucket_host_bytes(int count) { return 40 * (size_t)count + (size_t)count * (INFO_WORDS * 4 + 12); }
+
+int launch_pad_identity(const double* A, int64_t lda, int64_t n, double* Ap, int64_t np, cudaStream_t s) {
+    if (n < 1 || np < n) return SPIN_ERR_INVALID_ARG;
+    const int64_t total = np * np;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
+    pad_identity_kernel<<<blocks, 256, 0, s>>>(A, lda, n, Ap, np);
+    SPIN_CUDA_TRY(cudaGetLastError());
+    return SPIN_OK;
+}
+
+int run_bucket(const double* const* A, const int64_t* lda, double* const* X, const int* nvalid, int64_t n,
+               int count, const spin_opts& o, void* ws, size_t ws_bytes, void* host_stage, cudaStream_t s) {
+    if (n < 1 || count < 1 || count > 65535 || ws == nullptr || host_stage == nullptr) return SPIN_ERR_INVALID_ARG;
+    if (o.precision != SPIN_FP64 && o.precision != SPIN_MIXED_BF16X3) return SPIN_ERR_NOT_IMPLEMENTED;
+    const DirectLayout L = direct_layout(n, count, o);
+    if (ws_bytes < L.total || ((uintptr_t)ws & 255u) != 0 || L.leaf > kMaxLeaf) return SPIN_ERR_INVALID_ARG;
+    const bool mixed = o.precision != SPIN_FP64;
+    unsigned char* base = (unsigned char*)ws;
+    // pointer arrays: staged in pinned host memory, one copy up
+    unsigned char* up = (unsigned char*)host_stage;
+    const size_t c = (size_t)count;
+    double* wsb = (double*)(base + L.ws);
+    for (int z = 0; z < count; z++) {
+        ((const double**)up)[z] = A[z];
+        ((int64_t*)(up + 8 * c))[z] = lda[z];
+        ((double**)(up + 16 * c))[z] = X[z];
+        ((double**)(up + 24 * c))[z] = wsb + (size_t)z * L.ws_elems;
+        ((int*)(up + 32 * c))[z] = nvalid ? nvalid[z] : (int)n;
+    }
+    SPIN_CUDA_TRY(cudaMemcpyAsync(base + L.upload, up, 36 * c, cudaMemcpyHostToDevice, s));
+    BatchPlan p;
+    p.count = count;
+    p.precision = o.precision;
+    p.tol = o.tol;
+    p.max_refine = o.max_refine;
+    p.fp64_levels = o.fp64_levels;
+    p.sr = L.sr;
+    p.a_base = (const double**)(base + L.upload);
+    p.a_ld = (int64_t*)(base + L.upload + 8 * c);
+    p.x_base = (double**)(base + L.upload + 16 * c);
+    p.w_base = (double**)(base + L.upload + 24 * c);
+    p.nvalid = nvalid ? (const int*)(base + L.upload + 32 * c) : nullptr;
+    p.records = (int32_t*)(base + L.records);
+    p.active = (int*)(base + L.active);
+    p.rel = (double*)(base + L.rel);
+    p.iters = (int*)(base + L.iters);
+    p.norms = (double*)(base + L.norms);
+    p.err = (int*)(base + L.err);
+    p.ws = wsb;
+    p.arena = base + L.arena;
+    SPIN_CUDA_TRY(cudaMemsetAsync(p.records, 0, c * INFO_WORDS * 4, s));
+    SPIN_CUDA_TRY(cudaMemsetAsync(p.err, 0, 4, s));
+    Bucket b;
+    b.n = n;
+    b.leaf = L.leaf;
+    b.count = count;
+    b.first = 0;
+    b.ws_elems = L.ws_elems;
+    b.ws_offset = 0;
+    b.scratch_per = L.scratch_per;
+    b.cache_per = L.cache_per;
+    b.arena_offset = 0;
+    b.stream = 0;
+    BRun r{&p.kernels, s, p.records, 0, b.leaf, count, p.ws, (int64_t)b.ws_elems};
+    BatchView Av{p.a_base, p.a_ld, 0, 0, 0};
+    BatchView Xv{(const double* const*)p.x_base, nullptr, n, 0, 0};
+    int rc;
+    if (mixed) {
+        BMix x{p.arena, count, p.fp64_levels, p.err, &p.kernels, s};
+        rc = binv_mixed(r, x, 0, Av, Xv, (const double* const*)p.w_base, 0, n);
+        if (rc == SPIN_OK) rc = bucket_refine(p, b, s);
+        if (rc == SPIN_OK) rc = launch_refine_finish(p.err, p.records, count, s);
+    } else {
+        rc = binv(r, Av, Xv, (const double* const*)p.w_base, 0, n);
+    }
+    if (rc != SPIN_OK) return rc;
+    // results down: records, rel, iters (read by bucket_result after the stream is synchronised)
+    unsigned char* res = up + 40 * c;
+    SPIN_CUDA_TRY(cudaMemcpyAsync(res, p.records, c * INFO_WORDS * 4, cudaMemcpyDeviceToHost, s));
+    if (mixed) {
+        SPIN_CUDA_TRY(cudaMemcpyAsync(res + c * INFO_WORDS * 4, p.rel, 8 * c, cudaMemcpyDeviceToHost, s));
+        SPIN_CUDA_TRY(cudaMemcpyAsync(res + c * INFO_WORDS * 4 + 8 * c, p.iters, 4 * c, cudaMemcpyDeviceToHost, s));
+    }
+    return SPIN_OK;
+}
+
+void bucket_result(const void* host_stage, int count, int z, bool mixed, int32_t* status, double* rel, int* iters) {
+    const unsigned char* res = (const unsigned char*)host_stage + 40 * (size_t)count;
+    *status = ((const int32_t*)res)[(size_t)z * INFO_WORDS + INFO_STATUS];
+    *rel = mixed ? ((const double*)(res + (size_t)count * INFO_WORDS * 4))[z] : -1.0;
+    *iters = mixed ? ((const int*)(res + (size_t)count * INFO_WORDS * 4 + 8 * (size_t)count))[z] : 0;
+}
+
 }  // namespace spin
 
 using namespace spin;

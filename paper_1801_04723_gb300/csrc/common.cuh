@@ -109,4 +109,22 @@ int run_fp64_inversion(const double* A, int64_t lda, double* X, int64_t ldx, int
                        int32_t* info, cudaStream_t s);
 int64_t split_order(int64_t n);
 
+// One bucket of `count` matrices of order n inverted in lockstep directly on
+// stream s, no graph, every byte of device memory from the caller (batched.cu):
+//   bucket_bytes       device bytes run_bucket needs (ws, 256-byte aligned);
+//   bucket_host_bytes  pinned host staging bytes (pointer upload, results);
+//   run_bucket         A, lda, X: host arrays of device views (X ld = n);
+//                      nvalid (host, optional): order of each matrix inside
+//                      its identity padding (norms of the refinement cover
+//                      that leading block); precision FP64 or BF16X3;
+//   bucket_result      after the stream has finished: status, relative
+//                      residual (-1 for FP64) and refinement steps of z.
+size_t bucket_bytes(int64_t n, int count, const spin_opts& o);
+size_t bucket_host_bytes(int count);
+int run_bucket(const double* const* A, const int64_t* lda, double* const* X, const int* nvalid, int64_t n,
+               int count, const spin_opts& o, void* ws, size_t ws_bytes, void* host_stage, cudaStream_t s);
+void bucket_result(const void* host_stage, int count, int z, bool mixed, int32_t* status, double* rel, int* iters);
+// Ap = [[A, 0], [0, I]] (np x np, leading dimension np).
+int launch_pad_identity(const double* A, int64_t lda, int64_t n, double* Ap, int64_t np, cudaStream_t s);
+
 }  // namespace spin

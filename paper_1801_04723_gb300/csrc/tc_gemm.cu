@@ -184,6 +184,9 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
                                                  int nchunks_per_pair, int lane, uint32_t tempty_c0,
                                                  uint32_t tempty_c1, int z) {
     const bool row_ok = grow < p.M;
+    // the sum of squares covers the leading sum_order x sum_order block only
+    const int so = p.sum_order ? p.sum_order[z] : 0x7fffffff;
+    const bool sum_row = grow < so;
     double sumsq = 0.0;
     // alpha = +-1 (every product of the method) is a sign flip of the integer
     // sums (|sum| < 2^31, no overflow); anything else costs one FP64 multiply
@@ -264,7 +267,7 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
                                 val += drow[gcol];
                             }
                             drow[gcol] = val;
-                            if (last) sumsq = fma(val, val, sumsq);
+                            if (last && sum_row && gcol < so) sumsq = fma(val, val, sumsq);
                         }
                         acc[j] = 0;
                     }
@@ -292,7 +295,7 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
                             if (last) {
                                 if (ok_ij) {
                                     drow[gcol] = val;
-                                    sumsq = fma(val, val, sumsq);
+                                    if (sum_row && gcol < so) sumsq = fma(val, val, sumsq);
                                 }
                             } else {
                                 w[2 * j] = (uint32_t)__double2loint(val);
@@ -499,6 +502,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         double sumsq = 0.0;
 
         if (!EXACT) {
+            const int so = p.sum_order ? p.sum_order[z] : 0x7fffffff;
             bool ok = mbar_wait(&ctl->tfull[0], 0u, abort, WAIT_LIMIT_NS);
             if (!ok) raise_timeout(ctl, p.err);
             tc_fence_after();
@@ -519,7 +523,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                 if (p.beta != 0.0) val = fma(p.beta, crow[gcol], val);
                                 if (p.add_identity && gcol == grow) val += 1.0;
                                 drow[gcol] = val;
-                                sumsq = fma(val, val, sumsq);
+                                if (grow < so && gcol < so) sumsq = fma(val, val, sumsq);
                             }
                         }
                     }
@@ -783,22 +787,27 @@ __device__ __forceinline__ void split3(double a, uint16_t& hi, uint16_t& mid, ui
 }
 
 // Operand source of a split: one FP64 view, or problem z's view of a batch.
-// act (optional): problem z is split only while act[z] != 0.
+// act (optional): problem z is split only while act[z] != 0.  nv
+// (optional): the sum of squares of problem z covers only its leading
+// nv[z] x nv[z] block (a matrix padded with the identity).
 struct SrcOne {
     const double* p;
     int64_t ld;
     const int* act;
     __device__ __forceinline__ const double* row(int, int r) const { return p + (int64_t)r * ld; }
     __device__ __forceinline__ bool on(int) const { return act == nullptr || act[0] != 0; }
+    __device__ __forceinline__ int valid(int) const { return 0x7fffffff; }
 };
 struct SrcMany {
     BatchView v;
     const int* act;
+    const int* nv;
     __device__ __forceinline__ const double* row(int z, int r) const {
         const int64_t l = v.ld_of(z);
         return v.base[z] + (v.r0 + r) * l + v.c0;
     }
     __device__ __forceinline__ bool on(int z) const { return act == nullptr || act[z] != 0; }
+    __device__ __forceinline__ int valid(int z) const { return nv ? nv[z] : 0x7fffffff; }
 };
 
 // Every split kernel handles problem z = blockIdx.z: its planes start at
@@ -912,12 +921,14 @@ __global__ void row_exp_kernel(Src src, int rows, int cols, int* __restrict__ ex
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
     const double* sr = src.row(z, r);
+    const int nv = src.valid(z);
+    const bool sum_row = sumsq != nullptr && r < nv;
     int m = 0;
     double ss = 0.0;
     for (int c = lane; c < cols; c += 32) {
         const double v = sr[c];
         m = max(m, exp_field(v));
-        if (sumsq) ss = fma(v, v, ss);
+        if (sum_row && c < nv) ss = fma(v, v, ss);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -941,6 +952,8 @@ __global__ void col_exp_kernel(Src src, int rows, int cols, int rows_per_block, 
     const int r0 = blockIdx.y * rows_per_block;
     const int r1 = min(rows, r0 + rows_per_block);
     int m = 0;
+    const int nv = src.valid(z);
+    const bool sum_col = sumsq != nullptr && c < nv;
     double ss4[4] = {0.0, 0.0, 0.0, 0.0};  // four FMA chains: a dependent FP64 FMA takes 64+ cycles here
     if (c < cols) {
         int r = r0;
@@ -949,13 +962,13 @@ __global__ void col_exp_kernel(Src src, int rows, int cols, int rows_per_block, 
             for (int u = 0; u < 4; u++) {
                 const double v = src.row(z, r + u)[c];
                 m = max(m, exp_field(v));
-                if (sumsq) ss4[u] = fma(v, v, ss4[u]);
+                if (sum_col && r + u < nv) ss4[u] = fma(v, v, ss4[u]);
             }
         }
         for (; r < r1; r++) {
             const double v = src.row(z, r)[c];
             m = max(m, exp_field(v));
-            if (sumsq) ss4[0] = fma(v, v, ss4[0]);
+            if (sum_col && r < nv) ss4[0] = fma(v, v, ss4[0]);
         }
     }
     double ss = (ss4[0] + ss4[1]) + (ss4[2] + ss4[3]);
@@ -1270,13 +1283,14 @@ int launch_ozaki_split(const double* src, int64_t lds, int rows, int cols, bool 
 int launch_split_planes_batched(const BatchView& src, int rows, int cols, bool transpose, int planes,
                                 uint16_t* dst, int64_t ldd, int count, cudaStream_t s, const int* active) {
     if (planes != 2 && planes != 3) return SPIN_ERR_INVALID_ARG;
-    return split_planes(SrcMany{src, active}, rows, cols, transpose, planes, dst, ldd, count, s);
+    return split_planes(SrcMany{src, active, nullptr}, rows, cols, transpose, planes, dst, ldd, count, s);
 }
 
 int launch_ozaki_split_batched(const BatchView& src, int rows, int cols, bool transpose, int nslices, int* ex,
                                uint16_t* dst, int64_t ldd, double* sumsq, int count, cudaStream_t s,
-                               const int* active) {
-    return split_digits(SrcMany{src, active}, rows, cols, transpose, nslices, ex, dst, ldd, sumsq, 1, count, s);
+                               const int* active, const int* valid) {
+    return split_digits(SrcMany{src, active, valid}, rows, cols, transpose, nslices, ex, dst, ldd, sumsq, 1, count,
+                        s);
 }
 
 }  // namespace spin

@@ -41,6 +41,7 @@ struct TcGemmParams {
     double* sumsq;           // if set: += sum of squares of the final D values
     int* err;                // set to SPIN_ERR_TIMEOUT if a bounded wait gives up
     const int* active;       // if set: problem z runs only while active[z] != 0 (batch = 0: active[0])
+    const int* sum_order;    // if set: sumsq covers rows and columns < sum_order[z] only
     // Batched launches (batch > 0): problem z = blockIdx.y.  The operand
     // planes of problem z follow those of problem z - 1 in the slice stack
     // (a_zrows = slices * rows of one problem, filled by launch_tc_gemm);
@@ -76,11 +77,12 @@ int launch_ozaki_split(const double* src, int64_t lds, int rows, int cols, bool 
 // dst + z * planes * (transpose ? cols : rows) * ldd (the slice stack a
 // batched product expects), its exponents at ex + z * (rows or cols) and its
 // sum of squares at sumsq[z] (sumsq optional); problem z is split only while
-// active[z] != 0 (active optional, device).
+// active[z] != 0 (active optional, device); with valid (optional, device) the
+// sum of squares of problem z covers its leading valid[z] x valid[z] block.
 int launch_split_planes_batched(const BatchView& src, int rows, int cols, bool transpose, int planes,
                                 uint16_t* dst, int64_t ldd, int count, cudaStream_t s, const int* active = nullptr);
 int launch_ozaki_split_batched(const BatchView& src, int rows, int cols, bool transpose, int nslices, int* ex,
                                uint16_t* dst, int64_t ldd, double* sumsq, int count, cudaStream_t s,
-                               const int* active = nullptr);
+                               const int* active = nullptr, const int* valid = nullptr);
 
 }  // namespace spin

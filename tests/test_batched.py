@@ -113,6 +113,44 @@ def test_batch_mixed_precision(spin):
             assert np.linalg.norm(X - ref) / np.linalg.norm(ref) <= 1e3 * 10 * 1e-10
 
 
+def test_batch_mixed_refinement_in_the_graph(spin):
+    """The mixed batch is one graph replay: its kernel count includes every
+    refinement round of every order bucket (3 launches to split A, then per
+    round 6 for the residual and decision and 3 for the update, the last
+    round without one), a non-blocking call only enqueues, and the results
+    equal those of a blocking call bit for bit."""
+    orders = [96, 300, 300, 512]
+    mats = [inputs.sdd(n, seed=3000 + i) for i, n in enumerate(orders)]
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    Xs, info = spin.invert_batched(As, precision="bf16x3", tol=1e-10, blocking=False)
+    torch.cuda.synchronize()
+    st = spin.batched_stats()
+    assert st["buckets"] == 3
+    per_bucket = 3 + 7 * 6 + 6 * 3
+    assert st["kernels"] >= st["buckets"] * per_bucket
+    assert info.cpu().tolist() == [0] * len(orders)
+    first = [x.cpu().numpy() for x in Xs]
+    Xs2, _ = spin.invert_batched(As, precision="bf16x3", tol=1e-10)
+    for a, x1, x2 in zip(mats, first, Xs2):
+        np.testing.assert_array_equal(x1, x2.cpu().numpy())
+        assert oracle.residual(a, x1)[0] <= 1e-10
+    ri = spin.batched_refine_info()
+    assert ri["refine_iters"] >= 1 and 0 < ri["worst_rel_residual"] <= 1e-10
+
+
+def test_batch_mixed_result_independent_of_batch(spin):
+    """Per-matrix decisions: a matrix inverted in a batch equals the same
+    matrix inverted in a batch of its own, bit for bit."""
+    mats = [inputs.householder_spd(384, seed=inputs.SEED_BASE + 60 + i, reflectors=16, cond=1e3)[0]
+            for i in range(3)]
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    Xs, _ = spin.invert_batched(As, precision="bf16x3", tol=1e-10)
+    together = [x.cpu().numpy() for x in Xs]
+    for a, xt in zip(As, together):
+        alone, _ = spin.invert_batched([a], precision="bf16x3", tol=1e-10)
+        np.testing.assert_array_equal(alone[0].cpu().numpy(), xt)
+
+
 def test_batch_mixed_strided_singular_and_replay(spin):
     big = torch.zeros((700, 900), dtype=torch.float64, device="cuda:0")
     a0 = inputs.spd_gram(300, seed=7)

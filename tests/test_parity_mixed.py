@@ -79,10 +79,28 @@ def test_tighter_tolerance(spin):
     assert oracle.residual(A, host(X))[0] <= 1e-13
 
 
+def test_refinement_is_decided_on_the_device(spin):
+    """A non-blocking mixed call only enqueues: the Newton-Schulz rounds and
+    their stopping decision run on the device, and spin_sync reads the
+    status, steps and residual afterwards."""
+    A = inputs.householder_spd(1024, seed=inputs.SEED_BASE + 2, reflectors=16, cond=1e3)[0]
+    Ad = dev(A)
+    X, none = spin.invert(Ad, leaf=128, precision="bf16x3", tol=1e-10, blocking=False)
+    assert none is None
+    info = spin.sync()
+    assert info["status"] == 0 and info["refine_iters"] >= 1 and 0 < info["rel_residual"] <= 1e-10
+    assert info["fail_leaf"] == -1
+    Xb, infob = spin.invert(Ad, leaf=128, precision="bf16x3", tol=1e-10)
+    np.testing.assert_array_equal(X.cpu().numpy(), Xb.cpu().numpy())
+    assert infob["rel_residual"] == info["rel_residual"]
+    assert oracle.residual(A, X.cpu().numpy())[0] <= 1e-10
+
+
 def test_not_converged_status(spin):
     A, _, _ = inputs.householder_spd(512, seed=9, reflectors=16, cond=1e3)
     X, info = spin.invert(dev(A), leaf=64, precision="bf16x3", tol=1e-30, max_refine=1, check=False)
     assert info["status"] == 3 and info["refine_iters"] == 1
+    assert info["fail_leaf"] == -1 and info["fail_col"] == -1  # a refinement status, not a leaf's
     assert info["rel_residual"] > 0
 
 

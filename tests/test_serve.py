@@ -1,7 +1,9 @@
 """Serving: requests of mixed orders and precisions submitted while others
-run; every result must equal the same request run alone (bit for bit on the
-plain path, whose kernels are deterministic; within the requested residual
-on the mixed path), and admission must respect the memory budget."""
+run, batched as they arrive; every result must equal the same request served
+alone, bit for bit (every decision of both paths is per matrix and the
+kernels are deterministic), be within tolerance of the single-matrix library
+call and within the requested residual, and admission must respect the
+memory budget."""
 import time
 
 import numpy as np
@@ -23,10 +25,25 @@ def spin():
     return s
 
 
+def serve_alone(spin, A, prec, tol, **cfg):
+    """The same request through a server of its own, alone."""
+    srv = spin.Server(hbm_budget_bytes=16 << 30, max_slots=1, **cfg)
+    t = srv.submit(A, precision=prec, tol=tol)
+    deadline = time.time() + 300
+    while (got := srv.poll(t)) is None and time.time() < deadline:
+        time.sleep(0.001)
+    srv.close()
+    assert got is not None
+    return got
+
+
 @pytest.mark.parametrize("priority_order", [0, 512])
 def test_serve_mix_equals_alone(spin, priority_order):
-    # priority_order: requests of order <= 512 on high-priority streams
-    trace = inputs.serve_trace(inputs.SEED_BASE + 4004, rate=400.0, duration=0.08, lo=64, hi=1024)
+    """Requests of mixed orders and precisions arriving while others run:
+    each result equals the same request served alone, bit for bit (plain and
+    mixed: every decision of the batched path is per matrix), and is within
+    tolerance of the single-matrix library call."""
+    trace = inputs.serve_trace(inputs.SEED_BASE + 4004, rate=400.0, duration=0.08, lo=64, hi=1400)
     assert len(trace) >= 20
     srv = spin.Server(hbm_budget_bytes=16 << 30, max_slots=4, priority_order=priority_order)
     reqs = []
@@ -55,15 +72,67 @@ def test_serve_mix_equals_alone(spin, priority_order):
     for t, A, prec, tol in reqs:
         X, r = results[t]
         assert r["status"] == 0, r
-        alone, info = spin.invert(torch.from_numpy(A).cuda(), precision=prec, tol=tol)
-        alone = alone.cpu().numpy()
+        Xa, ra = serve_alone(spin, A, prec, tol)
+        assert ra["status"] == 0 and ra["batch"] == 1
+        np.testing.assert_array_equal(X, Xa)
+        lib, info = spin.invert(torch.from_numpy(A).cuda(), precision=prec, tol=tol)
+        lib = lib.cpu().numpy()
         if prec == "fp64":
-            np.testing.assert_array_equal(X, alone)
             assert oracle.residual(A, X)[0] <= 1e-13
+            assert np.linalg.norm(X - lib) / np.linalg.norm(lib) <= 64 * A.shape[0] * np.linalg.cond(A) * 2.0 ** -53
         else:
             assert r["rel_residual"] <= tol and oracle.residual(A, X)[0] <= tol
-            assert np.linalg.norm(X - alone) / np.linalg.norm(alone) <= np.linalg.cond(A) * 10 * tol
+            assert np.linalg.norm(X - lib) / np.linalg.norm(lib) <= np.linalg.cond(A) * 10 * tol
         assert r["latency_ms"] >= r["run_ms"] > 0
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("bf16x3", 1e-10)])
+def test_serve_batches_same_order_requests(spin, prec, tol):
+    """Requests queued behind a busy slot whose orders pad to the same
+    multiple of 32 (449 ... 480 -> 480) run as one batched launch group: each
+    reports the group's size, the server counts one group, and every result
+    equals the request served alone, bit for bit."""
+    srv = spin.Server(hbm_budget_bytes=16 << 30, max_slots=1)
+    big = torch.from_numpy(inputs.sdd(2048, seed=3)).cuda()
+    tb = srv.submit(big, precision="fp64")  # keeps the only slot busy
+    for _ in range(5000):  # bounded wait until it runs
+        if srv.stats()["running"] == 1:
+            break
+        time.sleep(0.001)
+    orders = [449, 480, 463, 470, 455, 477]
+    mats = [inputs.spd_gram(n, seed=inputs.SEED_BASE + 500 + i, alpha=0.5) for i, n in enumerate(orders)]
+    tickets = [srv.submit(a if i % 2 else torch.from_numpy(a).cuda(), precision=prec, tol=tol)
+               for i, a in enumerate(mats)]
+    got = {}
+    deadline = time.time() + 300
+    while len(got) < len(tickets) and time.time() < deadline:
+        for t in tickets:
+            if t not in got and (g := srv.poll(t)) is not None:
+                got[t] = g
+        time.sleep(0.001)
+    while srv.poll(tb, discard=True) is None:
+        time.sleep(0.001)
+    st = srv.stats()
+    srv.close()
+    assert len(got) == len(tickets)
+    assert st["groups"] >= 1 and st["max_group"] == len(orders), st
+    for t, A in zip(tickets, mats):
+        X, r = got[t]
+        assert r["status"] == 0 and r["batch"] == len(orders), r
+        Xa, _ = serve_alone(spin, A, prec, tol)
+        np.testing.assert_array_equal(X, Xa)
+        lim = 1e-13 if prec == "fp64" else tol
+        assert oracle.residual(A, X)[0] <= lim
+        if prec != "fp64":
+            assert r["rel_residual"] <= tol and r["refine_iters"] >= 1
+
+
+def test_serve_batching_off_uses_the_single_path(spin):
+    A = inputs.spd_gram(300, seed=9, alpha=0.5)
+    X, r = serve_alone(spin, A, "fp64", 1e-13, max_batch=1)
+    lib, _ = spin.invert(torch.from_numpy(A).cuda())
+    np.testing.assert_array_equal(X, lib.cpu().numpy())
+    assert r["batch"] == 0  # not a launch group
 
 
 def test_serve_budget_and_errors(spin):
@@ -141,8 +210,15 @@ st = srv.stats()
 srv.close()
 assert out[t1][1]["status"] == 0 and out[t2][1]["status"] == 0, (out[t1][1], out[t2][1])
 assert st["deferred"] == 1, st
-alone, _ = s.invert(torch.from_numpy(small).cuda())
-np.testing.assert_array_equal(out[t2][0], alone.cpu().numpy())
+srv2 = s.Server(hbm_budget_bytes=4 << 30, max_slots=1)  # the same request alone
+t = srv2.submit(small, precision="fp64")
+for _ in range(600000):
+    alone = srv2.poll(t)
+    if alone is not None:
+        break
+    time.sleep(0.0005)
+srv2.close()
+np.testing.assert_array_equal(out[t2][0], alone[0])
 print("DEFER-OK")
 """
 
@@ -152,7 +228,8 @@ def test_serve_defers_on_allocation_failure(spin):
     runs is put back at the head of the queue and admitted again when that
     one completes, instead of failing.  The allocation failures are made on
     the host (SPIN_SERVE_INJECT_OOM=ticket:count makes the first count
-    attempts of that ticket fail); the result equals the request run alone."""
+    attempts of that ticket fail); the result equals the request served
+    alone."""
     import os
     import subprocess
     import sys
