@@ -99,6 +99,8 @@ def parse():
     ap.add_argument("--profile-json", default="", help="write per-launch records here")
     ap.add_argument("--leaf-times", default="", help="comma-separated leaf orders: time one leaf inversion "
                     "(spin_leaf_inverse on its default cluster) per order and print the per-pivot-step times")
+    ap.add_argument("--leaf-batch", default="", help="L:count -- time count leaves of order L <= 128 side by side "
+                    "(one batched leaf launch, one CTA each) and print the per-pivot-step time and cycles")
     ap.add_argument("--leaf-sweep", default="", help="comma-separated orders: time every candidate leaf "
                     "(the U-shaped block-size sweep) with spin_autotune_leaf and print one JSON line")
     ap.add_argument("--gemm-probe", type=int, default=0, help="time one digit-slice (6 slices) and one bf16x3 "
@@ -1027,10 +1029,53 @@ def run_leaf_times(args):
     return 0
 
 
+def run_leaf_batch(args):
+    """Many leaves side by side: `count` matrices of order L <= 128 through
+    spin_invert_batched (plain FP64), where every matrix is one leaf, so a
+    call is one leaf_gj_batched_kernel launch (one CTA per matrix) plus a
+    status scatter.  CUDA events around each call, best of 5 after 2 warm-ups;
+    per pivot step = time / L; with the SM clock sampled meanwhile."""
+    import torch
+
+    import paper_1801_04723_gb300 as spin
+    from paper_1801_04723_gb300 import inputs
+
+    spin.build()
+    L, count = (int(v) for v in args.leaf_batch.split(":"))
+    As = [torch.from_numpy(inputs.sdd(L, seed=inputs.SEED_BASE + 9000 + i)).to("cuda:0") for i in range(count)]
+    Xs = [torch.empty_like(a) for a in As]
+    for _ in range(2):
+        spin.invert_batched(As, outs=Xs)
+    torch.cuda.synchronize()
+    best = float("inf")
+    with ClockSampler(0) as clk:
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, info = spin.invert_batched(As, outs=Xs)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+    assert int(info.abs().sum()) == 0
+    c = clk.summary()
+    mhz = c["sm_mhz"] or 2070.0
+    per_step_us = best * 1e3 / L
+    out = {"leaf_batch": {"L": L, "count": count, "ms": best, "us_per_step": per_step_us,
+                          "cycles_per_step": per_step_us * mhz, "fma_per_step_per_leaf": L * L,
+                          "fp64_bound_cycles_per_step": L * L / 2.0,
+                          "how": "CUDA events around one spin_invert_batched call, best of 5 after 2 warm-ups"},
+           "clocks": c}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.leaf_times:
         return run_leaf_times(args)
+    if args.leaf_batch:
+        return run_leaf_batch(args)
     if args.leaf_sweep:
         return run_leaf_sweep(args)
     if args.gemm_probe:

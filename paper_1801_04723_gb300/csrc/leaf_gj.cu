@@ -68,7 +68,7 @@ struct Cand {
 constexpr uint64_t kInfBits = 0x7ff0000000000000ull;
 
 struct LeafSmemLayout {
-    size_t bar_off, m_off, prow_off, fcol_off, info_off, phys_off, lpos_off, piv_off, sig_off, total;
+    size_t bar_off, m_off, prow_off, fcol_off, info_off, part_off, phys_off, lpos_off, piv_off, sig_off, total;
 };
 
 // Candidate-row slots hold L doubles padded to an even count, so that every
@@ -86,6 +86,7 @@ __host__ __device__ inline LeafSmemLayout leaf_layout(int L, int R, int C, bool 
     if (push) off += 2 * (size_t)C * slot_stride(L) * sizeof(double);
     s.fcol_off = off = a16(off); off += 2 * (size_t)R * sizeof(double);
     s.info_off = off = a16(off); off += 2 * (size_t)C * sizeof(Cand);
+    s.part_off = off; if (push) off += (size_t)(NT / 32) * sizeof(Cand);  // per-warp candidates of phase A
     s.phys_off = off; off += (size_t)L * sizeof(int);
     s.lpos_off = off; off += (size_t)L * sizeof(int);
     s.piv_off = off; off += (size_t)L * sizeof(int);
@@ -425,6 +426,7 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
     double* slots = reinterpret_cast<double*>(smem_raw + lay.prow_off);      // [2][C][L] candidate rows
     double* fcol = reinterpret_cast<double*>(smem_raw + lay.fcol_off);       // [2][R] multipliers
     Cand* infos = reinterpret_cast<Cand*>(smem_raw + lay.info_off);          // [2][C] candidates
+    Cand* parts = reinterpret_cast<Cand*>(smem_raw + lay.part_off);          // [NT / 32] phase A's
     int* phys_at = reinterpret_cast<int*>(smem_raw + lay.phys_off);
     int* lpos = reinterpret_cast<int*>(smem_raw + lay.lpos_off);
     int* piv = reinterpret_cast<int*>(smem_raw + lay.piv_off);
@@ -432,6 +434,7 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
 
     const int r0 = rank * R;
     const int nrows = max(0, min(R, L - r0));
+    const int nparts = (nrows + 31) / 32;  // warps that hold rows in phase A
     const int row_groups = NT / L;  // thread (tr, j): column j, rows tr, tr + row_groups, ...
     const int j = tid % L, tr = tid / L;
     const bool active = mt < 0 && tr < row_groups;
@@ -542,21 +545,47 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
             if (active) elim_column(M, L, j, fk, pj, j == k, tr, row_groups, nrows, pl, pl);
             break;
         }
-        // A: column k+1, one row per thread
-        if (tid < nrows) {
-            const double pjn = prow[k + 1] * inv;
-            if (tid == pl) {
-                fn[tid] = pjn;
-            } else {
-                double b = M[(size_t)tid * L + k + 1];
-                if (tid == pr) b *= pinv;
-                const double nv = elim_val(fk[tid], b, pjn, false);
-                M[(size_t)tid * L + k + 1] = nv;
-                fn[tid] = nv;
+        // A: column k+1, one row per thread; the same values give this
+        // CTA's candidate for column k+1, a warp argmax each.  A row is
+        // eligible if no step before k took it (position >= k) and step k
+        // did not (it is not p); the row that was at position k moves to
+        // w.pos.  Thread NT - 1 rewrites the position table meanwhile, but
+        // only for rows p and phys_at[k], and both values of the latter's
+        // entry (k before, w.pos after) give the same answer here.
+        if (tid < nparts * 32) {
+            uint64_t key = 0;
+            double val = 0.0;
+            int pos = INT_MAX, phys = -1;
+            if (tid < nrows) {
+                const double pjn = prow[k + 1] * inv;
+                if (tid == pl) {
+                    fn[tid] = pjn;
+                } else {
+                    double b = M[(size_t)tid * L + k + 1];
+                    if (tid == pr) b *= pinv;
+                    const double nv = elim_val(fk[tid], b, pjn, false);
+                    M[(size_t)tid * L + k + 1] = nv;
+                    fn[tid] = nv;
+                    const int lp = lpos[r0 + tid];
+                    if (lp >= k) {
+                        const uint64_t mag = (uint64_t)__double_as_longlong(nv) & ~(1ull << 63);
+                        key = mag > kInfBits ? kInfBits : mag;
+                        val = nv;
+                        pos = lp == k ? w.pos : lp;
+                        phys = r0 + tid;
+                    }
+                }
             }
+            const Cand wc = warp_argmax(key, val, 0.0, pos, phys);
+            if ((tid & 31) == 0) parts[tid >> 5] = wc;
         }
-        __syncthreads();  // column k+1 and the position table are up to date
-        const Cand c = warp_candidate(M, L, nrows, r0, lpos, k + 1);
+        __syncthreads();  // column k+1, the position table and the warp candidates are up to date
+        Cand c;
+        {
+            Cand q{0, 0.0, 0.0, INT_MAX, -1};
+            if ((tid & 31) < nparts) q = parts[tid & 31];
+            c = warp_argmax(q.key, q.val, 0.0, q.pos, q.phys);
+        }
         if (mt >= 0) {  // the messenger: the candidate now, its row once B is done
             send_info(c, s ^ 1);
             asm volatile("bar.sync 1, %0;" ::"n"(NT + kMessengers) : "memory");

@@ -92,7 +92,8 @@ def test_refinement_is_decided_on_the_device(spin):
     assert info["fail_leaf"] == -1
     Xb, infob = spin.invert(Ad, leaf=128, precision="bf16x3", tol=1e-10)
     np.testing.assert_array_equal(X.cpu().numpy(), Xb.cpu().numpy())
-    assert infob["rel_residual"] == info["rel_residual"]
+    # the sums of squares behind the residual are atomic adds: same X, last bits may differ
+    assert abs(infob["rel_residual"] - info["rel_residual"]) <= 1e-12 * info["rel_residual"]
     assert oracle.residual(A, X.cpu().numpy())[0] <= 1e-10
 
 
