@@ -73,7 +73,7 @@ def test_serve_mix_equals_alone(spin, priority_order):
         X, r = results[t]
         assert r["status"] == 0, r
         Xa, ra = serve_alone(spin, A, prec, tol)
-        assert ra["status"] == 0 and ra["batch"] == 1
+        assert ra["status"] == 0 and ra["batch"] == (1 if A.shape[0] <= 1024 else 0)  # orders above 1024: single path
         np.testing.assert_array_equal(X, Xa)
         lib, info = spin.invert(torch.from_numpy(A).cuda(), precision=prec, tol=tol)
         lib = lib.cpu().numpy()
