@@ -341,17 +341,19 @@ int read_info(StreamState* st, cudaStream_t s, spin_info* info) {
 // of A for the refinement residual.
 struct MixLayout {
     size_t region0, scratch, apl, off_scratch, off_apl, off_norms, total;
-    int sr;
+    int sr;  // digit slices of the certifying residuals (and of A's cached planes)
+    int s0;  // slices of the first residual's pairs (<= sr)
 };
 
 size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 MixLayout mix_layout(int64_t n, int64_t leaf, const spin_opts& o) {
     MixLayout L;
-    // 8-bit digits are relative to the largest entry of each row (column), so
-    // the residual is accurate to ~2^(-8 s) * sqrt(n) in the normalised
-    // measure: 6 slices certify down to ~1e-12, 7 below that.
-    L.sr = o.residual_slices > 0 ? o.residual_slices : (o.tol >= 1e-11 ? 6 : 7);
+    // 9-bit digits relative to the largest entry of each row (column): the
+    // residual's error is ~0.6 sqrt(n) 2^-(9s-1) in the normalised measure
+    // (residual_error_model); slices per round from that model
+    L.sr = o.residual_slices > 0 ? o.residual_slices : residual_slices_for(n, o.tol);
+    L.s0 = o.residual_slices > 0 ? o.residual_slices : first_residual_slices_for(n, o.tol, L.sr);
     const size_t nn = (size_t)n * (size_t)n;
     L.region0 = round256(std::max(ws_fp64_elems(n, leaf), nn) * sizeof(double));
     size_t sc = 0;
@@ -430,8 +432,10 @@ int refine(Run& r, StreamState* st, const double* A, int64_t lda, double* X, int
     }
     const double f = 2.0 * (double)n * n * n;
     const int sr = L.sr;
-    const int pairs = sr * (sr + 1) / 2;
     for (int it = 0; it <= o.max_refine; it++) {
+        // the first residual only feeds the update: fewer slice pairs
+        const int s_it = it == 0 ? L.s0 : sr;
+        const int pairs = s_it * (s_it + 1) / 2;
         SPIN_CUDA_TRY(cudaMemsetAsync(norms + 1, 0, 2 * sizeof(double), s));
         SplitPlan sp;
         RET(plan_ozaki(0, n, n, sr, scratch, L.scratch, &sp));
@@ -444,10 +448,10 @@ int refine(Run& r, StreamState* st, const double* A, int64_t lda, double* X, int
         {
             ProfScope ps(r.prof, s, SPIN_KERNEL_RESIDUAL, -1, n, n, n, pairs * f, 2.0 * sr * 2.0 * n * n + 8.0 * n * n,
                          act);
-            RET(product_ozaki(sp, n, n, n, -1.0, 0.0, nullptr, 0, R, n, 1, &norms[2], r.err, s, act));
+            RET(product_ozaki(sp, n, n, n, -1.0, 0.0, nullptr, 0, R, n, 1, &norms[2], r.err, s, act, s_it));
         }
-        RET(launch_refine_decide(norms, norms + 1, norms + 2, 1, o.tol, it, o.max_refine, act, st->rel(),
-                                 st->iters(), st->info_dev, s));
+        RET(launch_refine_decide(norms, norms + 1, norms + 2, 1, o.tol, residual_error_model(n, s_it), it,
+                                 o.max_refine, act, st->rel(), st->iters(), st->info_dev, s));
         if (it == o.max_refine) break;
         // X <- X + X R with three-plane BF16 splits and six products (~2^-22
         // relative): the correction's own error enters the next residual

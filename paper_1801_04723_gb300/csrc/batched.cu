@@ -49,7 +49,14 @@ struct Bucket {
     size_t cache_per;      // cached digit planes of A per matrix
     size_t arena_offset;   // bytes into the plan's arena
     int stream;            // pool stream the bucket runs on
+    int sr, s0;            // mixed: digit slices of the certifying residuals and of the first one
 };
+
+// Residual slices of a bucket of order n (the single-matrix rule).
+void set_slices(Bucket& b, const spin_opts& o) {
+    b.sr = o.residual_slices > 0 ? o.residual_slices : residual_slices_for(b.n, o.tol);
+    b.s0 = o.residual_slices > 0 ? o.residual_slices : first_residual_slices_for(b.n, o.tol, b.sr);
+}
 
 struct BatchPlan {
     std::vector<uint64_t> key;
@@ -68,7 +75,7 @@ struct BatchPlan {
     int graph_kernels = 0;  // kernel launches in the captured graph
     // mixed precision
     int precision = SPIN_FP64;
-    int fp64_levels = 2, sr = 6, max_refine = 6;
+    int fp64_levels = 2, max_refine = 6;
     double tol = 1e-10;
     unsigned char* arena = nullptr;
     size_t arena_bytes = 0;
@@ -321,7 +328,7 @@ int binv_mixed(BRun& r, BMix& x, int depth, BatchView A, BatchView X, const doub
 // order): SPIN_ERR_NOT_CONVERGED when the cap is reached above tol.
 int bucket_refine(BatchPlan& p, const Bucket& b, cudaStream_t s) {
     const int count = p.count;
-    const int sr = p.sr;
+    const int sr = b.sr;
     BatchView Av{p.a_base + b.first, p.a_ld + b.first, 0, 0, 0};
     BatchView Xv{(const double* const*)(p.x_base + b.first), nullptr, b.n, 0, 0};
     BatchView Rv{(const double* const*)(p.w_base + b.first), nullptr, b.n, 0, 0};
@@ -348,9 +355,11 @@ int bucket_refine(BatchPlan& p, const Bucket& b, cudaStream_t s) {
         SPIN_CUDA_TRY(cudaMemsetAsync(nX, 0, b.count * sizeof(double), s));
         SPIN_CUDA_TRY(cudaMemsetAsync(nR, 0, b.count * sizeof(double), s));
         BRET(launch_ozaki_split_batched(Xv, (int)b.n, (int)b.n, true, sr, xex, xplanes, ld, nX, b.count, s, act, nv));
+        // the first residual only feeds the update: fewer slice pairs
+        const int s_it = it == 0 ? b.s0 : sr;
         TcGemmParams q = {};
         q.M = q.N = q.K = (int)b.n;
-        tc_pairs_ozaki(q, sr);
+        tc_pairs_ozaki(q, s_it);
         q.alpha = -1.0;
         q.beta = 0.0;
         q.add_identity = 1;
@@ -364,8 +373,8 @@ int bucket_refine(BatchPlan& p, const Bucket& b, cudaStream_t s) {
         q.d_base = p.w_base + b.first;
         q.d_ld = b.n;
         BRET(launch_tc_gemm(TcOperand{aplanes, (int)b.n, sr, ld}, TcOperand{xplanes, (int)b.n, sr, ld}, q, s));
-        BRET(launch_refine_decide(nA, nX, nR, b.count, p.tol, it, p.max_refine, act, p.rel + b.first,
-                                  p.iters + b.first, rec, s));
+        BRET(launch_refine_decide(nA, nX, nR, b.count, p.tol, residual_error_model(b.n, s_it), it, p.max_refine, act,
+                                  p.rel + b.first, p.iters + b.first, rec, s));
         p.kernels += 6;
         if (it == p.max_refine) break;
         BRET(launch_split_planes_batched(Xv, (int)b.n, (int)b.n, false, 3, xp, ld, b.count, s, act));
@@ -404,7 +413,6 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
     p.tol = o.tol;
     p.max_refine = o.max_refine;
     p.fp64_levels = o.fp64_levels;
-    p.sr = o.residual_slices > 0 ? o.residual_slices : (o.tol >= 1e-11 ? 6 : 7);
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] < n[b]; });
@@ -422,8 +430,9 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
         if (mixed) b.ws_elems = std::max<size_t>(b.ws_elems, (size_t)b.n * (size_t)b.n);  // holds R
         b.ws_offset = ws_total;
         ws_total += b.ws_elems * (size_t)b.count;
-        b.scratch_per = mixed ? mixed_scratch_per(b.n, b.leaf, p.fp64_levels, p.sr) : 0;
-        b.cache_per = mixed ? mixed_cache_per(b.n, p.sr) : 0;
+        set_slices(b, o);
+        b.scratch_per = mixed ? mixed_scratch_per(b.n, b.leaf, p.fp64_levels, b.sr) : 0;
+        b.cache_per = mixed ? mixed_cache_per(b.n, b.sr) : 0;
         b.arena_offset = p.arena_bytes;
         p.arena_bytes += (size_t)b.count * (b.scratch_per + b.cache_per);
         b.stream = 0;
@@ -585,7 +594,7 @@ struct DirectLayout {
     size_t upload, records, active, rel, iters, norms, err, ws, arena, total;
     size_t ws_elems, scratch_per, cache_per;
     int64_t leaf;
-    int sr;
+    int sr, s0;
 };
 
 DirectLayout direct_layout(int64_t n, int count, const spin_opts& o) {
@@ -593,7 +602,11 @@ DirectLayout direct_layout(int64_t n, int count, const spin_opts& o) {
     const bool mixed = o.precision != SPIN_FP64;
     const size_t c = (size_t)count;
     L.leaf = batched_leaf(n, o.leaf);
-    L.sr = o.residual_slices > 0 ? o.residual_slices : (o.tol >= 1e-11 ? 6 : 7);
+    Bucket probe;
+    probe.n = n;
+    set_slices(probe, o);
+    L.sr = probe.sr;
+    L.s0 = probe.s0;
     L.ws_elems = std::max<size_t>(fp64_workspace_elems(n, L.leaf), 1);
     if (mixed) L.ws_elems = std::max<size_t>(L.ws_elems, (size_t)n * (size_t)n);  // holds R
     L.scratch_per = mixed ? mixed_scratch_per(n, L.leaf, o.fp64_levels, L.sr) : 0;
@@ -667,7 +680,6 @@ int run_bucket(const double* const* A, const int64_t* lda, double* const* X, con
     p.tol = o.tol;
     p.max_refine = o.max_refine;
     p.fp64_levels = o.fp64_levels;
-    p.sr = L.sr;
     p.a_base = (const double**)(base + L.upload);
     p.a_ld = (int64_t*)(base + L.upload + 8 * c);
     p.x_base = (double**)(base + L.upload + 16 * c);
@@ -694,6 +706,8 @@ int run_bucket(const double* const* A, const int64_t* lda, double* const* X, con
     b.cache_per = L.cache_per;
     b.arena_offset = 0;
     b.stream = 0;
+    b.sr = L.sr;
+    b.s0 = L.s0;
     BRun r{&p.kernels, s, p.records, 0, b.leaf, count, p.ws, (int64_t)b.ws_elems};
     BatchView Av{p.a_base, p.a_ld, 0, 0, 0};
     BatchView Xv{(const double* const*)p.x_base, nullptr, n, 0, 0};

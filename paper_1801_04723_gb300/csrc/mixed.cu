@@ -8,6 +8,7 @@
 // The split planes live in a per-stream scratch arena owned by the caller
 // (struct MixScratch), reused across calls.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "common.cuh"
@@ -49,9 +50,32 @@ void tc_pairs_ozaki(TcGemmParams& p, int slices) {
             q++;
         }
     p.num_pairs = q;
-    for (int w = 0; w < slices; w++) p.group_shift[w] = -14 - 8 * w;
+    // x = 2^(e - 8) sum_t d_t 2^(-9 t): pair (t, u) weighs 2^(e_i + f_j - 16 - 9 (t + u))
+    for (int w = 0; w < slices; w++) p.group_shift[w] = -16 - 9 * w;
     p.exact = 1;
-    p.chunk_kb = 16;  // runs of 1024: every partial sum is an integer of magnitude <= 2^24, exact in FP32
+    p.chunk_kb = 4;  // runs of 256: every partial sum is an integer of magnitude <= 2^24, exact in FP32
+}
+
+// The digit-slice residual's error relative to ||A||_F ||X||_F with s 9-bit
+// slices at order n.  An exact CPU simulation of the product (Householder
+// SPD matrices of condition 1e3 and approximate inverses, n = 1024, every
+// pair product exact, compared with an 80-bit reference) gives
+// 0.55 sqrt(n) 2^-(9s-1) for s = 5 and 0.61 sqrt(n) 2^-(9s-1) for s = 6;
+// the model takes 0.7.
+double residual_error_model(int64_t n, int s) {
+    return 0.7 * std::sqrt((double)n) * std::ldexp(1.0, -(9 * s - 1));
+}
+
+int residual_slices_for(int64_t n, double tol) {
+    for (int s = 5; s < kMaxResidualSlices; s++)
+        if (residual_error_model(n, s) <= 0.01 * tol) return s;
+    return kMaxResidualSlices;
+}
+
+int first_residual_slices_for(int64_t n, double tol, int sr) {
+    for (int s = 4; s < sr; s++)
+        if (residual_error_model(n, s) <= 0.2 * tol) return s;
+    return sr;
 }
 
 int MixScratch::reserve(size_t bytes) {
@@ -179,13 +203,14 @@ int product_bf16x6(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double 
 
 int product_ozaki(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
                   int64_t ldc, double* D, int64_t ldd, int add_identity, double* sumsq, int* err, cudaStream_t s,
-                  const int* active) {
+                  const int* active, int pair_slices) {
     const int slices = sp.slices;
+    if (pair_slices < 1 || pair_slices > slices) pair_slices = slices;
     TcGemmParams p = {};
     p.M = (int)m;
     p.N = (int)n;
     p.K = (int)k;
-    tc_pairs_ozaki(p, slices);
+    tc_pairs_ozaki(p, pair_slices);
     p.alpha = alpha;
     p.beta = beta;
     p.C = C;

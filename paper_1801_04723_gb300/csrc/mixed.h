@@ -8,8 +8,20 @@
 
 namespace spin {
 
-constexpr int kSchurSlices = 7;  // digit slices of the FP64-class Schur complements
-constexpr int kLevelSlices = 4;  // digit slices of the level products in SPIN_MIXED_DIGITS
+constexpr int kSchurSlices = 6;  // 9-bit digit slices of the FP64-class Schur complements (53 bits)
+constexpr int kLevelSlices = 4;  // digit slices of the level products in SPIN_MIXED_DIGITS (35 bits)
+constexpr int kMaxResidualSlices = 7;
+
+// Digit slices of the refinement residual R = I - A X.  The error of the
+// computed rel = ||R||_F / (||A||_F ||X||_F) is modelled as
+// residual_error_model(n, s); a residual that certifies a result (a
+// stopping decision) keeps it within 1 % of tol, the first residual, which
+// only feeds the Newton-Schulz update (its error enters the next residual
+// additively), within 20 %; each decision adds the model error of its own
+// residual to rel before comparing with tol.
+double residual_error_model(int64_t n, int s);
+int residual_slices_for(int64_t n, double tol);
+int first_residual_slices_for(int64_t n, double tol, int sr);
 // Products smaller than this in m or n stay in FP64: below it a product has
 // a handful of 128 x 256 tiles and a short K, so the tensor-core path (two
 // operand splits and a launch that fills a few SMs) costs more than the FP64
@@ -23,7 +35,7 @@ constexpr int64_t kTcMin = 384;
 // num_pairs and the exactness fields of p).
 void tc_pairs_bf16x3(TcGemmParams& p);           // planes hi, lo: hi hi + hi lo + lo hi
 void tc_pairs_bf16x6(TcGemmParams& p);           // planes hi, mid, lo: pairs of weight >= 2^-16
-void tc_pairs_ozaki(TcGemmParams& p, int slices);  // digit pairs t + u < slices, exact runs
+void tc_pairs_ozaki(TcGemmParams& p, int slices);  // digit pairs t + u < slices, exact runs of 256
 
 // A growable device arena for split planes.
 struct MixScratch {
@@ -80,9 +92,11 @@ int split_b_bf16x6(const SplitPlan& sp, const double* B, int64_t ldb, int64_t k,
                    const int* active = nullptr);
 int product_bf16x6(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
                    int64_t ldc, double* D, int64_t ldd, int* err, cudaStream_t s, const int* active = nullptr);
+// pair_slices (0: sp.slices): the pairs t + u < pair_slices of the first
+// pair_slices planes of each operand's stack.
 int product_ozaki(const SplitPlan& sp, int64_t m, int64_t n, int64_t k, double alpha, double beta, const double* C,
                   int64_t ldc, double* D, int64_t ldd, int add_identity, double* sumsq, int* err, cudaStream_t s,
-                  const int* active = nullptr);
+                  const int* active = nullptr, int pair_slices = 0);
 
 int ozaki_split_a(const double* A, int64_t lda, int64_t m, int64_t k, int slices, OzakiCachedA* out,
                   double* sumsq, cudaStream_t s, const int* active = nullptr);
@@ -96,8 +110,10 @@ int ozaki_split_a(const double* A, int64_t lda, int64_t m, int64_t k, int slices
 //   finish  a nonzero *err (a bounded wait that gave up) becomes the status of
 //           every matrix still at SPIN_OK.
 int launch_refine_init(const int32_t* records, int count, int* active, double* rel, int* iters, cudaStream_t s);
-int launch_refine_decide(const double* nA, const double* nX, const double* nR, int count, double tol, int it,
-                         int max_refine, int* active, double* rel, int* iters, int32_t* records, cudaStream_t s);
+// margin: the model error of this round's residual; converged when rel + margin <= tol.
+int launch_refine_decide(const double* nA, const double* nX, const double* nR, int count, double tol, double margin,
+                         int it, int max_refine, int* active, double* rel, int* iters, int32_t* records,
+                         cudaStream_t s);
 int launch_refine_finish(const int* err, int32_t* records, int count, cudaStream_t s);
 
 }  // namespace spin

@@ -7,7 +7,8 @@
 // the tensor-core products and the splits of a matrix whose flag is 0 return
 // at once, so a round costs a matrix nothing once it has converged.  The
 // decision kernel reads the round's sums of squares, computes
-// rel = ||R||_F / (||A||_F ||X||_F) and switches the matrix off when rel <= tol
+// rel = ||R||_F / (||A||_F ||X||_F) and switches the matrix off when
+// rel + margin <= tol, margin being the model error of that round's residual
 // (converged), when rel is not finite, or when the iteration cap is reached
 // (both recorded as SPIN_ERR_NOT_CONVERGED, leaf and column -1, unless a
 // status is already set).
@@ -32,13 +33,14 @@ __global__ void refine_init_kernel(const int32_t* records, int count, int* activ
 }
 
 __global__ void refine_decide_kernel(const double* nA, const double* nX, const double* nR, int count, double tol,
-                                     int it, int max_refine, int* active, double* rel, int* iters, int32_t* records) {
+                                     double margin, int it, int max_refine, int* active, double* rel, int* iters,
+                                     int32_t* records) {
     const int z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= count || active[z] == 0) return;
     const double r = sqrt(nR[z]) / (sqrt(nA[z]) * sqrt(nX[z]));
     rel[z] = r;
     iters[z] = it;
-    if (r <= tol) {
+    if (r + margin <= tol) {
         active[z] = 0;
     } else if (!(r == r) || it >= max_refine) {
         active[z] = 0;
@@ -66,11 +68,12 @@ int launch_refine_init(const int32_t* records, int count, int* active, double* r
     return SPIN_OK;
 }
 
-int launch_refine_decide(const double* nA, const double* nX, const double* nR, int count, double tol, int it,
-                         int max_refine, int* active, double* rel, int* iters, int32_t* records, cudaStream_t s) {
+int launch_refine_decide(const double* nA, const double* nX, const double* nR, int count, double tol, double margin,
+                         int it, int max_refine, int* active, double* rel, int* iters, int32_t* records,
+                         cudaStream_t s) {
     if (count <= 0) return SPIN_OK;
-    refine_decide_kernel<<<blocks_for(count), 256, 0, s>>>(nA, nX, nR, count, tol, it, max_refine, active, rel,
-                                                           iters, records);
+    refine_decide_kernel<<<blocks_for(count), 256, 0, s>>>(nA, nX, nR, count, tol, margin, it, max_refine, active,
+                                                           rel, iters, records);
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
 }
