@@ -68,7 +68,7 @@ struct Cand {
 constexpr uint64_t kInfBits = 0x7ff0000000000000ull;
 
 struct LeafSmemLayout {
-    size_t bar_off, m_off, prow_off, fcol_off, info_off, part_off, phys_off, lpos_off, piv_off, sig_off, total;
+    size_t bar_off, m_off, prow_off, fcol_off, zcol_off, info_off, part_off, phys_off, lpos_off, piv_off, sig_off, total;
 };
 
 // Candidate-row slots hold L doubles padded to an even count, so that every
@@ -85,6 +85,7 @@ __host__ __device__ inline LeafSmemLayout leaf_layout(int L, int R, int C, bool 
     s.prow_off = off = a16(off);
     if (push) off += 2 * (size_t)C * slot_stride(L) * sizeof(double);
     s.fcol_off = off = a16(off); off += 2 * (size_t)R * sizeof(double);
+    s.zcol_off = off; off += 2 * (size_t)R * sizeof(int);  // zero flags of the multipliers
     s.info_off = off = a16(off); off += 2 * (size_t)C * sizeof(Cand);
     s.part_off = off; if (push) off += (size_t)(NT / 32) * sizeof(Cand);  // per-warp candidates of phase A
     s.phys_off = off; off += (size_t)L * sizeof(int);
@@ -153,11 +154,17 @@ __device__ __forceinline__ bool slot_wait(uint64_t* bar, uint32_t parity, uint64
     }
 }
 
+// 1 if f is +0 or -0.  Evaluated once per row and step, where the
+// multiplier is produced, and kept beside it: tested per entry, the same
+// test costs an FP64-pipe instruction per FMA (measured: the pipe ran twice
+// the elimination's FMAs).
+__device__ __forceinline__ int zero_flag(double f) { return ((uint64_t)__double_as_longlong(f) << 1) == 0; }
+
 // Step k's update of one entry: pj is the pivot row's entry scaled by
-// 1/pivot (1/pivot itself in the pivot column, jk), f the row's multiplier,
-// b its current entry; a zero multiplier leaves the entry as it is.
-__device__ __forceinline__ double elim_val(double f, double b, double pj, bool jk) {
-    const bool fz = ((uint64_t)__double_as_longlong(f) << 1) == 0;
+// 1/pivot (1/pivot itself in the pivot column, jk), f the row's multiplier
+// (fz: f is zero), b its current entry; a zero multiplier leaves the entry
+// as it is.
+__device__ __forceinline__ double elim_val(int fz, double f, double b, double pj, bool jk) {
     return fz ? (jk ? f : b) : fma(-f, pj, jk ? 0.0 : b);
 }
 
@@ -165,19 +172,21 @@ __device__ __forceinline__ double elim_val(double f, double b, double pj, bool j
 // (U FMAs in flight per thread); rows skip1 and skip2 are computed but not
 // stored.  Returns the first row not done.
 template <int U>
-__device__ __forceinline__ int elim_rows(double* M, int L, int j, const double* fk, double pj, bool jk, int r, int rg,
-                                         int nrows, int skip1, int skip2) {
+__device__ __forceinline__ int elim_rows(double* M, int L, int j, const double* fk, const int* zk, double pj, bool jk,
+                                         int r, int rg, int nrows, int skip1, int skip2) {
     while (r + (U - 1) * rg < nrows) {
         double f[U], b[U];
+        int z[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             f[u] = fk[r + u * rg];
+            z[u] = zk[r + u * rg];
             b[u] = M[(size_t)(r + u * rg) * L + j];
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const int rr = r + u * rg;
-            const double nv = elim_val(f[u], b[u], pj, jk);
+            const double nv = elim_val(z[u], f[u], b[u], pj, jk);
             if (rr != skip1 && rr != skip2) M[(size_t)rr * L + j] = nv;
         }
         r += U * rg;
@@ -185,12 +194,12 @@ __device__ __forceinline__ int elim_rows(double* M, int L, int j, const double* 
     return r;
 }
 
-__device__ __forceinline__ void elim_column(double* M, int L, int j, const double* fk, double pj, bool jk, int r,
-                                            int rg, int nrows, int skip1, int skip2) {
-    r = elim_rows<8>(M, L, j, fk, pj, jk, r, rg, nrows, skip1, skip2);
-    r = elim_rows<4>(M, L, j, fk, pj, jk, r, rg, nrows, skip1, skip2);
-    r = elim_rows<2>(M, L, j, fk, pj, jk, r, rg, nrows, skip1, skip2);
-    elim_rows<1>(M, L, j, fk, pj, jk, r, rg, nrows, skip1, skip2);
+__device__ __forceinline__ void elim_column(double* M, int L, int j, const double* fk, const int* zk, double pj,
+                                            bool jk, int r, int rg, int nrows, int skip1, int skip2) {
+    r = elim_rows<8>(M, L, j, fk, zk, pj, jk, r, rg, nrows, skip1, skip2);
+    r = elim_rows<4>(M, L, j, fk, zk, pj, jk, r, rg, nrows, skip1, skip2);
+    r = elim_rows<2>(M, L, j, fk, zk, pj, jk, r, rg, nrows, skip1, skip2);
+    elim_rows<1>(M, L, j, fk, zk, pj, jk, r, rg, nrows, skip1, skip2);
 }
 
 // Shared end: scale the last pivot row, undo the row interchanges as column
@@ -267,6 +276,7 @@ __device__ __forceinline__ void leaf_gj_pull_body(const double* __restrict__ src
     const LeafSmemLayout lay = leaf_layout(L, R, C, ROWS_IN_SMEM, false);
     double* M = ROWS_IN_SMEM ? reinterpret_cast<double*>(smem_raw + lay.m_off) : gwork + (size_t)rank * R * L;
     double* fcol = reinterpret_cast<double*>(smem_raw + lay.fcol_off);  // [2][R] multipliers
+    int* zcol = reinterpret_cast<int*>(smem_raw + lay.zcol_off);        // [2][R] their zero flags
     Cand* infos = reinterpret_cast<Cand*>(smem_raw + lay.info_off);     // [2][C] candidates
     int* phys_at = reinterpret_cast<int*>(smem_raw + lay.phys_off);
     int* lpos = reinterpret_cast<int*>(smem_raw + lay.lpos_off);
@@ -294,7 +304,10 @@ __device__ __forceinline__ void leaf_gj_pull_body(const double* __restrict__ src
         const int r = (int)(idx / L), j = (int)(idx % L);
         M[idx] = src[(size_t)(r0 + r) * lds + j];
     }
-    for (int r = tid; r < nrows; r += NT) fcol[r] = src[(size_t)(r0 + r) * lds];  // step 0's multipliers
+    for (int r = tid; r < nrows; r += NT) {  // step 0's multipliers
+        fcol[r] = src[(size_t)(r0 + r) * lds];
+        zcol[r] = zero_flag(fcol[r]);
+    }
     for (int q = tid; q < L; q += NT) { phys_at[q] = q; lpos[q] = q; }
     __syncthreads();
     tc::cluster_sync_all();  // every CTA of the cluster runs before the first remote write
@@ -321,7 +334,9 @@ __device__ __forceinline__ void leaf_gj_pull_body(const double* __restrict__ src
                                             : gwork + (size_t)p * L;
         if (tr < row_groups) {
             const double* fk = fcol + (k & 1) * R;
+            const int* zk = zcol + (k & 1) * R;
             double* fn = fcol + ((k + 1) & 1) * R;
+            int* zn = zcol + ((k + 1) & 1) * R;
             // the previous pivot row is scaled by its 1/pivot first, by the
             // threads that eliminate it (its multiplier is already scaled)
             const int pr = prev_p - r0;
@@ -337,11 +352,17 @@ __device__ __forceinline__ void leaf_gj_pull_body(const double* __restrict__ src
                 // row's: its scaled entry)
                 auto store = [&](int rr, double nv) {
                     if (rr == pl) {
-                        if (jnext) fn[rr] = pj;
+                        if (jnext) {
+                            fn[rr] = pj;
+                            zn[rr] = zero_flag(pj);
+                        }
                         return;
                     }
                     M[(size_t)rr * L + j] = nv;
-                    if (jnext) fn[rr] = nv;
+                    if (jnext) {
+                        fn[rr] = nv;
+                        zn[rr] = zero_flag(nv);
+                    }
                 };
                 // groups of four rows, the next group's loads issued before
                 // this group's stores
@@ -349,21 +370,24 @@ __device__ __forceinline__ void leaf_gj_pull_body(const double* __restrict__ src
                 const int g4 = 4 * row_groups;
                 if (r + g4 - row_groups < nrows) {
                     double f[4], b[4];
+                    int z[4];
 #pragma unroll
                     for (int u = 0; u < 4; u++) {
                         f[u] = fk[r + u * row_groups];
+                        z[u] = zk[r + u * row_groups];
                         b[u] = M[(size_t)(r + u * row_groups) * L + j];
                     }
                     while (true) {
                         double nv[4];
 #pragma unroll
-                        for (int u = 0; u < 4; u++) nv[u] = elim_val(f[u], b[u], pj, jk);
+                        for (int u = 0; u < 4; u++) nv[u] = elim_val(z[u], f[u], b[u], pj, jk);
                         const int rn = r + g4;
                         const bool more = rn + g4 - row_groups < nrows;
                         if (more) {
 #pragma unroll
                             for (int u = 0; u < 4; u++) {
                                 f[u] = fk[rn + u * row_groups];
+                                z[u] = zk[rn + u * row_groups];
                                 b[u] = M[(size_t)(rn + u * row_groups) * L + j];
                             }
                         }
@@ -373,7 +397,7 @@ __device__ __forceinline__ void leaf_gj_pull_body(const double* __restrict__ src
                         if (!more) break;
                     }
                 }
-                for (; r < nrows; r += row_groups) store(r, elim_val(fk[r], M[(size_t)r * L + j], pj, jk));
+                for (; r < nrows; r += row_groups) store(r, elim_val(zk[r], fk[r], M[(size_t)r * L + j], pj, jk));
             }
         }
         prev_p = p;
@@ -425,6 +449,7 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
     double* M = reinterpret_cast<double*>(smem_raw + lay.m_off);             // [R][L] this CTA's rows
     double* slots = reinterpret_cast<double*>(smem_raw + lay.prow_off);      // [2][C][L] candidate rows
     double* fcol = reinterpret_cast<double*>(smem_raw + lay.fcol_off);       // [2][R] multipliers
+    int* zcol = reinterpret_cast<int*>(smem_raw + lay.zcol_off);             // [2][R] their zero flags
     Cand* infos = reinterpret_cast<Cand*>(smem_raw + lay.info_off);          // [2][C] candidates
     Cand* parts = reinterpret_cast<Cand*>(smem_raw + lay.part_off);          // [NT / 32] phase A's
     int* phys_at = reinterpret_cast<int*>(smem_raw + lay.phys_off);
@@ -480,7 +505,10 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
             const int r = (int)(idx / L), jj = (int)(idx % L);
             M[idx] = src[(size_t)(r0 + r) * lds + jj];
         }
-        for (int r = tid; r < nrows; r += NT) fcol[r] = src[(size_t)(r0 + r) * lds];  // step 0's multipliers
+        for (int r = tid; r < nrows; r += NT) {  // step 0's multipliers
+            fcol[r] = src[(size_t)(r0 + r) * lds];
+            zcol[r] = zero_flag(fcol[r]);
+        }
         for (int q = tid; q < L; q += NT) { phys_at[q] = q; lpos[q] = q; }
     }
     // slot s's barrier completes when the C - 1 other CTAs' candidates and
@@ -527,7 +555,9 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
         const double inv = w.inv;
         const double* prow = slots + ((size_t)s * C + p / R) * LS;
         const double* fk = fcol + s * R;
+        const int* zk = zcol + s * R;
         double* fn = fcol + (s ^ 1) * R;
+        int* zn = zcol + (s ^ 1) * R;
         const double pj = (j == k) ? inv : prow[j] * inv;
         // the previous pivot row is scaled by its 1/pivot (its multiplier is
         // already scaled); column k+1 is scaled in A by the thread that
@@ -542,7 +572,7 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
         prev_inv = inv;
         steps_done = k + 1;
         if (k + 1 == L) {  // last step: no next candidate
-            if (active) elim_column(M, L, j, fk, pj, j == k, tr, row_groups, nrows, pl, pl);
+            if (active) elim_column(M, L, j, fk, zk, pj, j == k, tr, row_groups, nrows, pl, pl);
             break;
         }
         // A: column k+1, one row per thread; the same values give this
@@ -560,12 +590,14 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
                 const double pjn = prow[k + 1] * inv;
                 if (tid == pl) {
                     fn[tid] = pjn;
+                    zn[tid] = zero_flag(pjn);
                 } else {
                     double b = M[(size_t)tid * L + k + 1];
                     if (tid == pr) b *= pinv;
-                    const double nv = elim_val(fk[tid], b, pjn, false);
+                    const double nv = elim_val(zk[tid], fk[tid], b, pjn, false);
                     M[(size_t)tid * L + k + 1] = nv;
                     fn[tid] = nv;
+                    zn[tid] = zero_flag(nv);
                     const int lp = lpos[r0 + tid];
                     if (lp >= k) {
                         const uint64_t mag = (uint64_t)__double_as_longlong(nv) & ~(1ull << 63);
@@ -597,7 +629,7 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
         if (active && c.phys >= 0 && rc % row_groups == tr) {
             double v = M[(size_t)rc * L + j];
             if (j != k + 1) {
-                v = elim_val(fk[rc], v, pj, j == k);
+                v = elim_val(zk[rc], fk[rc], v, pj, j == k);
                 M[(size_t)rc * L + j] = v;
             }
             slots[((size_t)(s ^ 1) * C + rank) * LS + j] = v;
@@ -606,7 +638,7 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
         asm volatile("bar.arrive 1, %0;" ::"n"(NT + kMessengers) : "memory");  // own slot row written
 
         // C: every other row, every column but k+1
-        if (active && j != k + 1) elim_column(M, L, j, fk, pj, j == k, tr, row_groups, nrows, pl, rc);
+        if (active && j != k + 1) elim_column(M, L, j, fk, zk, pj, j == k, tr, row_groups, nrows, pl, rc);
     }
     __syncthreads();
     if (steps_done < L) return;  // failure already recorded; X is undefined

@@ -92,17 +92,19 @@ def test_serve_batches_same_order_requests(spin, prec, tol):
     multiple of 32 (449 ... 480 -> 480) run as one batched launch group: each
     reports the group's size, the server counts one group, and every result
     equals the request served alone, bit for bit."""
+    orders = [449, 480, 463, 470, 455, 477]
+    mats = [inputs.spd_gram(n, seed=inputs.SEED_BASE + 500 + i, alpha=0.5) for i, n in enumerate(orders)]
+    srcs = [a if i % 2 else torch.from_numpy(a).cuda() for i, a in enumerate(mats)]  # host and device
+    big = torch.from_numpy(inputs.sdd(4096, seed=3)).cuda()
+    torch.cuda.synchronize()
     srv = spin.Server(hbm_budget_bytes=16 << 30, max_slots=1)
-    big = torch.from_numpy(inputs.sdd(2048, seed=3)).cuda()
-    tb = srv.submit(big, precision="fp64")  # keeps the only slot busy
+    tb = srv.submit(big, precision="fp64")  # keeps the only slot busy (~0.1 s)
     for _ in range(5000):  # bounded wait until it runs
         if srv.stats()["running"] == 1:
             break
         time.sleep(0.001)
-    orders = [449, 480, 463, 470, 455, 477]
-    mats = [inputs.spd_gram(n, seed=inputs.SEED_BASE + 500 + i, alpha=0.5) for i, n in enumerate(orders)]
-    tickets = [srv.submit(a if i % 2 else torch.from_numpy(a).cuda(), precision=prec, tol=tol)
-               for i, a in enumerate(mats)]
+    tickets = [srv.submit(a, precision=prec, tol=tol) for a in srcs]
+    assert srv.stats()["running"] == 1  # all six queued behind it
     got = {}
     deadline = time.time() + 300
     while len(got) < len(tickets) and time.time() < deadline:
