@@ -65,7 +65,7 @@ typedef enum {
                               then Newton-Schulz refinement to opts.tol                       */
     /* 2 is not a precision (a call passing it gets SPIN_ERR_INVALID_ARG)                     */
     SPIN_MIXED_DIGITS = 3  /* products on BF16 tensor cores as 4-slice fixed-point digit
-                              products with exact FP32 runs (~2^-34 relative), then the same
+                              products with exact FP32 runs (~2^-30 relative), then the same
                               refinement -- which usually stops at its first, certifying
                               residual                                                    */
 } spin_precision;
@@ -80,12 +80,13 @@ typedef struct spin_opts {
     int32_t fp64_levels;       /* mixed modes: top recursion levels whose Schur complement
                                   V = IV - A22 is formed FP64-accurately; default 2            */
     int32_t blocking;          /* 1: synchronise the stream and fill *info before returning    */
-    int32_t residual_slices;   /* mixed modes: 9-bit digit slices of the FP64-class refinement
+    int32_t residual_slices;   /* mixed modes: 8-bit digit slices of the FP64-class refinement
                                   residual, 1..7 (every round); 0 (default) = chosen per order
                                   from the residual's error model (about 0.6 sqrt(n)
-                                  2^-(9s-1) of ||A||_F ||X||_F): certifying residuals keep it
-                                  within 1 % of tol (6 slices for tol = 1e-10), the first one,
-                                  which only feeds the update, within 20 % (5 slices)        */
+                                  2^-(8s-1) of ||A||_F ||X||_F): certifying residuals keep it
+                                  within 1 % of tol, the first one, which only feeds the
+                                  update, within 20 % (6 slices for tol = 1e-10 up to
+                                  n = 32768; 7 for tol = 1e-13)                              */
     void* workspace;           /* optional caller device buffer (>= spin_workspace_bytes);
                                   NULL: the library uses its own cached per-device buffer     */
     size_t workspace_bytes;
@@ -410,9 +411,9 @@ int spin_gemm_bf16x3(int64_t m, int64_t n, int64_t k, double alpha,
  * spin_gemm_ozaki: D = beta*C + alpha*(A B) (+ I when add_identity) with
  * FP64-class accuracy on the BF16 tensor cores: every row of A and column
  * of B is scaled by a power of two and cut into `slices` (1..7) fixed-point
- * digit slices of 9 bits (balanced digits of magnitude <= 256, exact in
- * BF16; 9 * slices - 1 bits in all); digit products (<= 2^16) are summed
- * exactly in FP32 runs of 256, the runs in int32, and each slice-pair group
+ * digit slices of 8 bits (balanced digits of magnitude <= 128, exact in
+ * BF16; 8 * slices - 1 bits in all); digit products (<= 2^14) are summed
+ * exactly in FP32 runs of 1024, the runs in int32, and each slice-pair group
  * is scaled into the FP64 result (slice pairs (t, u) with t + u < slices).  The refinement residual
  * R = I - A X of the mixed method is this call with alpha = -1, beta = 0,
  * add_identity = 1.  sumsq_dev (device double, optional) receives

@@ -50,20 +50,20 @@ void tc_pairs_ozaki(TcGemmParams& p, int slices) {
             q++;
         }
     p.num_pairs = q;
-    // x = 2^(e - 8) sum_t d_t 2^(-9 t): pair (t, u) weighs 2^(e_i + f_j - 16 - 9 (t + u))
-    for (int w = 0; w < slices; w++) p.group_shift[w] = -16 - 9 * w;
+    // x = 2^(e - 7) sum_t d_t 2^(-8 t): pair (t, u) weighs 2^(e_i + f_j - 14 - 8 (t + u))
+    for (int w = 0; w < slices; w++) p.group_shift[w] = -14 - 8 * w;
     p.exact = 1;
-    p.chunk_kb = 4;  // runs of 256: every partial sum is an integer of magnitude <= 2^24, exact in FP32
+    p.chunk_kb = 16;  // runs of 1024: every partial sum is an integer of magnitude <= 2^24, exact in FP32
 }
 
-// The digit-slice residual's error relative to ||A||_F ||X||_F with s 9-bit
+// The digit-slice residual's error relative to ||A||_F ||X||_F with s 8-bit
 // slices at order n.  An exact CPU simulation of the product (Householder
 // SPD matrices of condition 1e3 and approximate inverses, n = 1024, every
 // pair product exact, compared with an 80-bit reference) gives
-// 0.55 sqrt(n) 2^-(9s-1) for s = 5 and 0.61 sqrt(n) 2^-(9s-1) for s = 6;
+// 0.62 sqrt(n) 2^-(8s-1) for s = 6 and 0.67 sqrt(n) 2^-(8s-1) for s = 7;
 // the model takes 0.7.
 double residual_error_model(int64_t n, int s) {
-    return 0.7 * std::sqrt((double)n) * std::ldexp(1.0, -(9 * s - 1));
+    return 0.7 * std::sqrt((double)n) * std::ldexp(1.0, -(8 * s - 1));
 }
 
 int residual_slices_for(int64_t n, double tol) {

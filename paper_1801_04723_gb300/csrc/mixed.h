@@ -8,8 +8,8 @@
 
 namespace spin {
 
-constexpr int kSchurSlices = 6;  // 9-bit digit slices of the FP64-class Schur complements (53 bits)
-constexpr int kLevelSlices = 4;  // digit slices of the level products in SPIN_MIXED_DIGITS (35 bits)
+constexpr int kSchurSlices = 7;  // digit slices of the FP64-class Schur complements (55 bits)
+constexpr int kLevelSlices = 4;  // digit slices of the level products in SPIN_MIXED_DIGITS (31 bits)
 constexpr int kMaxResidualSlices = 7;
 
 // Digit slices of the refinement residual R = I - A X.  The error of the
@@ -35,7 +35,7 @@ constexpr int64_t kTcMin = 384;
 // num_pairs and the exactness fields of p).
 void tc_pairs_bf16x3(TcGemmParams& p);           // planes hi, lo: hi hi + hi lo + lo hi
 void tc_pairs_bf16x6(TcGemmParams& p);           // planes hi, mid, lo: pairs of weight >= 2^-16
-void tc_pairs_ozaki(TcGemmParams& p, int slices);  // digit pairs t + u < slices, exact runs of 256
+void tc_pairs_ozaki(TcGemmParams& p, int slices);  // digit pairs t + u < slices, exact runs of 1024
 
 // A growable device arena for split planes.
 struct MixScratch {

@@ -10,15 +10,20 @@
 //       three accumulated in one FP32 TMEM accumulator (~2^-16 relative).
 //   exact mode (fixed-point digit slices, the Ozaki splitting): every row of
 //       A is scaled by a power of two 2^e_i so that |a_ik| < 2^e_i, and the
-//       scaled row is written as 9-bit digits d_1 + 2^-9 d_2 + ... (|d| <= 256,
+//       scaled row is written as digits d_1 + 2^-8 d_2 + ... (|d| <= 128,
 //       each an exact BF16 integer); likewise every column of B.  A product
-//       of two digits is an integer of at most 2^16, so a run of 256 of them
+//       of two digits is an integer of at most 2^14, so a run of 1024 of them
 //       sums exactly in the FP32 accumulator (every partial sum is an integer
 //       of magnitude <= 2^24).  Each run is drained into int32
 //       registers, and each group of slice pairs of equal weight
 //       (t + u = const) is scaled by 2^(e_i + f_j + shift) and added into the
 //       FP64 output: the result is exact up to the truncation of the digit
-//       expansion (9 s - 1 bits for s slices), i.e. FP64-class for 6-7 slices.
+//       expansion (8 s - 1 bits for s slices), i.e. FP64-class for 6-7 slices.
+//       Runs are as long as exactness allows because each run ends with one
+//       FP32-to-int32 conversion per output, and conversions issue at about
+//       16 per clock per SM: with 9-bit digits (|d| <= 256, runs of 256) a
+//       128 x 128 tile needs that whole rate to keep up with the MMAs, and the
+//       kernel measured 970 against 1265 TFLOP/s (n = 32768 residual).
 //
 // Kernel (tc_gemm_kernel): one CTA per output tile, warp-specialised:
 //   warp 0      TMA producer (one lane): a ~192 KB ring of BF16 operand
@@ -990,13 +995,11 @@ __global__ void fill_int_kernel(int* p, int64_t n, int v) {
     if (i < n) p[i] = v;
 }
 
-// Fixed-point digits of x relative to 2^e (|x| < 2^e): with t = x 2^(8-e)
-// (|t| < 256), N = round(|t| 2^(9(s-1))) is an integer below 2^(9s-1);
-// its balanced base-512 digits (low digits in [-256, 255], the top one in
-// [-256, 256]) are the slices, so x = 2^(e-8) sum_i d_i 2^(-9 i) to within
-// half a unit of the last slice.  Every digit is an integer of magnitude
-// <= 256, exact in BF16 (8 significant bits).  Integer arithmetic on the
-// IEEE fields.
+// Fixed-point digits of x relative to 2^e (|x| < 2^e): with t = x 2^(7-e)
+// (|t| < 128), N = round(|t| 2^(8(s-1))) is an integer below 2^(8s-1);
+// its balanced base-256 digits (low digits in [-128, 127], the top one in
+// [-128, 128]) are the slices, so x = 2^(e-7) sum_i d_i 2^(-8 i) to within
+// half a unit of the last slice.  Integer arithmetic on the IEEE fields.
 template <int MAXS>
 __device__ __forceinline__ void digits(double x, int e, int nslices, uint16_t (&d)[MAXS]) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -1007,10 +1010,10 @@ __device__ __forceinline__ void digits(double x, int e, int nslices, uint16_t (&
         fe = 1;  // subnormal: no implicit bit
     else
         m |= 1ull << 52;
-    const int sh = fe - 1075 + 8 - e + 9 * (nslices - 1);  // |x| 2^(8-e+9(s-1)) = m 2^sh
+    const int sh = fe - 1075 + 7 - e + 8 * (nslices - 1);  // |x| 2^(7-e+8(s-1)) = m 2^sh
     unsigned long long N;
     if (sh >= 0)
-        N = m << sh;  // < 2^(9 s - 1) because |t| < 256
+        N = m << sh;  // < 2^(8 s - 1) because |t| < 128
     else if (sh > -64)
         N = (m + (1ull << (-sh - 1))) >> (-sh);
     else
@@ -1019,10 +1022,10 @@ __device__ __forceinline__ void digits(double x, int e, int nslices, uint16_t (&
 #pragma unroll
     for (int i = MAXS - 1; i >= 1; i--) {
         if (i < nslices) {
-            int v = (int)(N & 511u);
-            N >>= 9;
-            if (v >= 256) {
-                v -= 512;
+            int v = (int)(N & 255u);
+            N >>= 8;
+            if (v >= 128) {
+                v -= 256;
                 N += 1;
             }
             dig[i] = v;
@@ -1031,7 +1034,7 @@ __device__ __forceinline__ void digits(double x, int e, int nslices, uint16_t (&
     dig[0] = (int)N;
 #pragma unroll
     for (int i = 0; i < MAXS; i++)
-        if (i < nslices) d[i] = bf16_bits((float)(neg ? -dig[i] : dig[i]));  // |d| <= 256: exact
+        if (i < nslices) d[i] = bf16_bits((float)(neg ? -dig[i] : dig[i]));  // |d| <= 128: exact
 }
 
 constexpr int kMaxSlices = 8;
@@ -1179,8 +1182,8 @@ int64_t tc_ld(int64_t k) { return (k + 7) / 8 * 8; }
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& prm, cudaStream_t s) {
     if (prm.M <= 0 || prm.N <= 0) return SPIN_OK;
     if (prm.K <= 0 || prm.num_pairs <= 0 || prm.num_pairs > kTcMaxPairs) return SPIN_ERR_INVALID_ARG;
-    // runs <= 256 k (exactness: 256 products of at most 2^16) made of whole pipeline stages
-    if (prm.exact && (prm.chunk_kb < 1 || prm.chunk_kb > 4 || prm.chunk_kb % KSUB_EXACT != 0)) return SPIN_ERR_INVALID_ARG;
+    // runs <= 1024 k (exactness: 1024 products of at most 2^14) made of whole pipeline stages
+    if (prm.exact && (prm.chunk_kb < 1 || prm.chunk_kb > 16 || prm.chunk_kb % KSUB_EXACT != 0)) return SPIN_ERR_INVALID_ARG;
     if (prm.batch < 0 || prm.batch > 65535) return SPIN_ERR_INVALID_ARG;
     if (prm.batch && (int64_t)prm.batch * a.rows * a.slices > INT32_MAX) return SPIN_ERR_INVALID_ARG;
     if (prm.batch && (int64_t)prm.batch * b.rows * b.slices > INT32_MAX) return SPIN_ERR_INVALID_ARG;
