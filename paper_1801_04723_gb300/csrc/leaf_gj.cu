@@ -662,9 +662,11 @@ leaf_gj_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__
     leaf_gj_body<ROWS_IN_SMEM, PUSH>(src, lds, dst, ldd, gwork, L, R, info, leaf_index, lw);
 }
 
-// Batched form: cluster blockIdx.y inverts problem z = blockIdx.y.
+// Batched form: cluster blockIdx.y inverts problem z = blockIdx.y.  Many
+// small leaves share an SM, so the registers are held to two CTAs per SM
+// (one leaf's step is latency-bound: a second CTA fills its gaps).
 template <bool ROWS_IN_SMEM, bool PUSH>
-__global__ void __launch_bounds__(PUSH ? NT + kMessengers : NT, 1)
+__global__ void __launch_bounds__(PUSH ? NT + kMessengers : NT, 2)
 leaf_gj_batched_kernel(BatchView src, BatchView dst, double* __restrict__ gwork, int64_t gwork_stride, int L, int R,
                        int32_t* info, int leaf_index, LeafWait lw) {
     const int z = blockIdx.y;
