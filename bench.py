@@ -861,9 +861,39 @@ def run_serve(args, w: dict):
                 done.append(r)
 
     submitted = 0
+    # Finished requests are polled on every pass of the loop, also while the
+    # client waits for the producer: results that nobody polls hold the
+    # server's budget, and the producer may be waiting for that memory.
+    # A run that makes no progress for stall_s aborts with its counters.
+    stall_s = 300.0
+    progress = {"t": time.perf_counter(), "done": 0, "last_print": time.perf_counter()}
+
+    def check_progress(where):
+        now = time.perf_counter()
+        if len(done) != progress["done"] or submitted != progress.get("submitted"):
+            progress.update(t=now, done=len(done), submitted=submitted)
+        if now - progress["last_print"] > 10.0:
+            progress["last_print"] = now
+            free, _ = torch.cuda.mem_get_info()
+            print(f"[serve] t={now - t0:.0f}s submitted={submitted} done={len(done)} pending={len(pending)} "
+                  f"shed={shed} ahead={state['ahead'] >> 20} MB device_free={free >> 30} GB "
+                  f"server={srv.stats()}", file=sys.stderr, flush=True)
+        if now - progress["t"] > stall_s:
+            raise RuntimeError(f"serving run made no progress for {stall_s:.0f} s ({where}): submitted={submitted} "
+                               f"done={len(done)} pending={len(pending)} shed={shed} "
+                               f"generation_retries={state['gen_retries']} server={srv.stats()}")
+
+    def next_item():
+        while True:
+            collect()
+            try:
+                return ready.get(timeout=0.002)
+            except queue.Empty:
+                check_progress("waiting for input generation")
+
     with ClockSampler(local) as clk:
         while True:
-            item = ready.get(timeout=600)
+            item = next_item()
             if item is None:
                 break
             j, t_arr, n, mixed, A, ev = item
@@ -872,6 +902,7 @@ def run_serve(args, w: dict):
             while time.perf_counter() - t0 < t_arr:
                 collect()  # poll finished requests while waiting for the next arrival
                 time.sleep(0.0005)
+            check_progress("submitting")
             ev.synchronize()
             if mixed:
                 prec, tol = "bf16x3", 1e-10
@@ -892,6 +923,7 @@ def run_serve(args, w: dict):
         t_last_arrival = time.perf_counter() - t0
         while pending:
             collect()
+            check_progress("draining")
             time.sleep(0.001)
         makespan = time.perf_counter() - t0
     st = srv.stats()
@@ -952,6 +984,11 @@ def run_serve(args, w: dict):
 
 
 def run_gemm_probe(args):
+    """One digit-slice (6 slices, 21 pairs: the refinement residual's form)
+    and one bf16x3 tensor-core product of order n, each timed 3 times after a
+    warm-up (CUDA events, splits included), with the SM clock sampled over
+    the timed calls: the kernel variant switches (SPIN_TC_WIDE, SPIN_TC_PAIR)
+    are compared this way, clock and all."""
     import torch
 
     import paper_1801_04723_gb300 as spin
@@ -962,18 +999,24 @@ def run_gemm_probe(args):
     A = inputs.sdd_device(n, SEED_BASE + 11, "cuda")
     B = inputs.sdd_device(n, SEED_BASE + 12, "cuda")
     D = torch.empty_like(A)
-    out = {"probe": "tensor-core products", "n": n}
+    out = {"probe": "tensor-core products", "n": n,
+           "variant": {k: os.environ.get(k, "") for k in ("SPIN_TC_WIDE", "SPIN_TC_PAIR")}}
     for name, fn, pairs in (("ozaki6", lambda: spin.gemm_ozaki(A, B, slices=6, out=D), 21),
                             ("bf16x3", lambda: spin.gemm_bf16x3(A, B, out=D), 3)):
         fn()  # warm
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        fn()
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        out[name] = {"ms_with_splits": ms, "bf16_tflops_incl_splits": pairs * 2.0 * n ** 3 / (ms * 1e-3) / 1e12}
+        times = []
+        with ClockSampler(0) as clk:
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        out[name] = {"ms_with_splits": ms, "bf16_tflops_incl_splits": pairs * 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                     "clocks": clk.summary()}
     out["device_error"] = spin.take_device_error()
     print(json.dumps(out), flush=True)
     return 0
@@ -1049,14 +1092,17 @@ def run_leaf_batch(args):
     torch.cuda.synchronize()
     best = float("inf")
     with ClockSampler(0) as clk:
-        for _ in range(5):
+        for _ in range(3):
+            # five calls back to back between the events: the host's
+            # marshalling of the next call overlaps the previous call's kernel
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            _, info = spin.invert_batched(As, outs=Xs)
+            for _ in range(5):
+                _, info = spin.invert_batched(As, outs=Xs, blocking=False)
             e1.record()
             e1.synchronize()
-            best = min(best, e0.elapsed_time(e1))
+            best = min(best, e0.elapsed_time(e1) / 5)
     assert int(info.abs().sum()) == 0
     c = clk.summary()
     mhz = c["sm_mhz"] or 2070.0
@@ -1064,7 +1110,8 @@ def run_leaf_batch(args):
     out = {"leaf_batch": {"L": L, "count": count, "ms": best, "us_per_step": per_step_us,
                           "cycles_per_step": per_step_us * mhz, "fma_per_step_per_leaf": L * L,
                           "fp64_bound_cycles_per_step": L * L / 2.0,
-                          "how": "CUDA events around one spin_invert_batched call, best of 5 after 2 warm-ups"},
+                          "how": "CUDA events around 5 back-to-back spin_invert_batched calls (per call), best of "
+                                 "3 after 2 warm-ups"},
            "clocks": c}
     print(json.dumps(out), flush=True)
     return 0

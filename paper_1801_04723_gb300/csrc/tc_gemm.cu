@@ -1166,14 +1166,18 @@ bool use_pair_kernel() {
     return v != 0;
 }
 
-// Large exact products use the 256-wide tiles unless SPIN_TC_WIDE=0.
-bool use_wide_exact() {
+// Large exact products use the 256-wide tiles unless SPIN_TC_WIDE=0
+// (SPIN_TC_WIDE=2: at any K as well, for measurement).
+int wide_exact_mode() {
     static const int v = [] {
         const char* e = getenv("SPIN_TC_WIDE");
-        return (e && e[0] == '0') ? 0 : 1;
+        if (e && e[0] == '0') return 0;
+        if (e && e[0] == '2') return 2;
+        return 1;
     }();
-    return v != 0;
+    return v;
 }
+bool use_wide_exact() { return wide_exact_mode() != 0; }
 
 }  // namespace
 
@@ -1200,7 +1204,7 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& p
                 return launch_pair<256, 16>(a, b, p, s);
             return launch_pair<128, kExactEpiWarps>(a, b, p, s);
         }
-        if (use_wide_exact() && wide_tiles >= kExactWideMinTiles && p.K <= kExactWideMaxK)
+        if (use_wide_exact() && wide_tiles >= kExactWideMinTiles && (p.K <= kExactWideMaxK || wide_exact_mode() == 2))
             return launch_impl<256, true, 16>(a, b, p, s);
         return launch_impl<kExactBN, true, kExactEpiWarps>(a, b, p, s);
     }
