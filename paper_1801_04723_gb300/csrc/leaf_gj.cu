@@ -194,9 +194,10 @@ __device__ __forceinline__ int elim_rows(double* M, int L, int j, const double* 
     return r;
 }
 
+template <int G = 8>
 __device__ __forceinline__ void elim_column(double* M, int L, int j, const double* fk, const int* zk, double pj,
                                             bool jk, int r, int rg, int nrows, int skip1, int skip2) {
-    r = elim_rows<8>(M, L, j, fk, zk, pj, jk, r, rg, nrows, skip1, skip2);
+    if constexpr (G >= 8) r = elim_rows<8>(M, L, j, fk, zk, pj, jk, r, rg, nrows, skip1, skip2);
     r = elim_rows<4>(M, L, j, fk, zk, pj, jk, r, rg, nrows, skip1, skip2);
     r = elim_rows<2>(M, L, j, fk, zk, pj, jk, r, rg, nrows, skip1, skip2);
     elim_rows<1>(M, L, j, fk, zk, pj, jk, r, rg, nrows, skip1, skip2);
@@ -645,6 +646,167 @@ __device__ __forceinline__ void leaf_gj_push_body(const double* __restrict__ src
     leaf_finish(M, L, R, r0, nrows, rank, prev_p, prev_inv, lpos, piv, sigma, dst, ldd, info, leaf_index);
 }
 
+// ---------------------------------------------------------------------------
+// One CTA per leaf (the batched paths' leaves, L <= kCtaMaxL): the cluster
+// forms' exchange machinery (slot barriers, async-proxy fences, the
+// messenger's named barrier) costs every step several thousand cycles on a
+// single CTA, against 2 L^2 / 4 cycles of FMAs per sub-partition.  Here a
+// step is: winner (every warp combines the per-warp candidates of the last
+// step's phase A) -> A: column k+1 of every row and this step's candidates
+// -> barrier -> C: every other column of every row; meanwhile one lane
+// computes the next pivot's reciprocal -> barrier.  The arithmetic, the
+// pivot choice and the order of operations on every entry are those of the
+// cluster forms, so the results are identical bit for bit.
+constexpr int kCtaMaxL = 128;
+
+__host__ __device__ inline size_t cta_leaf_smem(int L) {
+    size_t off = (size_t)L * L * sizeof(double);              // M
+    off += 2 * (size_t)L * sizeof(double);                    // fcol
+    off += 2 * (size_t)L * sizeof(int);                       // zcol
+    off = (off + 15) & ~(size_t)15;
+    off += (size_t)(NT / 32) * sizeof(Cand);                  // parts
+    off += 2 * sizeof(double);                                // sinv
+    off += 4 * (size_t)L * sizeof(int);                       // phys_at, lpos, piv, sigma
+    return (off + 15) & ~(size_t)15;
+}
+
+__global__ void __launch_bounds__(NT, 3)
+leaf_gj_cta_kernel(BatchView srcv, BatchView dstv, int L, int32_t* info_base, int leaf_index) {
+    const int z = blockIdx.x;
+    const int64_t lds = srcv.ld_of(z), ldd = dstv.ld_of(z);
+    const double* __restrict__ src = srcv.ptr(z, lds);
+    double* __restrict__ dst = const_cast<double*>(dstv.ptr(z, ldd));
+    int32_t* info = info_base + (int64_t)z * INFO_WORDS;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* M = reinterpret_cast<double*>(smem_raw);
+    double* fcol = M + (size_t)L * L;                        // [2][L] multipliers
+    int* zcol = reinterpret_cast<int*>(fcol + 2 * L);        // [2][L] their zero flags
+    size_t off = ((size_t)L * L + 2 * L) * sizeof(double) + 2 * (size_t)L * sizeof(int);
+    off = (off + 15) & ~(size_t)15;
+    Cand* parts = reinterpret_cast<Cand*>(smem_raw + off);   // [NT / 32] phase A's candidates
+    double* sinv = reinterpret_cast<double*>(parts + NT / 32);  // [2] next pivot's reciprocal
+    int* phys_at = reinterpret_cast<int*>(sinv + 2);
+    int* lpos = phys_at + L;
+    int* piv = lpos + L;
+    int* sigma = piv + L;
+
+    const int row_groups = NT / L;  // thread (tr, j): column j, rows tr, tr + row_groups, ...
+    const int j = tid % L, tr = tid / L;
+    const bool active = tr < row_groups;
+    const int nparts = (L + 31) / 32;
+
+    for (int idx = tid; idx < L * L; idx += NT) {
+        const int r = idx / L, c = idx % L;
+        M[idx] = src[(size_t)r * lds + c];
+    }
+    for (int r = tid; r < L; r += NT) {  // step 0's multipliers (column 0)
+        fcol[r] = src[(size_t)r * lds];
+        zcol[r] = zero_flag(fcol[r]);
+        phys_at[r] = r;
+        lpos[r] = r;
+    }
+    __syncthreads();
+    // step 0's winner: every warp scans column 0 (contiguous in fcol)
+    Cand w;
+    {
+        uint64_t key = 0;
+        double val = 0.0;
+        int pos = INT_MAX, phys = -1;
+        for (int r = lane; r < L; r += 32) {
+            const double a = fcol[r];
+            const uint64_t mag = (uint64_t)__double_as_longlong(a) & ~(1ull << 63);
+            const uint64_t kk = mag > kInfBits ? kInfBits : mag;
+            if (kk > key || (kk == key && r < pos)) { key = kk; val = a; pos = r; phys = r; }
+        }
+        w = warp_argmax(key, val, 0.0, pos, phys);
+        w.inv = __drcp_rn(w.val);  // once per leaf, in every thread
+    }
+    int steps_done = 0;
+    int prev_p = -1;
+    double prev_inv = 0.0;
+    for (int k = 0; k < L; k++) {
+        if (bad_pivot(w)) {  // identical decision in every thread: the CTA leaves together
+            if (tid == 0) record_failure(info, SPIN_ERR_SINGULAR, leaf_index, k);
+            break;
+        }
+        apply_pivot(k, w, phys_at, lpos, piv);
+        const int p = w.phys;  // the pivot row stays raw in step k
+        const double inv = w.inv;
+        const double* fk = fcol + (k & 1) * L;
+        const int* zk = zcol + (k & 1) * L;
+        double* fn = fcol + ((k + 1) & 1) * L;
+        int* zn = zcol + ((k + 1) & 1) * L;
+        const double pj = (j == k) ? inv : M[(size_t)p * L + j] * inv;
+        // the previous pivot row is scaled by its 1/pivot (its multiplier is
+        // already scaled), except column k+1, which A scales
+        const int pr = prev_p;
+        const double pinv = prev_inv;
+        if (active && pr >= 0 && pr % row_groups == tr && j != k + 1) {
+            double* rp = M + (size_t)pr * L + j;
+            *rp = (j == k - 1) ? pinv : *rp * pinv;
+        }
+        prev_p = p;
+        prev_inv = inv;
+        steps_done = k + 1;
+        if (k + 1 == L) {  // last step: no next column
+            if (active) elim_column<4>(M, L, j, fk, zk, pj, j == k, tr, row_groups, L, p, p);
+            break;
+        }
+        // A: column k+1, one row per thread, and this CTA's candidates for it
+        // (eligible: not taken before step k, not p; the row that was at
+        // position k moves to w.pos -- both values of its position entry,
+        // which thread NT - 1 is rewriting, give the same answer)
+        if (tid < nparts * 32) {
+            uint64_t key = 0;
+            double val = 0.0;
+            int pos = INT_MAX, phys = -1;
+            if (tid < L) {
+                const double pjn = M[(size_t)p * L + k + 1] * inv;
+                if (tid == p) {
+                    fn[tid] = pjn;
+                    zn[tid] = zero_flag(pjn);
+                } else {
+                    double b = M[(size_t)tid * L + k + 1];
+                    if (tid == pr) b *= pinv;
+                    const double nv = elim_val(zk[tid], fk[tid], b, pjn, false);
+                    M[(size_t)tid * L + k + 1] = nv;
+                    fn[tid] = nv;
+                    zn[tid] = zero_flag(nv);
+                    const int lp = lpos[tid];
+                    if (lp >= k) {
+                        const uint64_t mag = (uint64_t)__double_as_longlong(nv) & ~(1ull << 63);
+                        key = mag > kInfBits ? kInfBits : mag;
+                        val = nv;
+                        pos = lp == k ? w.pos : lp;
+                        phys = tid;
+                    }
+                }
+            }
+            const Cand wc = warp_argmax(key, val, 0.0, pos, phys);
+            if (lane == 0) parts[warp] = wc;
+        }
+        __syncthreads();  // candidates, column k+1 and the position table are up to date
+        Cand c;
+        {
+            Cand q{0, 0.0, 0.0, INT_MAX, -1};
+            if (lane < nparts) q = parts[lane];
+            c = warp_argmax(q.key, q.val, 0.0, q.pos, q.phys);
+        }
+        // the next pivot's reciprocal, by one lane while the others eliminate
+        if (tid == NT - 32) sinv[(k + 1) & 1] = __drcp_rn(c.val);  // inf or NaN for no candidate: never used
+        // C: every row but the pivot row, every column but k+1
+        if (active && j != k + 1) elim_column<4>(M, L, j, fk, zk, pj, j == k, tr, row_groups, L, p, p);
+        __syncthreads();  // M, the next reciprocal and the multipliers are up to date
+        w = c;
+        w.inv = sinv[(k + 1) & 1];
+    }
+    __syncthreads();
+    if (steps_done < L) return;  // failure already recorded; X is undefined
+    leaf_finish(M, L, L, 0, L, 0, prev_p, prev_inv, lpos, piv, sigma, dst, ldd, info, leaf_index);
+}
+
 template <bool ROWS_IN_SMEM, bool PUSH>
 __device__ __forceinline__ void leaf_gj_body(const double* __restrict__ src, int64_t lds, double* __restrict__ dst,
                                              int64_t ldd, double* __restrict__ gwork, int L, int R, int32_t* info,
@@ -742,6 +904,16 @@ LeafConfig leaf_config(int64_t L, bool have_scratch, bool batched = false) {
     return c;
 }
 
+// Batched leaves of order <= kCtaMaxL run on the one-CTA kernel unless
+// SPIN_LEAF_CLUSTER_BATCH=1 (the cluster form on one CTA; for measurement).
+bool use_cluster_leaf_for_batches() {
+    static const int v = [] {
+        const char* e = getenv("SPIN_LEAF_CLUSTER_BATCH");
+        return (e && e[0] == '1') ? 1 : 0;
+    }();
+    return v != 0;
+}
+
 template <typename K>
 int prepare_leaf_kernel(K kern) {
     SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
@@ -807,6 +979,19 @@ int launch_leaf_gj_batched(const BatchView& src, const BatchView& dst, int64_t L
                            int64_t scratch_stride, int32_t* info, int leaf_index, int count, cudaStream_t s) {
     if (L <= 0 || count <= 0) return SPIN_OK;
     if (L > kMaxLeaf || count > 65535) return SPIN_ERR_INVALID_ARG;
+    if (L <= kCtaMaxL && !use_cluster_leaf_for_batches()) {
+        static PerDeviceOnce attrs;
+        const size_t smem = cta_leaf_smem((int)L);
+        const int rc = attrs.run([&]() -> int {
+            SPIN_CUDA_TRY(cudaFuncSetAttribute(leaf_gj_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)cta_leaf_smem(kCtaMaxL)));
+            return SPIN_OK;
+        });
+        if (rc != SPIN_OK) return rc;
+        leaf_gj_cta_kernel<<<(unsigned)count, NT, smem, s>>>(src, dst, (int)L, info, leaf_index);
+        SPIN_CUDA_TRY(cudaGetLastError());
+        return SPIN_OK;
+    }
     const LeafConfig c = leaf_config(L, scratch_base != nullptr, true);
     if (c.smem > kSmemBudget) return SPIN_ERR_INVALID_ARG;
     if (c.push) return launch_leaf_batched_impl<true, true>(src, dst, c, L, nullptr, 0, info, leaf_index, count, s);
