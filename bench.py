@@ -773,7 +773,10 @@ def run_serve(args, w: dict):
     spin.lib()
     trace = inputs.serve_trace(w["seed"] + 1000 * rank, rate=args.serve_rate, duration=args.serve_seconds,
                                lo=64, hi=min(8192, w["n"]))
-    gen_stream = torch.cuda.Stream(device)
+    # the client's input generation must keep up with the trace while the
+    # server saturates the GPU: its kernels go ahead of the server's pending blocks
+    lo_prio, hi_prio = torch.cuda.Stream.priority_range()
+    gen_stream = torch.cuda.Stream(device, priority=hi_prio)
 
     def make(j, n, alpha):
         # G G^T / n on the TF32 tensor cores (input preparation only: the
@@ -959,8 +962,11 @@ def run_serve(args, w: dict):
                    "priority_order": args.serve_priority_order, "max_batch": args.serve_max_batch,
                    "hbm_budget_gb": 150, "fp64_class_path": args.serve_fp64_path, "desc": w["desc"],
                    "inputs": "A = G G^T / n + alpha I generated on the device ahead of arrival (G G^T on TF32 "
-                             "tensor cores, symmetrised in FP64), at most 4 GB ahead"},
+                             "tensor cores, symmetrised in FP64; a high-priority stream), at most 4 GB ahead"},
         "arrivals": arrivals, "submitted": submitted, "served": served_ok, "failed": bad, "shed": shed,
+        "client_lag_s": {"p50": pct(sorted(submit_lag.values()), 0.5) / 1e3 if submit_lag else None,
+                         "max": max(submit_lag.values()) / 1e3 if submit_lag else None,
+                         "note": "submit time minus arrival time in the trace (input generation falling behind)"},
         "not_generated": not_generated, "generation_retries": state["gen_retries"],
         "p50_ms": pct(lat, 0.50), "p99_ms": pct(lat, 0.99), "max_ms": lat[-1] if lat else None,
         "latency_from": "arrival time in the trace (p50_ms, p99_ms, max_ms)",
