@@ -98,7 +98,6 @@ constexpr uint32_t A_TILE_BYTES = BM * BK * 2;  // 16 KB
 // and which need the deeper ring (4 stages rather than 2).
 constexpr int KSUB_EXACT = SPIN_KSUB_EXACT;
 constexpr int KSUB_FLOAT = SPIN_KSUB_FLOAT;
-constexpr int kTcPrefetchKb = 0;  // default L2 prefetch distance (k-blocks); 0: none
 constexpr int FLUSH_LIMIT = 96;  // exact runs summed in int32 before an FP64 flush (96 * 2^24 < 2^31)
 constexpr uint64_t WAIT_LIMIT_NS = 10ull * 1000 * 1000 * 1000;
 
@@ -399,23 +398,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            // L2 prefetch of the tiles prefetch_kb k-blocks ahead in the order
-            // the stages are issued (exact: pair by pair, K inside; float: K
-            // outside, pairs inside), so that an L2 miss's DRAM latency is
-            // covered well before the ring reaches it
-            auto prefetch = [&](int pair, int kb) {
-                if (p.prefetch_kb <= 0) return;
-                int q2 = pair, kb2 = kb + p.prefetch_kb;
-                if (EXACT) {
-                    q2 += kb2 / KB;
-                    kb2 %= KB;
-                    if (q2 >= p.num_pairs) return;
-                } else if (kb2 >= KB) {
-                    return;
-                }
-                tma_prefetch_2d(&tmA, kb2 * BK, (int)(z * p.a_zrows) + p.pa[q2] * p.a_rows + m0);
-                tma_prefetch_2d(&tmB, kb2 * BK, (int)(z * p.b_zrows) + p.pb[q2] * p.b_rows + n0);
-            };
             // one stage = k-blocks kb .. kb + KS - 1 of one slice pair (past K: zero fill)
             auto issue = [&](int pair, int kb) -> bool {
                 const int s = it % STAGES;
@@ -429,8 +411,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     tma_load_2d(smB + (s * KS + u) * B_TILE_BYTES, &tmB, (kb + u) * BK,
                                 (int)(z * p.b_zrows) + p.pb[pair] * p.b_rows + n0, &ctl->full[s]);
                 }
-#pragma unroll
-                for (int u = 0; u < KS; u++) prefetch(pair, kb + u);
                 it++;
                 return true;
             };
@@ -1203,20 +1183,6 @@ bool use_wide_exact() { return wide_exact_mode() != 0; }
 
 int64_t tc_ld(int64_t k) { return (k + 7) / 8 * 8; }
 
-// L2 prefetch distance of the tensor-core producer in 64-wide k-blocks
-// (SPIN_TC_PREFETCH overrides it, for measurement; 0 turns it off).
-int tc_prefetch_kb() {
-    static const int v = [] {
-        const char* e = getenv("SPIN_TC_PREFETCH");
-        if (e && *e) {
-            const int x = atoi(e);
-            return x < 0 ? 0 : (x > 256 ? 256 : x);
-        }
-        return kTcPrefetchKb;
-    }();
-    return v;
-}
-
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& prm, cudaStream_t s) {
     if (prm.M <= 0 || prm.N <= 0) return SPIN_OK;
     if (prm.K <= 0 || prm.num_pairs <= 0 || prm.num_pairs > kTcMaxPairs) return SPIN_ERR_INVALID_ARG;
@@ -1226,7 +1192,6 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, const TcGemmParams& p
     if (prm.batch && (int64_t)prm.batch * a.rows * a.slices > INT32_MAX) return SPIN_ERR_INVALID_ARG;
     if (prm.batch && (int64_t)prm.batch * b.rows * b.slices > INT32_MAX) return SPIN_ERR_INVALID_ARG;
     TcGemmParams p = prm;
-    p.prefetch_kb = tc_prefetch_kb();
     p.a_rows = a.rows;
     p.b_rows = b.rows;
     p.a_zrows = p.batch ? (int64_t)a.rows * a.slices : 0;

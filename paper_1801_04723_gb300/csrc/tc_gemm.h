@@ -42,7 +42,6 @@ struct TcGemmParams {
     int* err;                // set to SPIN_ERR_TIMEOUT if a bounded wait gives up
     const int* active;       // if set: problem z runs only while active[z] != 0 (batch = 0: active[0])
     const int* sum_order;    // if set: sumsq covers rows and columns < sum_order[z] only
-    int prefetch_kb;         // filled by launch_tc_gemm: L2 prefetch distance in 64-wide k-blocks (0: none)
     // Batched launches (batch > 0): problem z = blockIdx.y.  The operand
     // planes of problem z follow those of problem z - 1 in the slice stack
     // (a_zrows = slices * rows of one problem, filled by launch_tc_gemm);
