@@ -20,6 +20,10 @@
 // so the six products and two subtractions of each level are six fused
 // GEMM launches, and the only memory beyond A and X is W with
 // ws(n) = max(ws(n1), n1 n2 + n2^2 + ws(n2)) elements (2n^2/3 for n = 2^p).
+// For the plain method at orders up to 8192 the schedule is a small DAG
+// instead of a sequence: II = A21 I (which needs only I) runs on a second
+// stream beside III, S and the recursion on S, and C21, C11 wait for it;
+// II then has its own slab of W (n^2 elements for n = 2^p).
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -50,13 +54,24 @@ void record_cuda_error(cudaError_t e, const char* what, const char* file, int li
 
 int64_t split_order(int64_t n) { return n > 64 ? 32 * ((n + 63) / 64) : (n + 1) / 2; }
 
-static size_t ws_fp64_elems(int64_t n, int64_t leaf) {
+// Workspace of the plain recursion: T (n1 x n2) and S (n2 x n2) per node,
+// plus, in the overlapped schedule, II (n2 x n1) so that II = A21 I can run
+// beside the recursion on S.
+static size_t ws_fp64_elems(int64_t n, int64_t leaf, bool overlap = false) {
     if (n <= leaf) return leaf_scratch_elems(n);
     const int64_t n1 = split_order(n), n2 = n - n1;
-    const size_t a = ws_fp64_elems(n1, leaf);
-    const size_t b = (size_t)(n1 * n2 + n2 * n2) + ws_fp64_elems(n2, leaf);
+    const size_t a = ws_fp64_elems(n1, leaf, overlap);
+    const size_t b = (size_t)(n1 * n2 + n2 * n2) + (overlap ? (size_t)(n2 * n1) : 0) + ws_fp64_elems(n2, leaf, overlap);
     return a > b ? a : b;
 }
+
+// The plain method runs II = A21 I on a second stream, beside the recursion
+// on S (which depends only on III = I A12), for problems up to this order:
+// there the leaves (one cluster of at most 16 SMs) and the small products
+// leave SMs idle.  Above it the products fill the GPU and the schedule stays
+// sequential.
+constexpr int64_t kOverlapMaxN = 8192;
+bool overlap_schedule(int64_t n, int precision) { return precision == SPIN_FP64 && n <= kOverlapMaxN; }
 
 namespace {
 
@@ -99,6 +114,8 @@ struct StreamState {
     Profiler prof;
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    cudaStream_t side = nullptr;        // second stream of the overlapped schedule
+    std::vector<cudaEvent_t> events;    // its fork / join events (one per use within a call)
     int32_t* info_dev = nullptr;   // CTL_BYTES: info record + refinement control
     int32_t* info_host = nullptr;  // pinned mirror
     double* hostA = nullptr;       // device staging for spin_invert_host
@@ -153,6 +170,10 @@ struct Run {
     int leaf_counter;
     int64_t leaf;
     Profiler* prof;  // nullptr when not recording
+    // overlapped schedule (plain method): II on `side`, events from `events`
+    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t>* events = nullptr;
+    size_t next_event = 0;
     // mixed precision only
     int precision = SPIN_FP64;
     int fp64_levels = 0;
@@ -267,9 +288,60 @@ int level_gemm(Run& r, int depth, bool schur, int64_t m, int64_t n, int64_t k, d
     return product_bf16x3(sp, m, n, k, alpha, beta, C, ldc, D, ldd, r.err, r.s);
 }
 
+// A fresh event for this call (created on first use, kept for later calls).
+int take_event(Run& r, cudaEvent_t* e) {
+    if (r.next_event == r.events->size()) {
+        cudaEvent_t ne = nullptr;
+        SPIN_CUDA_TRY(cudaEventCreateWithFlags(&ne, cudaEventDisableTiming));
+        r.events->push_back(ne);
+    }
+    *e = (*r.events)[r.next_event++];
+    return SPIN_OK;
+}
+
 int inv_rec(Run& r, int depth, const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, double* W) {
     if (n <= r.leaf) return leaf_prof(r, depth, A, lda, X, ldx, n, W);
     const int64_t n1 = split_order(n), n2 = n - n1;
+    if (r.side != nullptr) {
+        // Overlapped schedule: the same products on the same operands, so the
+        // same values as the sequential one.  II = A21 I depends only on I:
+        // it runs on the side stream from the moment I is done, beside
+        // III, S and the whole recursion on S; C21 and C11 wait for it.
+        const double* A11 = A;
+        const double* A12 = A + n1;
+        const double* A21 = A + n1 * lda;
+        const double* A22 = A21 + n1;
+        double* X11 = X;
+        double* X12 = X + n1;
+        double* X21 = X + n1 * ldx;
+        double* X22 = X21 + n1;
+        double* T = W;                  // III, n1 x n2
+        double* S = W + n1 * n2;        // -V, n2 x n2
+        double* II = S + n2 * n2;       // II, n2 x n1
+        double* Wsub = II + n2 * n1;
+        const int d = depth;
+        RET(inv_rec(r, d + 1, A11, lda, X11, ldx, n1, W));                                          // I
+        cudaEvent_t e_i = nullptr, e_ii = nullptr;
+        RET(take_event(r, &e_i));
+        RET(take_event(r, &e_ii));
+        SPIN_CUDA_TRY(cudaEventRecord(e_i, r.s));
+        SPIN_CUDA_TRY(cudaStreamWaitEvent(r.side, e_i, 0));
+        {
+            Run rs = r;  // II alone on the side stream (a product, no recursion)
+            rs.s = r.side;
+            rs.side = nullptr;
+            RET(gemm_f64_prof(rs, d, n2, n1, n1, 1.0, A21, lda, X11, ldx, 0.0, nullptr, 0, II, n1));  // II
+        }
+        SPIN_CUDA_TRY(cudaEventRecord(e_ii, r.side));
+        RET(level_gemm(r, d, false, n1, n2, n1, 1.0, X11, ldx, A12, lda, 0.0, nullptr, 0, T, n2));   // III
+        RET(level_gemm(r, d, true, n2, n2, n1, -1.0, A21, lda, T, n2, 1.0, A22, lda, S, n2));       // -V
+        RET(inv_rec(r, d + 1, S, n2, X22, ldx, n2, Wsub));                                        // C22
+        RET(level_gemm(r, d, false, n1, n2, n2, -1.0, T, n2, X22, ldx, 0.0, nullptr, 0, X12, ldx)); // C12
+        SPIN_CUDA_TRY(cudaStreamWaitEvent(r.s, e_ii, 0));
+        RET(level_gemm(r, d, false, n2, n1, n2, -1.0, X22, ldx, II, n1, 0.0, nullptr, 0, X21, ldx)); // C21
+        RET(level_gemm(r, d, false, n1, n1, n2, -1.0, X12, ldx, II, n1, 1.0, X11, ldx, X11, ldx));  // C11
+        return SPIN_OK;
+    }
     const double* A11 = A;
     const double* A12 = A + n1;
     const double* A21 = A + n1 * lda;
@@ -375,7 +447,7 @@ MixLayout mix_layout(int64_t n, int64_t leaf, const spin_opts& o) {
 }
 
 size_t inner_bytes(int64_t n, int64_t leaf, const spin_opts& o) {
-    if (o.precision == SPIN_FP64) return ws_fp64_elems(n, leaf) * sizeof(double);
+    if (o.precision == SPIN_FP64) return ws_fp64_elems(n, leaf, overlap_schedule(n, o.precision)) * sizeof(double);
     return mix_layout(n, leaf, o).total;
 }
 
@@ -499,6 +571,11 @@ int enqueue_once(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n
         inner = ws + R.off_inner;
     }
     if (!mixed) {
+        if (overlap_schedule(n_in, o.precision) && n_in > leaf) {
+            if (st->side == nullptr) SPIN_CUDA_TRY(cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking));
+            r.side = st->side;
+            r.events = &st->events;
+        }
         RET(inv_rec(r, 0, Ain, lda_in, Xout, ldx_out, n_in, (double*)inner));
         if (rbt) RET(launch_rbt_backward(Xout, R.np, kRbtDepth, (const double*)ws, X, ldx, n, s));
         return SPIN_OK;

@@ -51,23 +51,27 @@ def split(n):
     return 32 * ((n + 63) // 64) if n > 64 else (n + 1) // 2
 
 
-def ws_elems(n, leaf):
+def ws_elems(n, leaf, overlap=False):
+    # per node T (n1 x n2) and S (n2 x n2); the overlapped schedule (plain
+    # method, orders up to 8192) adds II (n2 x n1)
     if n <= leaf:
         return n * n if n > 256 else 0
     n1 = split(n)
     n2 = n - n1
-    return max(ws_elems(n1, leaf), n1 * n2 + n2 * n2 + ws_elems(n2, leaf))
+    return max(ws_elems(n1, leaf, overlap), n1 * n2 + n2 * n2 + (n2 * n1 if overlap else 0) + ws_elems(n2, leaf, overlap))
 
 
 @pytest.mark.parametrize("n,leaf", [(1, 1), (2, 1), (1024, 128), (1000, 64), (777, 100), (32768, 512),
-                                    (8192, 2048), (4096, 4096), (65, 8)])
+                                    (8192, 2048), (4096, 4096), (65, 8), (8193, 512)])
 def test_workspace_bytes(L, n, leaf):
-    assert spin.workspace_bytes(n, leaf=leaf) == 8 * ws_elems(n, leaf)
+    assert spin.workspace_bytes(n, leaf=leaf) == 8 * ws_elems(n, leaf, overlap=n <= 8192)
 
 
 def test_workspace_power_of_two_is_two_thirds_n2(L):
-    n, leaf = 1 << 14, 1 << 7
+    n, leaf = 1 << 14, 1 << 7  # above 8192: the sequential schedule, 2 n^2 / 3
     assert abs(spin.workspace_bytes(n, leaf=leaf) / 8 - 2 * n * n / 3) < n * n / 1000
+    n = 1 << 13  # the overlapped schedule: n^2
+    assert abs(spin.workspace_bytes(n, leaf=leaf) / 8 - n * n) < n * n / 1000
 
 
 def test_invalid_arguments_rejected_on_host(L):
