@@ -69,6 +69,7 @@ WORKLOADS = {
 
 
 BATCH_COUNT = 4096
+BATCH_LEAF_CANDIDATES = (32, 64, 128, 256)
 
 
 def measured_peaks() -> dict:
@@ -435,6 +436,17 @@ class BatchWork:
         self.Xhs = [torch.empty_like(a) for a in self.Ahs]
         self.h2d = self.d2h = sum(8 * m * m for m in self.orders)
         self.info = None
+        self.tuned = None
+        if leaf == 0:
+            # per order bucket, the fastest leaf on a bucket of the same size
+            # (outside the timed region); leaf 0 then uses the records
+            t0 = time.perf_counter()
+            rec = spin.autotune_batched_leaf(self.orders, self.precision, candidates=BATCH_LEAF_CANDIDATES)
+            chosen = {}
+            for m in sorted(set(self.orders)):
+                chosen.setdefault(str(rec[m][0]), []).append(m)
+            self.tuned = {"candidates": list(BATCH_LEAF_CANDIDATES), "leaf_orders": chosen,
+                          "tuning_s": time.perf_counter() - t0}
 
     def step(self):
         _, self.info = self.spin.invert_batched(self.As, leaf=self.leaf, outs=self.Xs, blocking=False,
@@ -646,6 +658,9 @@ def run_ours(args, w: dict, n: int, leaf: int):
     if batch:
         config["l2"] = f"inputs larger than L2 ({work.h2d / 1e9:.1f} GB of matrices)"
         config["orders"] = {"min": min(work.orders), "max": max(work.orders), "distinct": len(set(work.orders))}
+        if work.tuned is not None:
+            config["leaf"] = "autotuned per order"
+            config["leaf_autotune"] = work.tuned
     else:
         config["l2"] = (f"inputs larger than L2 ({8 * n * n / 1e9:.1f} GB per matrix)" if n >= 4096 else
                         "inputs smaller than L2; no flush between steps")

@@ -155,8 +155,9 @@ int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t
  *   opts     NULL or spin_opts: precision SPIN_FP64 (plain method) or
  *            SPIN_MIXED_BF16X3 (tensor-core level products, FP64 leaves,
  *            FP64-class Schur complements at the top fp64_levels levels,
- *            Newton-Schulz refinement of every matrix to tol); leaf (0 = n
- *            for n <= 128, else 64), blocking, and for the mixed form tol,
+ *            Newton-Schulz refinement of every matrix to tol); leaf (0 = the
+ *            leaf spin_autotune_batched_leaf recorded for the order, else n
+ *            for n <= 128 and 64 above), blocking, and for the mixed form tol,
  *            max_refine, fp64_levels and residual_slices are used.
  *   info_dev device int32[count] (may be NULL): status of each matrix
  *            (SPIN_OK, SPIN_ERR_SINGULAR, or SPIN_ERR_NOT_CONVERGED for the
@@ -181,6 +182,28 @@ int spin_invert_batched(const double* const* A, const int64_t* lda, double* cons
  * 53-bit uniform of splitmix64(seed) at counter (b * depth + k) * np + i.
  * For tests and for callers that apply the transform themselves. */
 int spin_rbt_diagonals(uint64_t seed, int64_t n, int depth, double* out_dev, spin_stream_t stream);
+
+/*
+ * spin_autotune_batched_leaf: the block-size trade-off of Sec. 5.3 (the
+ * U-shaped running time against the number of splits) per order bucket of
+ * a batch.  orders: host array of the batch's `count` orders (repeats give
+ * the bucket sizes); for every distinct order one lockstep run of its bucket
+ * (seeded strictly diagonally dominant matrices, the same count) per
+ * candidate leaf (host array of ncand orders; candidates above the order
+ * are clamped to it), after a warm-up run, CUDA events around each; the
+ * fastest leaf is recorded for (precision, order) and spin_invert_batched
+ * with opts.leaf = 0 uses it (plans captured before are rebuilt).
+ * precision: SPIN_FP64 or SPIN_MIXED_BF16X3.  leaf_out (host, count): the
+ * chosen leaf for each entry of orders; ms_out (host, count, optional): its
+ * time per bucket run.  Allocates the buckets' matrices and workspaces for
+ * the duration of the call; synchronises the stream.  ncand = 0 (candidates
+ * may be NULL) forgets the records of the listed orders instead and returns
+ * the default leaves in leaf_out.  Errors: SPIN_ERR_INVALID_ARG (null
+ * arrays, count < 1, an order outside [1, 65536], another precision),
+ * SPIN_ERR_OOM (nothing is recorded).
+ */
+int spin_autotune_batched_leaf(const int64_t* orders, int count, int precision, const int* candidates, int ncand,
+                               int* leaf_out, double* ms_out, spin_stream_t stream);
 
 /* Shape of the graph the latest spin_invert_batched on `stream` replays:
  * kernel launches per call and order buckets.  SPIN_ERR_INVALID_ARG if none. */

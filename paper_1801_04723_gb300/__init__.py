@@ -18,6 +18,7 @@ from .binding import (  # noqa: F401
     model_seconds,
     rbt_diagonals,
     autotune_leaf,
+    autotune_batched_leaf,
     gemm_f64,
     gemm_bf16x3,
     gemm_ozaki,

@@ -198,6 +198,10 @@ def lib():
         L.spin_batched_refine_info.restype = ctypes.c_int
         L.spin_autotune_leaf.argtypes = [i64, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp, vp]
         L.spin_autotune_leaf.restype = ctypes.c_int
+        L.spin_autotune_batched_leaf.argtypes = [ctypes.POINTER(i64), ctypes.c_int, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dbl), vp]
+        L.spin_autotune_batched_leaf.restype = ctypes.c_int
         L.spin_take_device_error.argtypes = [vp]
         L.spin_take_device_error.restype = ctypes.c_int
         L.spin_test_leaf_timeout.argtypes = [i64, ctypes.c_int, ctypes.c_double]
@@ -522,6 +526,24 @@ def invert_batched(As, *, leaf: int = 0, outs=None, stream=None, blocking: bool 
     if rc != SPIN_OK:
         raise SpinError(rc, "spin_invert_batched")
     return outs, info
+
+
+def autotune_batched_leaf(orders, precision="fp64", candidates=(32, 64, 128), stream=None) -> dict:
+    """Per order bucket of a batch, the fastest leaf among the candidates
+    (spin_autotune_batched_leaf); recorded for later batched calls with leaf 0.
+    Returns {order: (leaf, ms per bucket run)}.  Empty candidates forget the
+    records of these orders (ms -1, leaf the default)."""
+    orders = [int(v) for v in orders]
+    cand = [int(c) for c in candidates]
+    arr = (ctypes.c_int64 * len(orders))(*orders)
+    carr = (ctypes.c_int * max(len(cand), 1))(*cand)
+    out = (ctypes.c_int * len(orders))()
+    ms = (ctypes.c_double * len(orders))()
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    rc = lib().spin_autotune_batched_leaf(arr, len(orders), p, carr, len(cand), out, ms, _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_autotune_batched_leaf")
+    return {o: (out[i], ms[i]) for i, o in enumerate(orders)}
 
 
 def batched_refine_info(stream=None) -> dict:

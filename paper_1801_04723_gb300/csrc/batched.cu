@@ -397,8 +397,20 @@ int bucket_refine(BatchPlan& p, const Bucket& b, cudaStream_t s) {
     return SPIN_OK;
 }
 
-int64_t batched_leaf(int64_t n, int leaf_opt) {
-    int64_t L = leaf_opt > 0 ? leaf_opt : (n <= 128 ? n : 64);
+// Leaf of a bucket of order n: the caller's, else the one the batched
+// autotuner recorded for (precision, n), else n for n <= 128 and 64 above.
+std::mutex g_bleaf_mu;
+std::map<std::pair<int, int64_t>, int64_t> g_bleaf;  // (precision, order) -> leaf
+uint64_t g_bleaf_gen = 0;                           // bumped on every record (part of the plan key)
+
+int64_t batched_leaf(int64_t n, int leaf_opt, int precision) {
+    int64_t L = leaf_opt > 0 ? leaf_opt : 0;
+    if (L == 0) {
+        std::lock_guard<std::mutex> lk(g_bleaf_mu);
+        auto it = g_bleaf.find(std::make_pair(precision, n));
+        if (it != g_bleaf.end()) L = it->second;
+    }
+    if (L == 0) L = n <= 128 ? n : 64;
     return std::min<int64_t>(L, n);
 }
 
@@ -423,7 +435,7 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
         while (j < count && n[order[j]] == n[order[i]]) j++;
         Bucket b;
         b.n = n[order[i]];
-        b.leaf = batched_leaf(b.n, leaf_opt);
+        b.leaf = batched_leaf(b.n, leaf_opt, o.precision);
         b.count = j - i;
         b.first = i;
         b.ws_elems = std::max<size_t>(fp64_workspace_elems(b.n, b.leaf), 1);
@@ -565,6 +577,10 @@ std::vector<uint64_t> make_key(const double* const* A, const int64_t* lda, doubl
     k.push_back((uint64_t)(int64_t)o.max_refine);
     k.push_back((uint64_t)(int64_t)o.fp64_levels);
     k.push_back((uint64_t)(int64_t)o.residual_slices);
+    {
+        std::lock_guard<std::mutex> lk(g_bleaf_mu);
+        k.push_back(g_bleaf_gen);  // a new autotuned leaf invalidates captured plans
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     k.push_back((uint64_t)dev);
@@ -601,7 +617,7 @@ DirectLayout direct_layout(int64_t n, int count, const spin_opts& o) {
     DirectLayout L;
     const bool mixed = o.precision != SPIN_FP64;
     const size_t c = (size_t)count;
-    L.leaf = batched_leaf(n, o.leaf);
+    L.leaf = batched_leaf(n, o.leaf, o.precision);
     Bucket probe;
     probe.n = n;
     set_slices(probe, o);
@@ -756,7 +772,7 @@ extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, d
     for (int i = 0; i < count; i++) {
         if (n[i] < 1 || n[i] > 65536 || lda[i] < n[i] || A[i] == nullptr || X[i] == nullptr) return SPIN_ERR_INVALID_ARG;
         if (((uintptr_t)A[i] & 7u) || ((uintptr_t)X[i] & 7u)) return SPIN_ERR_INVALID_ARG;
-        if (batched_leaf(n[i], o.leaf) > kMaxLeaf) return SPIN_ERR_INVALID_ARG;
+        if (batched_leaf(n[i], o.leaf, o.precision) > kMaxLeaf) return SPIN_ERR_INVALID_ARG;
     }
     if (count > 65535) return SPIN_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -815,5 +831,136 @@ extern "C" int spin_batched_stats(spin_stream_t stream, int* kernels, int* bucke
     if (it == g_plans.end() || it->second.exec == nullptr) return SPIN_ERR_INVALID_ARG;
     if (kernels) *kernels = it->second.kernels;
     if (buckets) *buckets = (int)it->second.buckets.size();
+    return SPIN_OK;
+}
+
+namespace spin {
+namespace {
+
+// Seeded strictly diagonally dominant matrices for the autotuner: entry
+// (z, i, j) = U(-1, 1) from splitmix64 of its position, plus n on the diagonal.
+__global__ void synth_batch_kernel(double* A, int64_t n, int64_t count, uint64_t seed) {
+    const int64_t total = n * n * count;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t x = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        x ^= x >> 31;
+        double v = 2.0 * (double)(x >> 11) * 0x1.0p-53 - 1.0;
+        const int64_t e = i % (n * n);
+        if (e / n == e % n) v += (double)n;
+        A[i] = v;
+    }
+}
+
+}  // namespace
+}  // namespace spin
+
+// Batched leaf autotuning: for every distinct order of `orders` (with its
+// multiplicity in the list, i.e. the bucket that order forms in a batch), one
+// lockstep run of the bucket per candidate leaf on seeded diagonally
+// dominant matrices, after a warm-up run; the fastest is recorded for
+// (precision, order) and used by spin_invert_batched when opts.leaf is 0.
+extern "C" int spin_autotune_batched_leaf(const int64_t* orders, int count, int precision, const int* candidates,
+                                          int ncand, int* leaf_out, double* ms_out, spin_stream_t stream) {
+    using namespace spin;
+    if (orders == nullptr || count < 1 || ncand < 0 || (ncand > 0 && candidates == nullptr) || leaf_out == nullptr)
+        return SPIN_ERR_INVALID_ARG;
+    if (precision != SPIN_FP64 && precision != SPIN_MIXED_BF16X3) return SPIN_ERR_INVALID_ARG;
+    for (int i = 0; i < count; i++)
+        if (orders[i] < 1 || orders[i] > 65536) return SPIN_ERR_INVALID_ARG;
+    if (ncand == 0) {  // forget the records of these orders
+        {
+            std::lock_guard<std::mutex> lk(g_bleaf_mu);
+            for (int i = 0; i < count; i++) g_bleaf.erase(std::make_pair(precision, orders[i]));
+            g_bleaf_gen++;
+        }
+        for (int i = 0; i < count; i++) {
+            leaf_out[i] = (int)batched_leaf(orders[i], 0, precision);
+            if (ms_out) ms_out[i] = -1.0;
+        }
+        return SPIN_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::map<int64_t, int> mult;
+    for (int i = 0; i < count; i++) mult[orders[i]]++;
+    spin_opts o = spin_opts_default();
+    o.precision = precision;
+    std::map<int64_t, std::pair<int64_t, double>> chosen;  // order -> (leaf, ms)
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SPIN_CUDA_TRY(cudaEventCreate(&e0));
+    SPIN_CUDA_TRY(cudaEventCreate(&e1));
+    int rc = SPIN_OK;
+    for (const auto& kv : mult) {
+        const int64_t n = kv.first;
+        const int k = std::min(kv.second, 65535);
+        double* A = nullptr;
+        double* X = nullptr;
+        void* host = nullptr;
+        const size_t nn = (size_t)n * (size_t)n;
+        if (cudaMalloc(&A, nn * k * sizeof(double)) != cudaSuccess || cudaMalloc(&X, nn * k * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&host, bucket_host_bytes(k)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(A);
+            cudaFree(X);
+            rc = SPIN_ERR_OOM;
+            break;
+        }
+        synth_batch_kernel<<<1024, 256, 0, s>>>(A, n, k, 0x5EEDBA7Cull + (uint64_t)n);
+        std::vector<const double*> ap(k);
+        std::vector<int64_t> ld(k, n);
+        std::vector<double*> xp(k);
+        for (int z = 0; z < k; z++) {
+            ap[z] = A + (size_t)z * nn;
+            xp[z] = X + (size_t)z * nn;
+        }
+        int64_t best = 0;
+        double best_ms = 1e300;
+        std::vector<int64_t> tried;
+        for (int c = 0; c < ncand && rc == SPIN_OK; c++) {
+            const int64_t L = std::min<int64_t>(candidates[c], n);
+            if (candidates[c] < 1 || L > kMaxLeaf || std::find(tried.begin(), tried.end(), L) != tried.end()) continue;
+            tried.push_back(L);
+            o.leaf = (int)L;
+            const size_t wsb = bucket_bytes(n, k, o);
+            void* ws = nullptr;
+            if (cudaMalloc(&ws, wsb) != cudaSuccess) {
+                cudaGetLastError();
+                rc = SPIN_ERR_OOM;
+                break;
+            }
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && rc == SPIN_OK; rep++) {  // warm-up, then timed
+                if (rep == 1) cudaEventRecord(e0, s);
+                rc = run_bucket(ap.data(), ld.data(), xp.data(), nullptr, n, k, o, ws, wsb, host, s);
+                if (rep == 1) cudaEventRecord(e1, s);
+                if (rc == SPIN_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = SPIN_ERR_CUDA;
+            }
+            if (rc == SPIN_OK) cudaEventElapsedTime(&ms, e0, e1);
+            cudaFree(ws);
+            if (rc == SPIN_OK && ms < best_ms) {
+                best_ms = ms;
+                best = L;
+            }
+        }
+        cudaFree(A);
+        cudaFree(X);
+        cudaFreeHost(host);
+        if (rc != SPIN_OK) break;
+        if (best > 0) chosen[n] = std::make_pair(best, best_ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SPIN_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_bleaf_mu);
+        for (const auto& kv : chosen) g_bleaf[std::make_pair(precision, kv.first)] = kv.second.first;
+        g_bleaf_gen++;
+    }
+    for (int i = 0; i < count; i++) {
+        auto it = chosen.find(orders[i]);
+        leaf_out[i] = it == chosen.end() ? 0 : (int)it->second.first;
+        if (ms_out) ms_out[i] = it == chosen.end() ? -1.0 : it->second.second;
+    }
     return SPIN_OK;
 }

@@ -166,3 +166,34 @@ def test_batch_mixed_strided_singular_and_replay(spin):
         assert st[0] == 0 and st[1] == 2 and st[2] == 0
         assert oracle.residual(a0, Xs[0].cpu().numpy())[0] <= 1e-10
         assert oracle.residual(a2, Xs[2].cpu().numpy())[0] <= 1e-10
+
+
+def test_batch_autotuned_leaf(spin):
+    """The batched autotuner picks each order bucket's leaf among the
+    candidates; a batch with leaf 0 then runs every bucket at its recorded
+    leaf (bitwise the same results as that leaf given explicitly, and the
+    oracle's Algorithm 1 at that leaf), until the records are forgotten."""
+    orders = [64] * 6 + [300] * 3 + [1024] * 2
+    cands = (32, 64, 128)
+    try:
+        rec = spin.autotune_batched_leaf(orders, "fp64", candidates=cands)
+        for o in set(orders):
+            leaf, ms = rec[o]
+            assert leaf in {min(c, o) for c in cands}
+            assert ms > 0.0
+        As = [inputs.sdd(o, seed=inputs.SEED_BASE + 700 + i) for i, o in enumerate(orders)]
+        dev = [torch.from_numpy(a).cuda() for a in As]
+        X0, info = spin.invert_batched(dev, leaf=0)
+        assert int(info.abs().sum()) == 0
+        for o in set(orders):
+            idx = [i for i, v in enumerate(orders) if v == o]
+            X1, info1 = spin.invert_batched([dev[i] for i in idx], leaf=rec[o][0])
+            assert int(info1.abs().sum()) == 0
+            for i, x in zip(idx, X1):
+                assert torch.equal(X0[i], x)
+        for i in (0, 6, 9):
+            check(As[i], X0[i].cpu().numpy(), rec[orders[i]][0])
+    finally:
+        back = spin.autotune_batched_leaf(sorted(set(orders)), "fp64", candidates=())
+    for o, (leaf, ms) in back.items():
+        assert leaf == leaf_rule(o) and ms == -1.0
