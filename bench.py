@@ -517,9 +517,16 @@ def time_work(spin, work, steps: int, warmup: int, stream, barrier, local: int) 
     if warmup == 0:
         work.step()  # at least one warm call
         work.finish()
+    # Steps under a second: the launch records come from a second pass of the
+    # same steps, so that the timed region runs as a user's calls do
+    # (repeated calls replay the captured schedule; recording events around
+    # every launch would run it launch by launch).  Longer steps record in
+    # the timed region, where the records cost nothing measurable.
+    separate = bool(e2e_times) and statistics.median(e2e_times) < 1.0
     with ClockSampler(local) as clk:
         barrier()
-        spin.profile_start()
+        if not separate:
+            spin.profile_start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -527,10 +534,18 @@ def time_work(spin, work, steps: int, warmup: int, stream, barrier, local: int) 
             work.step()
         e1.record(stream)
         barrier()
-        recs = spin.profile_collect()
+        recs = None if separate else spin.profile_collect()
         info = work.finish()
+    if separate:
+        barrier()
+        spin.profile_start()
+        for _ in range(steps):
+            work.step()
+        barrier()
+        recs = spin.profile_collect()
+        work.finish()
     return {"ms_local": e0.elapsed_time(e1) / steps, "e2e_times": e2e_times, "recs": recs, "info": info,
-            "clocks": clk.summary()}
+            "clocks": clk.summary(), "records": "separate pass of the same steps" if separate else "timed region"}
 
 
 def kernel_table(recs) -> dict:
@@ -654,7 +669,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
               **({"pretransform": args.pretransform} if args.pretransform else {}),
               **({"fp64_levels": args.fp64_levels} if w["precision"] != "fp64" else {}),
               "matrices_per_gpu": len(work.orders) if batch else 1, "parallelism": f"replicas{world}",
-              "desc": w["desc"]}
+              "desc": w["desc"], "launch_records": t["records"]}
     if batch:
         config["l2"] = f"inputs larger than L2 ({work.h2d / 1e9:.1f} GB of matrices)"
         config["orders"] = {"min": min(work.orders), "max": max(work.orders), "distinct": len(set(work.orders))}
@@ -754,6 +769,7 @@ def mixed_subrecord(args, spin, plain_work, n: int, plain_ms: float, device, str
         "cold": {"first_call_ms": e2e_times[0] * 1e3 if e2e_times else None},
         "roofline": roof,
         "gpu_launches": len(t["recs"]),
+        "launch_records": t["records"],
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"], "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9}
                     for k, v in by_kind.items()},
     }

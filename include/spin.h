@@ -142,6 +142,15 @@ int spin_invert(const double* A, double* X, int64_t n, int64_t lda, int leaf, sp
  * unless blocking or info asks for it; pretransform = 2 waits once for the
  * first attempt's status.  The caller-provided workspace (opts->workspace)
  * must be 256-byte aligned.
+ * Schedule: the recursion (Algorithm 2's driver) is a DAG of product and
+ * leaf launches over views of X, A and the workspace, on the stream and, up
+ * to order 8192 in FP64, a second library stream (II, then C21, beside the
+ * main chain).  A call whose arguments (pointers, leading dimensions,
+ * order, options, workspace) equal the previous call's on the same stream
+ * captures that DAG into a CUDA graph, and later calls with the same
+ * arguments replay it (one graph launch; the dependencies are resolved on
+ * the device, and the graph reads A's current contents).  Calls made while
+ * spin_profile_start is active, and pretransform = 2, launch directly.
  */
 int spin_invert_ex(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n,
                    const spin_opts* opts, spin_info* info, spin_stream_t stream);
@@ -333,6 +342,10 @@ int spin_serve_destroy(spin_server* sv);
  * caller.
  */
 int spin_invert_noalloc(const double* A, double* X, int64_t n, int64_t lda, int leaf, spin_stream_t stream);
+
+/* Graph replays of spin_invert_ex on `stream` so far, and the node count
+ * of its captured schedule (0 if none).  Host values; no synchronisation. */
+int spin_schedule_stats(spin_stream_t stream, int64_t* replays, int64_t* nodes);
 
 /* Synchronise the stream and fill *info with the status of the latest
  * non-blocking spin_invert_ex enqueued on it by this thread. */

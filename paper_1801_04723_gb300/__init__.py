@@ -19,6 +19,7 @@ from .binding import (  # noqa: F401
     rbt_diagonals,
     autotune_leaf,
     autotune_batched_leaf,
+    schedule_stats,
     gemm_f64,
     gemm_bf16x3,
     gemm_ozaki,

@@ -202,6 +202,8 @@ def lib():
                                                  ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dbl), vp]
         L.spin_autotune_batched_leaf.restype = ctypes.c_int
+        L.spin_schedule_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.spin_schedule_stats.restype = ctypes.c_int
         L.spin_take_device_error.argtypes = [vp]
         L.spin_take_device_error.restype = ctypes.c_int
         L.spin_test_leaf_timeout.argtypes = [i64, ctypes.c_int, ctypes.c_double]
@@ -544,6 +546,16 @@ def autotune_batched_leaf(orders, precision="fp64", candidates=(32, 64, 128), st
     if rc != SPIN_OK:
         raise SpinError(rc, "spin_autotune_batched_leaf")
     return {o: (out[i], ms[i]) for i, o in enumerate(orders)}
+
+
+def schedule_stats(stream=None) -> dict:
+    """Graph replays of single inversions on the stream, and the node count
+    of the captured schedule (spin_schedule_stats)."""
+    r, nd = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib().spin_schedule_stats(_stream(stream), ctypes.byref(r), ctypes.byref(nd))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_schedule_stats")
+    return {"replays": r.value, "nodes": nd.value}
 
 
 def batched_refine_info(stream=None) -> dict:

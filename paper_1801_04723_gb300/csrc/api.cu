@@ -124,6 +124,14 @@ struct StreamState {
     int* err_dev = nullptr;        // device: tensor-core bounded-wait failures
     int last_mixed = 0;            // host: the latest call refined (mixed precision)
     int last_pretransformed = 0;   // host: the latest call went through the butterfly transform
+    // The schedule as a CUDA graph: the previous call's arguments, and the
+    // graph captured when a call repeated them (replayed while they repeat).
+    std::vector<uint64_t> prev_key, graph_key;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;    // private capture stream
+    int graph_mixed = 0, graph_rbt = 0;
+    int64_t graph_launches = 0;    // graph replays (host counter)
+    int64_t graph_nodes = 0;       // nodes of the captured graph
     int* active() { return (int*)(info_dev + CTL_ACTIVE); }
     int* iters() { return (int*)(info_dev + CTL_ITERS); }
     double* rel() { return (double*)(info_dev + CTL_REL); }
@@ -306,7 +314,10 @@ int inv_rec(Run& r, int depth, const double* A, int64_t lda, double* X, int64_t 
         // Overlapped schedule: the same products on the same operands, so the
         // same values as the sequential one.  II = A21 I depends only on I:
         // it runs on the side stream from the moment I is done, beside
-        // III, S and the whole recursion on S; C21 and C11 wait for it.
+        // III, S and the whole recursion on S.  C21 = -C22 II needs C22 and
+        // II only: it follows II on the side stream once C22 is done, beside
+        // C12 and C11 (which write X12 and X11); the level ends when both
+        // streams are through.
         const double* A11 = A;
         const double* A12 = A + n1;
         const double* A21 = A + n1 * lda;
@@ -336,10 +347,22 @@ int inv_rec(Run& r, int depth, const double* A, int64_t lda, double* X, int64_t 
         RET(level_gemm(r, d, false, n1, n2, n1, 1.0, X11, ldx, A12, lda, 0.0, nullptr, 0, T, n2));   // III
         RET(level_gemm(r, d, true, n2, n2, n1, -1.0, A21, lda, T, n2, 1.0, A22, lda, S, n2));       // -V
         RET(inv_rec(r, d + 1, S, n2, X22, ldx, n2, Wsub));                                        // C22
+        cudaEvent_t e_c22 = nullptr, e_c21 = nullptr;
+        RET(take_event(r, &e_c22));
+        RET(take_event(r, &e_c21));
+        SPIN_CUDA_TRY(cudaEventRecord(e_c22, r.s));
+        SPIN_CUDA_TRY(cudaStreamWaitEvent(r.side, e_c22, 0));
+        {
+            Run rs = r;  // C21 on the side stream, after II
+            rs.s = r.side;
+            rs.side = nullptr;
+            RET(gemm_f64_prof(rs, d, n2, n1, n2, -1.0, X22, ldx, II, n1, 0.0, nullptr, 0, X21, ldx));  // C21
+        }
+        SPIN_CUDA_TRY(cudaEventRecord(e_c21, r.side));
         RET(level_gemm(r, d, false, n1, n2, n2, -1.0, T, n2, X22, ldx, 0.0, nullptr, 0, X12, ldx)); // C12
         SPIN_CUDA_TRY(cudaStreamWaitEvent(r.s, e_ii, 0));
-        RET(level_gemm(r, d, false, n2, n1, n2, -1.0, X22, ldx, II, n1, 0.0, nullptr, 0, X21, ldx)); // C21
         RET(level_gemm(r, d, false, n1, n1, n2, -1.0, X12, ldx, II, n1, 1.0, X11, ldx, X11, ldx));  // C11
+        SPIN_CUDA_TRY(cudaStreamWaitEvent(r.s, e_c21, 0));
         return SPIN_OK;
     }
     const double* A11 = A;
@@ -593,6 +616,62 @@ int enqueue_once(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n
     return refine(r, st, A, lda, X, ldx, n, o, mix_layout(n, leaf, o), inner);
 }
 
+// Whether repeated calls replay a captured graph (SPIN_GRAPH=0 turns it
+// off, for measurement; read once).
+bool graph_mode() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("SPIN_GRAPH");
+        v = (e && atoi(e) == 0) ? 0 : 1;
+    }
+    return v == 1;
+}
+
+uint64_t bits_of(double x) {
+    uint64_t u;
+    memcpy(&u, &x, sizeof u);
+    return u;
+}
+
+// Every argument that shapes the launch sequence or its operands.
+std::vector<uint64_t> call_key(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, int64_t leaf,
+                               const spin_opts& o, const void* ws) {
+    return {(uint64_t)(uintptr_t)A, (uint64_t)lda, (uint64_t)(uintptr_t)X, (uint64_t)ldx, (uint64_t)n,
+            (uint64_t)leaf, (uint64_t)o.precision, bits_of(o.tol), (uint64_t)o.max_refine,
+            (uint64_t)o.fp64_levels, (uint64_t)o.residual_slices, (uint64_t)o.pretransform, o.rbt_seed,
+            (uint64_t)(uintptr_t)ws};
+}
+
+// Capture the whole schedule of one call (every launch enqueue_once makes,
+// on this stream and on the side stream) into a graph on a private stream.
+int capture_schedule(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, int64_t leaf,
+                     const spin_opts& o, StreamState* st, unsigned char* ws) {
+    if (st->cap == nullptr) SPIN_CUDA_TRY(cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking));
+    if (st->exec) {
+        cudaGraphExecDestroy(st->exec);
+        st->exec = nullptr;
+        st->graph_key.clear();
+    }
+    SPIN_CUDA_TRY(cudaStreamBeginCapture(st->cap, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_once(A, lda, X, ldx, n, leaf, o, o.pretransform == 1, st, st->cap, ws);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st->cap, &graph);
+    if (rc != SPIN_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    SPIN_CUDA_TRY(ec);
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    st->graph_nodes = (int64_t)nodes;
+    const cudaError_t ei = cudaGraphInstantiate(&st->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    SPIN_CUDA_TRY(ei);
+    st->graph_mixed = st->last_mixed;
+    st->graph_rbt = st->last_pretransformed;
+    return SPIN_OK;
+}
+
 int enqueue(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, const spin_opts& o,
             StreamState* st, cudaStream_t s) {
     const int64_t leaf = resolve_leaf(n, o.leaf, o.precision);
@@ -611,7 +690,26 @@ int enqueue(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, con
         RET(ensure_ws(st, need));
         ws = (unsigned char*)st->ws;
     }
-    if (o.pretransform != 2) return enqueue_once(A, lda, X, ldx, n, leaf, o, o.pretransform == 1, st, s, ws);
+    if (o.pretransform != 2) {
+        if (!graph_mode() || st->prof.on) return enqueue_once(A, lda, X, ldx, n, leaf, o, o.pretransform == 1, st, s, ws);
+        // The second call with the same arguments captures the schedule;
+        // later ones replay it (one graph launch, dependencies resolved on
+        // the device); any other call runs the launches directly.
+        std::vector<uint64_t> key = call_key(A, lda, X, ldx, n, leaf, o, ws);
+        if (st->exec == nullptr || key != st->graph_key) {
+            if (key != st->prev_key) {
+                st->prev_key = key;
+                return enqueue_once(A, lda, X, ldx, n, leaf, o, o.pretransform == 1, st, s, ws);
+            }
+            RET(capture_schedule(A, lda, X, ldx, n, leaf, o, st, ws));
+            st->graph_key = key;
+        }
+        st->last_mixed = st->graph_mixed;
+        st->last_pretransformed = st->graph_rbt;
+        SPIN_CUDA_TRY(cudaGraphLaunch(st->exec, s));
+        st->graph_launches++;
+        return SPIN_OK;
+    }
     // plain first; a zero or non-finite pivot (A11 or a Schur complement
     // singular in working precision) sends the call through the transform
     RET(enqueue_once(A, lda, X, ldx, n, leaf, o, false, st, s, ws));
@@ -803,7 +901,8 @@ int spin_autotune_leaf(int64_t n, int precision, const int* candidates, int ncan
         o.precision = precision;
         o.leaf = L;
         spin_info info;
-        rc = spin_invert_ex(A, n, X, n, n, &o, &info, stream);  // warm (workspace, modules)
+        // warm: workspace and modules, then the captured schedule
+        for (int w = 0; w < 2 && rc == SPIN_OK; w++) rc = spin_invert_ex(A, n, X, n, n, &o, &info, stream);
         if (rc != SPIN_OK) break;
         cudaEventRecord(e0, s);
         rc = spin_invert_ex(A, n, X, n, n, &o, &info, stream);
@@ -858,6 +957,15 @@ int spin_invert(const double* A, double* X, int64_t n, int64_t lda, int leaf, sp
     o.leaf = leaf;
     o.blocking = 1;
     return spin_invert_ex(A, lda, X, n, n, &o, nullptr, stream);
+}
+
+int spin_schedule_stats(spin_stream_t stream, int64_t* replays, int64_t* nodes) {
+    cudaStream_t s = (cudaStream_t)stream;
+    StreamState* st = nullptr;
+    RET(get_state(s, &st));
+    if (replays) *replays = st->graph_launches;
+    if (nodes) *nodes = st->exec ? st->graph_nodes : 0;
+    return SPIN_OK;
 }
 
 int spin_sync(spin_stream_t stream, spin_info* info) {
