@@ -27,6 +27,7 @@ namespace spin {
 namespace {
 
 constexpr int BK = 16, NT = 256;
+constexpr int kTileGroup = 1;  // row-major tile order
 
 // One TM x TM output tile per 256-thread CTA: thread (tx, ty) of a 16 x 16
 // grid owns a (TM/16) x (TM/16) register tile.
@@ -34,14 +35,15 @@ template <int TM>
 __device__ __forceinline__ void gemm_f64_tile(int64_t m, int64_t n, int64_t k, double alpha,
                                               const double* __restrict__ A, int64_t lda,
                                               const double* __restrict__ B, int64_t ldb, double beta,
-                                              const double* C, int64_t ldc, double* D, int64_t ldd) {
+                                              const double* C, int64_t ldc, double* D, int64_t ldd,
+                                              int64_t tile_m, int64_t tile_n) {
     constexpr int T = TM / 16;        // outputs per thread along each side
     constexpr int BR = NT / TM;       // B tile rows loaded per pass
     __shared__ double As[2][BK][TM + 1];
     __shared__ double Bs[2][BK][TM];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int64_t m0 = (int64_t)blockIdx.y * TM, n0 = (int64_t)blockIdx.x * TM;
+    const int64_t m0 = tile_m * TM, n0 = tile_n * TM;
 
     // load mapping: A tile (TM x BK): row = ty + 16*i, kk = tx; B tile (BK x TM): kr = tid/TM + BR*i, col = tid%TM
     const int a_kk = tx;
@@ -113,12 +115,35 @@ __device__ __forceinline__ void gemm_f64_tile(int64_t m, int64_t n, int64_t k, d
     }
 }
 
+// Output tile of this CTA.  With group > 1 consecutive CTAs walk `group`
+// tile rows down before moving one tile column right, so that the CTAs
+// resident at once cover a squarer block of the output and share more of
+// their A row panels and B column panels in L2; group <= 1 is row-major
+// order.  A bijection of the grid either way (the last group may be short).
+__device__ __forceinline__ void tile_of(int group, int64_t& tile_m, int64_t& tile_n) {
+    if (group <= 1) {
+        tile_m = blockIdx.y;
+        tile_n = blockIdx.x;
+        return;
+    }
+    const int64_t gx = gridDim.x, gy = gridDim.y;
+    const int64_t pid = (int64_t)blockIdx.y * gx + blockIdx.x;
+    const int64_t per = (int64_t)group * gx;
+    const int64_t g = pid / per, first = g * group;
+    const int64_t rows = gy - first < group ? gy - first : (int64_t)group;
+    const int64_t local = pid - g * per;
+    tile_m = first + local % rows;
+    tile_n = local / rows;
+}
+
 template <int TM>
 __global__ void __launch_bounds__(NT, 2)
 gemm_f64_kernel(int64_t m, int64_t n, int64_t k, double alpha, const double* __restrict__ A, int64_t lda,
                 const double* __restrict__ B, int64_t ldb, double beta, const double* C, int64_t ldc,
-                double* D, int64_t ldd) {
-    gemm_f64_tile<TM>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
+                double* D, int64_t ldd, int group) {
+    int64_t tile_m, tile_n;
+    tile_of(group, tile_m, tile_n);
+    gemm_f64_tile<TM>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, tile_m, tile_n);
 }
 
 // Batched form: problem blockIdx.z uses the views described by the BatchView
@@ -137,7 +162,8 @@ gemm_f64_batched_kernel(int64_t m, int64_t n, int64_t k, double alpha, BatchView
         ldc = c.ld_of(z);
         C = c.ptr(z, ldc);
     }
-    gemm_f64_tile<TM>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, const_cast<double*>(d.ptr(z, ldd)), ldd);
+    gemm_f64_tile<TM>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, const_cast<double*>(d.ptr(z, ldd)), ldd,
+                      blockIdx.y, blockIdx.x);
 }
 
 // SPIN_F64_TILE=64|32|16 forces a tile size (for measurement); read once.
@@ -149,6 +175,18 @@ int forced_tile() {
         t = (v == 64 || v == 32 || v == 16) ? v : 0;
     }
     return t;
+}
+
+// Tile rows per group of the single-product tile order (SPIN_F64_GROUP
+// overrides it, for measurement; read once).
+int tile_group() {
+    static int g = -1;
+    if (g < 0) {
+        const char* e = getenv("SPIN_F64_GROUP");
+        const int v = e ? atoi(e) : 0;
+        g = v > 0 ? v : kTileGroup;
+    }
+    return g;
 }
 
 }  // namespace
@@ -197,11 +235,11 @@ int launch_gemm_f64(int64_t m, int64_t n, int64_t k, double alpha, const double*
     dim3 grid((unsigned)((n + tm - 1) / tm), (unsigned)((m + tm - 1) / tm));
     if (grid.y > 65535u) return SPIN_ERR_INVALID_ARG;
     if (tm == 64)
-        gemm_f64_kernel<64><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
+        gemm_f64_kernel<64><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, tile_group());
     else if (tm == 32)
-        gemm_f64_kernel<32><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
+        gemm_f64_kernel<32><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, tile_group());
     else
-        gemm_f64_kernel<16><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd);
+        gemm_f64_kernel<16><<<grid, NT, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, tile_group());
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
 }
