@@ -767,8 +767,8 @@ constexpr double kModelClock = 2.07e9;
 constexpr double kModelPsm = 4.0 * kModelClock;
 constexpr double kModelPgpu = 152.0 * kModelPsm;
 constexpr double kModelLaunch = 4e-6;
-constexpr double kModelAPush = 1.55e-6, kModelBPush = 5e-9, kModelAPull = 1.8e-6, kModelBPull = 14e-9;
-constexpr double kModelG = 0.55e-9;
+constexpr double kModelAPush = 1.85e-6, kModelBPush = 0.0, kModelAPull = 3.46e-6, kModelBPull = 6.4e-9;
+constexpr double kModelG = 0.44e-9;
 
 double model_gemm(int64_t m, int64_t n, int64_t k) {
     const int64_t tm = gemm_f64_tile_size(m, n, 1);
