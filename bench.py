@@ -35,11 +35,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "2n³/t TFLOP/s vs FP64/BF16 peak at residual ≤1e-10; served req/s with p50/p99"
 
-# DRAM bytes per flop of gemm_f64_kernel: one ncu capture of a 4096^3 launch
-# of the top recursion level at n = 8192 read and wrote 3.852e9 bytes
+# DRAM bytes per flop of gemm_f64_kernel (tiles in groups of 16 tile rows):
+# one ncu capture of a 4096^3 launch read and wrote 1.028e9 bytes
 # (dram__bytes_read.sum + dram__bytes_write.sum); operand re-reads grow with
 # the flops of a launch, so per-launch traffic is scaled by flops.
-GEMM_F64_DRAM_BYTES_PER_FLOP = 3.852e9 / (2.0 * 4096 ** 3)
+GEMM_F64_DRAM_BYTES_PER_FLOP = 1.028e9 / (2.0 * 4096 ** 3)
 SEED_BASE = 0x5EED0000
 
 WORKLOADS = {

@@ -27,7 +27,11 @@ namespace spin {
 namespace {
 
 constexpr int BK = 16, NT = 256;
-constexpr int kTileGroup = 1;  // row-major tile order
+// Tile rows per group of the single-product tile order.  Measured on a
+// 4096^3 product (ncu dram__bytes_read.sum + dram__bytes_write.sum, same
+// duration every time): 3.87 GB in row-major order, 1.49 GB with groups of
+// 8 tile rows, 1.03 GB with 16, against 0.40 GB of operands and result.
+constexpr int kTileGroup = 16;
 
 // One TM x TM output tile per 256-thread CTA: thread (tx, ty) of a 16 x 16
 // grid owns a (TM/16) x (TM/16) register tile.
