@@ -34,6 +34,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "2n³/t TFLOP/s vs FP64/BF16 peak at residual ≤1e-10; served req/s with p50/p99"
+T_START = time.perf_counter()
+# The batched and serving sub-records of the default run start only before
+# this many seconds (the driver's limit for the whole run is 1800 s).
+SUBRECORD_DEADLINE_S = 1540.0
 
 # DRAM bytes per flop of gemm_f64_kernel (tiles in groups of 16 tile rows):
 # one ncu capture of a 4096^3 launch read and wrote 1.028e9 bytes
@@ -93,6 +97,10 @@ def parse():
     ap.add_argument("--probes", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="plain_fp64: skip the mixed-precision sub-record")
+    ap.add_argument("--no-batched", action="store_true", help="plain_fp64: skip the batched sub-record")
+    ap.add_argument("--no-serve", action="store_true", help="plain_fp64: skip the serving sub-record")
+    ap.add_argument("--serve-sub-seconds", type=float, default=15.0,
+                    help="plain_fp64: arrival window of the serving sub-record (s)")
     ap.add_argument("--mixed-steps", type=int, default=3, help="plain_fp64: timed steps of the mixed sub-record "
                     "(at most --steps)")
     ap.add_argument("--mixed-warmup", type=int, default=2, help="plain_fp64: warm-up steps of the mixed sub-record "
@@ -630,9 +638,25 @@ def run_ours(args, w: dict, n: int, leaf: int):
     ms, value = replica_rate(t["ms_local"], flops, world, device)
     acc = work.accuracy(args.probes)
 
-    mixed = None
+    mixed = batched = served = None
     if args.workload == "plain_fp64" and not args.no_mixed:
         mixed = mixed_subrecord(args, spin, work, n, ms, device, stream, barrier, local, world, peak_fp64)
+    # the batching and serving forms, while the run stays well inside its
+    # time limit (the plain steps take most of it)
+    if args.workload == "plain_fp64" and not args.no_batched and world == 1:
+        if time.perf_counter() - T_START < SUBRECORD_DEADLINE_S:
+            batched = batched_subrecord(args, spin, device, stream, barrier, local, world, peak_fp64)
+        else:
+            batched = {"skipped": f"run time above {SUBRECORD_DEADLINE_S:.0f} s"}
+    if args.workload == "plain_fp64" and not args.no_serve and world == 1:
+        if time.perf_counter() - T_START < SUBRECORD_DEADLINE_S:
+            sargs = argparse.Namespace(**vars(args))
+            sargs.serve_seconds = args.serve_sub_seconds
+            served = run_serve(sargs, dict(WORKLOADS["serve"]), sub=True)
+            served = {k: v for k, v in served.items()
+                      if k not in ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data")}
+        else:
+            served = {"skipped": f"run time above {SUBRECORD_DEADLINE_S:.0f} s"}
 
     if rank != 0:
         if world > 1:
@@ -691,7 +715,8 @@ def run_ours(args, w: dict, n: int, leaf: int):
         "cold": {"first_call_ms": e2e_times[0] * 1e3 if e2e_times else None,
                  "how": "the first end-to-end call of the process: workspace allocation, module load and "
                         "copies included"},
-        "gpu_launches": work.launches(recs, args.steps) + (mixed["gpu_launches"] if mixed else 0),
+        "gpu_launches": work.launches(recs, args.steps) + (mixed["gpu_launches"] if mixed else 0)
+        + sum(batched[k]["gpu_launches"] for k in ("batched_fp64", "batched_mixed") if batched and k in batched),
         "roofline": roof,
         "status": info["status"],
         "refine_iters": info.get("refine_iters"),
@@ -707,6 +732,10 @@ def run_ours(args, w: dict, n: int, leaf: int):
     line.update(acc)
     if mixed is not None:
         line["mixed"] = mixed
+    if batched is not None:
+        line["batched"] = batched
+    if served is not None:
+        line["serve"] = served
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if args.profile_json:
@@ -775,7 +804,47 @@ def mixed_subrecord(args, spin, plain_work, n: int, plain_ms: float, device, str
     }
 
 
-def run_serve(args, w: dict):
+def batched_subrecord(args, spin, device, stream, barrier, local: int, world: int, peak_fp64: float) -> dict:
+    """The batching workload (4096 matrices of orders 32..1024) on the same
+    GPU in the same process, FP64 and mixed, each with its leaves autotuned
+    per order bucket before the timed steps; the mixed batch is compared
+    with the FP64 batch."""
+    import gc
+
+    import torch
+
+    out = {}
+    steps, warmup = max(1, min(args.steps, 3)), max(3, min(args.warmup, 3))
+    for name in ("batched_fp64", "batched_mixed"):
+        wb = dict(WORKLOADS[name])
+        work = BatchWork(spin, wb, wb["n"], 0, device, BATCH_COUNT)
+        t = time_work(spin, work, steps, warmup, stream, barrier, local)
+        ms, value = replica_rate(t["ms_local"], work.flops, world, device)
+        fin = t["info"]
+        acc = work.accuracy(args.probes)
+        e2e_ok = t["e2e_times"][1:] if len(t["e2e_times"]) > 1 else t["e2e_times"]
+        e2e_t = statistics.median(e2e_ok) if e2e_ok else None
+        out[name] = {
+            "desc": wb["desc"], "precision": wb["precision"], "matrices": len(work.orders),
+            "orders": {"min": min(work.orders), "max": max(work.orders), "distinct": len(set(work.orders))},
+            "leaf_autotune": work.tuned, "steps": steps, "warmup": warmup,
+            "value": value, "unit": "TFLOP/s", "ms_per_step": ms, "frac_of_fp64_peak": value / world / peak_fp64,
+            "failed": fin["failed"], "refine_iters": fin["refine_iters"], "worst_rel_residual_lib": fin["rel_residual"],
+            **acc,
+            "clocks": t["clocks"],
+            "e2e": {"value": work.flops / e2e_t / 1e12 if e2e_t else None, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": work.h2d, "d2h_bytes_per_step": work.d2h,
+                    "how": "pinned host buffers, copies inside the timed call, warm-up steps 2..W, host wall clock"},
+            "gpu_launches": work.launches(t["recs"], steps),
+        }
+        del work, t
+        gc.collect()
+        torch.cuda.empty_cache()
+    out["mixed_speedup_vs_fp64_batch"] = out["batched_fp64"]["ms_per_step"] / out["batched_mixed"]["ms_per_step"]
+    return out
+
+
+def run_serve(args, w: dict, sub: bool = False):
     """Serving benchmark: replay a Poisson arrival trace against spin_serve_*.
 
     A producer thread generates every request's matrix on the device ahead
@@ -899,7 +968,7 @@ def run_serve(args, w: dict):
     # client waits for the producer: results that nobody polls hold the
     # server's budget, and the producer may be waiting for that memory.
     # A run that makes no progress for stall_s aborts with its counters.
-    stall_s = 300.0
+    stall_s = 60.0 if sub else 300.0
     progress = {"t": time.perf_counter(), "done": 0, "last_print": time.perf_counter()}
 
     def check_progress(where):
@@ -1015,6 +1084,8 @@ def run_serve(args, w: dict):
                 "how": "requests submitted from device memory; results left on the device"},
         "gpu_launches": None,
     }
+    if sub:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
