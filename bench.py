@@ -39,11 +39,6 @@ T_START = time.perf_counter()
 # this many seconds (the driver's limit for the whole run is 1800 s).
 SUBRECORD_DEADLINE_S = 1540.0
 
-# DRAM bytes per flop of gemm_f64_kernel (tiles in groups of 16 tile rows):
-# one ncu capture of a 4096^3 launch read and wrote 1.028e9 bytes
-# (dram__bytes_read.sum + dram__bytes_write.sum); operand re-reads grow with
-# the flops of a launch, so per-launch traffic is scaled by flops.
-GEMM_F64_DRAM_BYTES_PER_FLOP = 1.028e9 / (2.0 * 4096 ** 3)
 SEED_BASE = 0x5EED0000
 
 WORKLOADS = {
@@ -587,10 +582,12 @@ def top_roofline(by_kind: dict, ms_step: float, steps: int, peaks: dict, peak_fp
                 "frac": achieved / peak, "traffic": None, "peak_source": src,
                 "flops_counted": "BF16 tensor-core products actually issued (slice pairs x 2mnk)",
                 "launches": d["launches"], "share_of_step": d["ms"] / (ms_step * steps)}
-    traffic = GEMM_F64_DRAM_BYTES_PER_FLOP * d["flops"] / d["launches"] if top == "gemm_f64" else None
     return {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-            "frac": achieved / peak_fp64, "traffic": traffic,
-            "traffic_note": "bytes per launch: ncu dram read+write of a 4096^3 launch, scaled by flops",
+            "frac": achieved / peak_fp64, "traffic": None,
+            "traffic_note": ("gemm_f64: ncu dram read+write was 0.96 GB for a 4096^3 launch and 12.7 GB for "
+                             "8192^3 (algorithmic 0.40 and 1.61 GB); it does not grow in proportion to the "
+                             "flops, and this workload's launches were not captured" if top == "gemm_f64"
+                             else "not captured"),
             "peak_source": "FP64 FMA rate measured live by spin_probe_fp64_peak on this GPU",
             "launches": d["launches"], "share_of_step": d["ms"] / (ms_step * steps)}
 
