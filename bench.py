@@ -636,13 +636,17 @@ def run_ours(args, w: dict, n: int, leaf: int):
     acc = work.accuracy(args.probes)
 
     mixed = batched = served = None
+    # seconds since the start of the process at the end of each phase
+    timeline = {"plain_s": time.perf_counter() - T_START}
     if args.workload == "plain_fp64" and not args.no_mixed:
         mixed = mixed_subrecord(args, spin, work, n, ms, device, stream, barrier, local, world, peak_fp64)
+        timeline["mixed_s"] = time.perf_counter() - T_START
     # the batching and serving forms, while the run stays well inside its
     # time limit (the plain steps take most of it)
     if args.workload == "plain_fp64" and not args.no_batched and world == 1:
         if time.perf_counter() - T_START < SUBRECORD_DEADLINE_S:
             batched = batched_subrecord(args, spin, device, stream, barrier, local, world, peak_fp64)
+            timeline["batched_s"] = time.perf_counter() - T_START
         else:
             batched = {"skipped": f"run time above {SUBRECORD_DEADLINE_S:.0f} s"}
     if args.workload == "plain_fp64" and not args.no_serve and world == 1:
@@ -652,6 +656,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
             served = run_serve(sargs, dict(WORKLOADS["serve"]), sub=True)
             served = {k: v for k, v in served.items()
                       if k not in ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data")}
+            timeline["serve_s"] = time.perf_counter() - T_START
         else:
             served = {"skipped": f"run time above {SUBRECORD_DEADLINE_S:.0f} s"}
 
@@ -735,6 +740,8 @@ def run_ours(args, w: dict, n: int, leaf: int):
         line["serve"] = served
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
+    timeline["end_s"] = time.perf_counter() - T_START
+    line["timeline"] = timeline
     if args.profile_json:
         with open(args.profile_json, "w") as f:
             json.dump(recs, f)
