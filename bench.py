@@ -69,6 +69,7 @@ WORKLOADS = {
 
 BATCH_COUNT = 4096
 BATCH_LEAF_CANDIDATES = (32, 64, 128, 256)
+PERSIST_MAX_LEAF = 64  # largest leaf of the persistent batch kernel
 
 
 def measured_peaks() -> dict:
@@ -100,6 +101,8 @@ def parse():
                     "(at most --steps)")
     ap.add_argument("--mixed-warmup", type=int, default=2, help="plain_fp64: warm-up steps of the mixed sub-record "
                     "(at most --warmup, at least 1)")
+    ap.add_argument("--batch-schedule", default="default", choices=["default", "lockstep", "persistent"],
+                    help="batched workloads, plain form: one persistent launch (default) or lockstep launches")
     ap.add_argument("--profile-json", default="", help="write per-launch records here")
     ap.add_argument("--leaf-times", default="", help="comma-separated leaf orders: time one leaf inversion "
                     "(spin_leaf_inverse on its default cluster) per order and print the per-pivot-step times")
@@ -424,13 +427,18 @@ class SingleWork:
 class BatchWork:
     """Thousands of matrices of uneven order: one spin_invert_batched call."""
 
-    def __init__(self, spin, w, n, leaf, device, count):
+    def __init__(self, spin, w, n, leaf, device, count, schedule="default"):
         import torch
 
         from paper_1801_04723_gb300 import inputs
 
         self.spin, self.leaf = spin, leaf
         self.precision = w["precision"]
+        # the plain batch runs as one persistent launch unless lockstep is asked for
+        self.schedule = schedule
+        persistent = self.precision == "fp64" and schedule != "lockstep"
+        cands = tuple(c for c in BATCH_LEAF_CANDIDATES if c <= PERSIST_MAX_LEAF) if persistent \
+            else BATCH_LEAF_CANDIDATES
         self.orders = [int(v) for v in inputs.batch_orders(count, seed=w["seed"], lo=32, hi=min(1024, n))]
         self.As = [inputs.sdd_device(m, w["seed"] + 1000 * 3 + j, device) for j, m in enumerate(self.orders)]
         self.Xs = [torch.empty_like(a) for a in self.As]
@@ -444,19 +452,24 @@ class BatchWork:
             # per order bucket, the fastest leaf on a bucket of the same size
             # (outside the timed region); leaf 0 then uses the records
             t0 = time.perf_counter()
-            rec = spin.autotune_batched_leaf(self.orders, self.precision, candidates=BATCH_LEAF_CANDIDATES)
+            rec = spin.autotune_batched_leaf(self.orders, self.precision, candidates=cands)
             chosen = {}
             for m in sorted(set(self.orders)):
                 chosen.setdefault(str(rec[m][0]), []).append(m)
-            self.tuned = {"candidates": list(BATCH_LEAF_CANDIDATES), "leaf_orders": chosen,
+            self.tuned = {"candidates": list(cands), "leaf_orders": chosen,
                           "tuning_s": time.perf_counter() - t0}
 
     def step(self):
         _, self.info = self.spin.invert_batched(self.As, leaf=self.leaf, outs=self.Xs, blocking=False,
-                                                precision=self.precision)
+                                                precision=self.precision, schedule=self.schedule)
 
     def launches(self, recs, steps):
         return self.spin.batched_stats()["kernels"] * steps
+
+    def schedule_desc(self):
+        if self.precision == "fp64" and self.schedule != "lockstep":
+            return "persistent: one launch over a device-side task list (leaves <= 64 on one CTA, product tiles)"
+        return "lockstep: per order bucket one launch per product and per leaf, buckets on 8 streams"
 
     def finish(self):
         import torch
@@ -474,7 +487,8 @@ class BatchWork:
 
         for a, ah in zip(self.As, self.Ahs):
             a.copy_(ah, non_blocking=True)
-        self.spin.invert_batched(self.As, leaf=self.leaf, outs=self.Xs, blocking=False, precision=self.precision)
+        self.spin.invert_batched(self.As, leaf=self.leaf, outs=self.Xs, blocking=False, precision=self.precision,
+                                 schedule=self.schedule)
         for x, xh in zip(self.Xs, self.Xhs):
             xh.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
@@ -615,7 +629,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
         torch.cuda.synchronize()
 
     if w["family"] == "batch_sdd":
-        work = BatchWork(spin, w, n, leaf, device, BATCH_COUNT)
+        work = BatchWork(spin, w, n, leaf, device, BATCH_COUNT, args.batch_schedule)
     else:
         work = SingleWork(spin, w, n, leaf, device, args.pretransform, args.fp64_levels)
     stream = torch.cuda.current_stream()
@@ -674,7 +688,9 @@ def run_ours(args, w: dict, n: int, leaf: int):
     if isinstance(work, BatchWork) and work.precision == "fp64":
         # the batch replays one CUDA graph: no per-launch events; the whole
         # graph is FP64-pipe bound (batched products and leaves)
-        roof = {"kernel": "batched graph (gemm_f64_batched_kernel + leaf_gj_batched_kernel)", "bound": "alu",
+        roof = {"kernel": ("persistent_batch_kernel (product tiles and leaves, one launch)"
+                           if work.schedule != "lockstep" else
+                           "batched graph (gemm_f64_batched_kernel + leaf_gj_cta_kernel)"), "bound": "alu",
                 "achieved": value / world, "peak": peak_fp64, "unit": "TFLOP/s", "frac": value / world / peak_fp64,
                 "traffic": None, "peak_source": "FP64 FMA rate measured live by spin_probe_fp64_peak on this GPU"}
     elif isinstance(work, BatchWork):
@@ -699,6 +715,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
     if batch:
         config["l2"] = f"inputs larger than L2 ({work.h2d / 1e9:.1f} GB of matrices)"
         config["orders"] = {"min": min(work.orders), "max": max(work.orders), "distinct": len(set(work.orders))}
+        config["schedule"] = work.schedule_desc()
         if work.tuned is not None:
             config["leaf"] = "autotuned per order"
             config["leaf_autotune"] = work.tuned
@@ -821,7 +838,7 @@ def batched_subrecord(args, spin, device, stream, barrier, local: int, world: in
     steps, warmup = max(1, min(args.steps, 3)), max(3, min(args.warmup, 3))
     for name in ("batched_fp64", "batched_mixed"):
         wb = dict(WORKLOADS[name])
-        work = BatchWork(spin, wb, wb["n"], 0, device, BATCH_COUNT)
+        work = BatchWork(spin, wb, wb["n"], 0, device, BATCH_COUNT, args.batch_schedule)
         t = time_work(spin, work, steps, warmup, stream, barrier, local)
         ms, value = replica_rate(t["ms_local"], work.flops, world, device)
         fin = t["info"]
@@ -831,7 +848,7 @@ def batched_subrecord(args, spin, device, stream, barrier, local: int, world: in
         out[name] = {
             "desc": wb["desc"], "precision": wb["precision"], "matrices": len(work.orders),
             "orders": {"min": min(work.orders), "max": max(work.orders), "distinct": len(set(work.orders))},
-            "leaf_autotune": work.tuned, "steps": steps, "warmup": warmup,
+            "leaf_autotune": work.tuned, "schedule": work.schedule_desc(), "steps": steps, "warmup": warmup,
             "value": value, "unit": "TFLOP/s", "ms_per_step": ms, "frac_of_fp64_peak": value / world / peak_fp64,
             "failed": fin["failed"], "refine_iters": fin["refine_iters"], "worst_rel_residual_lib": fin["rel_residual"],
             **acc,
@@ -1200,7 +1217,7 @@ def run_leaf_batch(args):
     As = [torch.from_numpy(inputs.sdd(L, seed=inputs.SEED_BASE + 9000 + i)).to("cuda:0") for i in range(count)]
     Xs = [torch.empty_like(a) for a in As]
     for _ in range(2):
-        spin.invert_batched(As, outs=Xs)
+        spin.invert_batched(As, outs=Xs, schedule="lockstep")
     torch.cuda.synchronize()
     best = float("inf")
     with ClockSampler(0) as clk:
@@ -1211,7 +1228,7 @@ def run_leaf_batch(args):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(5):
-                _, info = spin.invert_batched(As, outs=Xs, blocking=False)
+                _, info = spin.invert_batched(As, outs=Xs, blocking=False, schedule="lockstep")
             e1.record()
             e1.synchronize()
             best = min(best, e0.elapsed_time(e1) / 5)

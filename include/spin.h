@@ -70,6 +70,13 @@ typedef enum {
                               residual                                                    */
 } spin_precision;
 
+/* How spin_invert_batched runs a plain batch (spin_opts.schedule). */
+typedef enum {
+    SPIN_SCHEDULE_DEFAULT = 0,
+    SPIN_SCHEDULE_LOCKSTEP = 1,
+    SPIN_SCHEDULE_PERSISTENT = 2
+} spin_batch_schedule;
+
 /* Options of spin_invert_ex.  Zero-initialise and set what you need;
  * spin_opts_default() returns the defaults. */
 typedef struct spin_opts {
@@ -98,7 +105,15 @@ typedef struct spin_opts {
                                     to a multiple of 4); the mixed modes then refine X against A;
                                   2 the plain recursion first, and on a zero or non-finite pivot
                                     the transform (the call then waits for the first attempt)  */
-    int32_t reserved0;
+    int32_t schedule;          /* spin_invert_batched, plain form (spin_batch_schedule):
+                                  0 (default) the persistent kernel -- one launch that walks a
+                                  device-side task list -- unless leaf > 64; 1 lockstep
+                                  launches per order bucket on a pool of streams; 2 the
+                                  persistent kernel (leaf > 64 refused).  The persistent
+                                  kernel inverts leaves of order <= 64 on one CTA each: a
+                                  larger leaf chosen by the library (n for n <= 128, or an
+                                  autotuned one) becomes 64.  Ignored by the other calls and
+                                  by the mixed form                                          */
     uint64_t rbt_seed;         /* seed of the butterflies' random diagonals (splitmix64)      */
 } spin_opts;
 
@@ -213,6 +228,20 @@ int spin_rbt_diagonals(uint64_t seed, int64_t n, int depth, double* out_dev, spi
  */
 int spin_autotune_batched_leaf(const int64_t* orders, int count, int precision, const int* candidates, int ncand,
                                int* leaf_out, double* ms_out, spin_stream_t stream);
+
+/* The persistent schedule a plain spin_invert_batched would run for these
+ * orders (host only, no device work; count entries, leaf as opts.leaf,
+ * 0..64): order buckets become stage lists (Algorithm 1's leaf inversions
+ * and its six level products per node), merged into one task order.
+ * Writes the stages, the tasks (matrix x output tile), the leaf inversions
+ * and the products over all matrices, and their flops (2 L^3 per leaf,
+ * 2 m n k per product; the method's total is 2 n^3 per matrix, Sec. 4).
+ * Any output pointer may be NULL.  SPIN_ERR_INVALID_ARG for bad orders or
+ * leaf; SPIN_ERR_CUDA if the task order breaks one of its invariants (each
+ * bucket's stages in recursion order, every stage's dependency count equal
+ * to the tasks of the bucket's earlier stages). */
+int spin_batch_schedule_info(const int64_t* n, int count, int leaf, int64_t* stages, int64_t* tasks,
+                             int64_t* leaves, int64_t* products, double* flops);
 
 /* Shape of the graph the latest spin_invert_batched on `stream` replays:
  * kernel launches per call and order buckets.  SPIN_ERR_INVALID_ARG if none. */

@@ -38,7 +38,7 @@ class Opts(ctypes.Structure):
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
         ("pretransform", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("schedule", ctypes.c_int32),
         ("rbt_seed", ctypes.c_uint64),
     ]
 
@@ -242,8 +242,11 @@ def _check_matrix(t, name):
         raise ValueError(f"{name} must be row-major (unit column stride)")
 
 
+SCHEDULES = {"default": 0, "lockstep": 1, "persistent": 2}
+
+
 def make_opts(precision="fp64", leaf=0, tol=1e-10, max_refine=6, fp64_levels=2, blocking=True,
-              workspace=None, residual_slices=0, pretransform=0, rbt_seed=0) -> Opts:
+              workspace=None, residual_slices=0, pretransform=0, rbt_seed=0, schedule="default") -> Opts:
     o = lib().spin_opts_default()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.leaf = int(leaf)
@@ -254,6 +257,7 @@ def make_opts(precision="fp64", leaf=0, tol=1e-10, max_refine=6, fp64_levels=2, 
     o.residual_slices = int(residual_slices)
     o.pretransform = int(pretransform)
     o.rbt_seed = int(rbt_seed) & 0xFFFFFFFFFFFFFFFF
+    o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     if workspace is not None:
         o.workspace = ctypes.c_void_p(workspace.data_ptr())
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -501,12 +505,14 @@ def batched_stats(stream=None) -> dict:
 
 
 def invert_batched(As, *, leaf: int = 0, outs=None, stream=None, blocking: bool = True, precision="fp64",
-                   tol: float = 1e-10, max_refine: int = 6, fp64_levels: int = 2):
+                   tol: float = 1e-10, max_refine: int = 6, fp64_levels: int = 2, schedule="default"):
     """X_i = A_i^-1 for a list of square float64 CUDA tensors of any orders
     (spin_invert_batched).  Returns (list of X, int32 CUDA tensor of statuses).
     precision "bf16x3" runs the mixed form (its refinement is part of the
-    captured graph).  With ``blocking=False`` the call returns once the work
-    is enqueued on the stream."""
+    captured graph).  schedule (plain form): "default" / "persistent" (one
+    persistent launch over a device-side task list) or "lockstep" (launches
+    per order bucket on a pool of streams).  With ``blocking=False`` the call
+    returns once the work is enqueued on the stream."""
     import torch
 
     count = len(As)
@@ -522,7 +528,8 @@ def invert_batched(As, *, leaf: int = 0, outs=None, stream=None, blocking: bool 
     lda = (ctypes.c_int64 * count)(*[a.stride(0) for a in As])
     ns = (ctypes.c_int64 * count)(*[a.shape[0] for a in As])
     info = torch.zeros(count, dtype=torch.int32, device=As[0].device)
-    o = make_opts(precision, leaf, blocking=blocking, tol=tol, max_refine=max_refine, fp64_levels=fp64_levels)
+    o = make_opts(precision, leaf, blocking=blocking, tol=tol, max_refine=max_refine, fp64_levels=fp64_levels,
+                  schedule=schedule)
     rc = lib().spin_invert_batched(pa, lda, px, ns, count, ctypes.byref(o), ctypes.c_void_p(info.data_ptr()),
                                    _stream(stream))
     if rc != SPIN_OK:

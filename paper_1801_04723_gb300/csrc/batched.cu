@@ -31,6 +31,7 @@
 
 #include "common.cuh"
 #include "mixed.h"
+#include "persistent.h"
 #include "tc_gemm.h"
 
 namespace spin {
@@ -85,6 +86,15 @@ struct BatchPlan {
     int* iters = nullptr;          // device: [count] refinement steps taken
     int* err = nullptr;            // device: SPIN_ERR_TIMEOUT from a bounded wait
     const int* nvalid = nullptr;   // device, optional: [count] order of the matrix inside its identity padding
+    // plain form on the persistent kernel (persistent.cu): stage list, task
+    // starts, control block (done counters, task counter, error flag)
+    bool persistent = false;
+    PStage* pstages = nullptr;
+    int64_t* pstart = nullptr;
+    unsigned char* pctl = nullptr;
+    size_t pctl_bytes = 0;
+    int nstages = 0;
+    int64_t ptasks = 0;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;  // private stream the launch sequence is captured on
     cudaStream_t streams[kStreams] = {};
@@ -116,6 +126,16 @@ void free_plan(BatchPlan& p) {
     cudaFree(p.user_index);
     cudaFree(p.records);
     cudaFree(p.ws);
+    cudaFree(p.pstages);
+    cudaFree(p.pstart);
+    cudaFree(p.pctl);
+    p.pstages = nullptr;
+    p.pstart = nullptr;
+    p.pctl = nullptr;
+    p.pctl_bytes = 0;
+    p.nstages = 0;
+    p.ptasks = 0;
+    p.persistent = false;
     p.exec = nullptr;
     p.a_base = nullptr;
     p.a_ld = nullptr;
@@ -180,6 +200,153 @@ int binv(BRun& r, BatchView A, BatchView X, const double* const* wbase, int64_t 
     BRET(launch_gemm_f64_batched(n2, n1, n2, -1.0, X22, T2, 0.0, none, X21, r.count, r.s));
     BRET(launch_gemm_f64_batched(n1, n1, n2, -1.0, X12, T2, 1.0, X11, X11, r.count, r.s));
     return SPIN_OK;
+}
+
+// ---- the plain form as one persistent launch ----
+
+PView pview(int src, int64_t ld, int64_t r0, int64_t c0) {
+    PView v;
+    v.src = src;
+    v.pad = 0;
+    v.ld = ld;
+    v.r0 = r0;
+    v.c0 = c0;
+    return v;
+}
+
+PView psub(PView v, int64_t dr, int64_t dc) {
+    v.r0 += dr;
+    v.c0 += dc;
+    return v;
+}
+
+// Product tile of the persistent schedule: every bucket's tasks run side by
+// side, so a product need not fill the GPU by itself.  The tile with the
+// least CTA time: padded FMAs (one per clock for one of the two CTAs of an
+// SM) plus a fixed cost per task (taking the task, its dependency check and
+// its completion, about 3000 clocks).  The tile never changes a result bit.
+int persist_tile(int64_t m, int64_t n, int64_t k) {
+    const int forced = forced_f64_tile();
+    if (forced) return forced;
+    constexpr double kTaskClocks = 3000.0;
+    int best = 64;
+    double best_cost = 0.0;
+    for (int tm : {64, 32, 16}) {
+        const double tiles = (double)((m + tm - 1) / tm) * (double)((n + tm - 1) / tm);
+        const double cost = tiles * ((double)tm * tm * (double)k + kTaskClocks);
+        if (tm == 64 || cost < best_cost) {
+            best = tm;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
+// Stages of one bucket's recursion, in binv's order (the lockstep launches
+// become stages; their tile choice and leaf numbering are binv's).
+struct StageList {
+    std::vector<PStage> st;
+    int first = 0, count = 0;
+    int64_t leaf = 0;
+    int leaf_counter = 0;
+    int32_t need = 0;
+
+    PStage base(int kind) const {
+        PStage x;
+        memset(&x, 0, sizeof x);
+        x.kind = kind;
+        x.first = first;
+        x.count = count;
+        x.need = need;
+        return x;
+    }
+    void leaf_inv(int64_t L, PView a, PView d) {
+        PStage x = base(PSTAGE_LEAF);
+        x.tiles = 1;
+        x.tiles_n = 1;
+        x.leaf_index = leaf_counter++;
+        x.m = x.n = x.k = L;
+        x.a = a;
+        x.d = d;
+        st.push_back(x);
+        need += 1;
+    }
+    void product(int64_t m, int64_t n, int64_t k, double alpha, PView a, PView b, double beta, PView c, PView d) {
+        if (m <= 0 || n <= 0) return;
+        PStage x = base(PSTAGE_PRODUCT);
+        x.tm = persist_tile(m, n, k);
+        x.tiles_n = (int32_t)((n + x.tm - 1) / x.tm);
+        x.tiles = (int32_t)((m + x.tm - 1) / x.tm) * x.tiles_n;
+        x.m = m;
+        x.n = n;
+        x.k = k;
+        x.alpha = alpha;
+        x.beta = beta;
+        x.a = a;
+        x.b = b;
+        x.c = c;
+        x.d = d;
+        st.push_back(x);
+        need += x.tiles;
+    }
+};
+
+// binv's recursion with the launches recorded as stages.
+void pinv(StageList& L, PView A, PView X, int64_t woff, int64_t n) {
+    if (n <= L.leaf) {
+        L.leaf_inv(n, A, X);
+        return;
+    }
+    const int64_t n1 = split_order(n), n2 = n - n1;
+    PView A12 = psub(A, 0, n1), A21 = psub(A, n1, 0), A22 = psub(A, n1, n1);
+    PView X11 = X, X12 = psub(X, 0, n1), X21 = psub(X, n1, 0), X22 = psub(X, n1, n1);
+    PView T = pview(2, n2, 0, woff);             // n1 x n2
+    PView S = pview(2, n2, 0, woff + n1 * n2);   // n2 x n2
+    PView T2 = pview(2, n1, 0, woff);            // n2 x n1 (II)
+    const int64_t wsub = woff + n1 * n2 + n2 * n2;
+    PView none = pview(2, 1, 0, 0);
+    pinv(L, A, X11, woff, n1);
+    L.product(n1, n2, n1, 1.0, X11, A12, 0.0, none, T);
+    L.product(n2, n2, n1, -1.0, A21, T, 1.0, A22, S);
+    pinv(L, S, X22, wsub, n2);
+    L.product(n1, n2, n2, -1.0, T, X22, 0.0, none, X12);
+    L.product(n2, n1, n1, 1.0, A21, X11, 0.0, none, T2);
+    L.product(n2, n1, n2, -1.0, X22, T2, 0.0, none, X21);
+    L.product(n1, n1, n2, -1.0, X12, T2, 1.0, X11, X11);
+}
+
+// Task order of the whole batch: stage position first, larger orders first
+// within a position (each bucket's stages stay in their order, so every
+// task only depends on tasks before it).  start gets nstages + 1 entries.
+// Starting the buckets 1 to 3 positions apart, so that a position mixes
+// leaves and products, measured the same on the batching workload (709.8 to
+// 710.2 ms against 710.2): the leaves' pivot steps already share the SMs
+// with product tiles as the positions drift apart.
+void order_stages(const std::vector<Bucket>& buckets, std::vector<PStage>& out, std::vector<int64_t>& start) {
+    std::vector<StageList> lists(buckets.size());
+    size_t longest = 0;
+    for (size_t i = 0; i < buckets.size(); i++) {
+        const Bucket& b = buckets[i];
+        StageList& L = lists[i];
+        L.first = b.first;
+        L.count = b.count;
+        L.leaf = b.leaf;
+        pinv(L, pview(0, 0, 0, 0), pview(1, b.n, 0, 0), 0, b.n);
+        longest = std::max(longest, L.st.size());
+    }
+    std::vector<size_t> by_order(buckets.size());
+    std::iota(by_order.begin(), by_order.end(), 0);
+    std::stable_sort(by_order.begin(), by_order.end(),
+                     [&](size_t a, size_t b) { return buckets[a].n > buckets[b].n; });
+    out.clear();
+    start.assign(1, 0);
+    for (size_t pos = 0; pos < longest; pos++)
+        for (size_t i : by_order)
+            if (pos < lists[i].st.size()) {
+                const PStage& x = lists[i].st[pos];
+                out.push_back(x);
+                start.push_back(start.back() + (int64_t)x.count * x.tiles);
+            }
 }
 
 // ---- mixed precision ----
@@ -414,11 +581,82 @@ int64_t batched_leaf(int64_t n, int leaf_opt, int precision) {
     return std::min<int64_t>(L, n);
 }
 
+// Plain batches run on the persistent kernel unless the caller asks for the
+// lockstep launches (opts.schedule 1) or passes a leaf above its limit.
+bool use_persistent(const spin_opts& o) {
+    if (o.precision != SPIN_FP64) return false;
+    if (o.schedule == SPIN_SCHEDULE_LOCKSTEP) return false;
+    return o.leaf <= kPersistMaxLeaf;
+}
+
+// Bound of one dependency wait of the persistent kernel: a whole batch of
+// thousands of matrices takes under a second.
+constexpr uint64_t kPersistWaitNs = 5000000000ull;
+
+// The plain batch as one persistent launch: the stage list goes up once,
+// and the captured graph is two memsets (records; done counters, task
+// counter and error flag) and the kernel.
+int capture_persistent(BatchPlan& p) {
+    std::vector<PStage> stages;
+    std::vector<int64_t> start;
+    order_stages(p.buckets, stages, start);
+    p.nstages = (int)stages.size();
+    p.ptasks = start.back();
+    int64_t max_leaf = 1;
+    for (const Bucket& b : p.buckets) max_leaf = std::max(max_leaf, std::min(b.leaf, b.n));
+    const size_t smem = persistent_smem_bytes(max_leaf);
+    int grid = 0;
+    BRET(persistent_grid(smem, p.ptasks, &grid));
+    const size_t done_bytes = align256((size_t)p.count * sizeof(unsigned));
+    p.pctl_bytes = done_bytes + 256;
+    SPIN_CUDA_TRY(cudaMalloc(&p.pstages, std::max<size_t>(stages.size(), 1) * sizeof(PStage)));
+    SPIN_CUDA_TRY(cudaMalloc(&p.pstart, start.size() * sizeof(int64_t)));
+    SPIN_CUDA_TRY(cudaMalloc(&p.pctl, p.pctl_bytes));
+    SPIN_CUDA_TRY(cudaMemcpy(p.pstages, stages.data(), stages.size() * sizeof(PStage), cudaMemcpyHostToDevice));
+    SPIN_CUDA_TRY(cudaMemcpy(p.pstart, start.data(), start.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    PersistentArgs a;
+    a.stages = p.pstages;
+    a.start = p.pstart;
+    a.nstages = p.nstages;
+    a.a_base = p.a_base;
+    a.a_ld = p.a_ld;
+    a.x_base = p.x_base;
+    a.w_base = p.w_base;
+    a.records = p.records;
+    a.done = (unsigned*)p.pctl;
+    a.next = (unsigned long long*)(p.pctl + done_bytes);
+    a.err = (int*)(p.pctl + done_bytes + 8);
+    a.limit_ns = kPersistWaitNs;
+    cudaStream_t s = p.cap;
+    cudaGraph_t graph = nullptr;
+    SPIN_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = SPIN_OK;
+    cudaError_t e = cudaMemsetAsync(p.records, 0, (size_t)p.count * INFO_WORDS * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.pctl, 0, p.pctl_bytes, s);
+    if (e != cudaSuccess) {
+        record_cuda_error(e, "persistent batch memsets", __FILE__, __LINE__);
+        rc = SPIN_ERR_CUDA;
+    }
+    if (rc == SPIN_OK) rc = launch_persistent_batch(a, smem, grid, s);
+    cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    if (rc != SPIN_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    SPIN_CUDA_TRY(ec);
+    cudaError_t ei = cudaGraphInstantiate(&p.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    SPIN_CUDA_TRY(ei);
+    p.kernels = p.graph_kernels = 1;
+    return SPIN_OK;
+}
+
 int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
                int count, const spin_opts& o, cudaStream_t s) {
     free_plan(p);
     const int leaf_opt = o.leaf;
     const bool mixed = o.precision != SPIN_FP64;
+    p.persistent = use_persistent(o);
     p.count = count;
     p.kernels = 0;
     p.precision = o.precision;
@@ -436,6 +674,7 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
         Bucket b;
         b.n = n[order[i]];
         b.leaf = batched_leaf(b.n, leaf_opt, o.precision);
+        if (p.persistent) b.leaf = std::min(b.leaf, kPersistMaxLeaf);
         b.count = j - i;
         b.first = i;
         b.ws_elems = std::max<size_t>(fp64_workspace_elems(b.n, b.leaf), 1);
@@ -497,6 +736,8 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
     }
     if (!p.fork) SPIN_CUDA_TRY(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming));
     if (!p.cap) SPIN_CUDA_TRY(cudaStreamCreateWithFlags(&p.cap, cudaStreamNonBlocking));
+
+    if (p.persistent) return capture_persistent(p);
 
     // Capture on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured); the graph is launched on the
@@ -577,6 +818,7 @@ std::vector<uint64_t> make_key(const double* const* A, const int64_t* lda, doubl
     k.push_back((uint64_t)(int64_t)o.max_refine);
     k.push_back((uint64_t)(int64_t)o.fp64_levels);
     k.push_back((uint64_t)(int64_t)o.residual_slices);
+    k.push_back((uint64_t)(int64_t)o.schedule);
     {
         std::lock_guard<std::mutex> lk(g_bleaf_mu);
         k.push_back(g_bleaf_gen);  // a new autotuned leaf invalidates captured plans
@@ -758,6 +1000,60 @@ void bucket_result(const void* host_stage, int count, int z, bool mixed, int32_t
 
 using namespace spin;
 
+// Host-side description of the persistent schedule of a plain batch (no
+// device work): stages, tasks, leaves, products and their flops, after
+// checking the task order's invariants (each bucket's stages in recursion
+// order, each stage's `need` equal to the tasks of the bucket's earlier
+// stages, task starts the running sums of count x tiles).
+extern "C" int spin_batch_schedule_info(const int64_t* n, int count, int leaf, int64_t* stages, int64_t* tasks,
+                                        int64_t* leaves, int64_t* products, double* flops) {
+    if (n == nullptr || count < 1 || count > 65535 || leaf < 0 || leaf > kPersistMaxLeaf) return SPIN_ERR_INVALID_ARG;
+    std::vector<int64_t> sorted(n, n + count);
+    for (int64_t v : sorted)
+        if (v < 1 || v > 65536) return SPIN_ERR_INVALID_ARG;
+    std::stable_sort(sorted.begin(), sorted.end());
+    std::vector<Bucket> buckets;
+    for (int i = 0; i < count;) {
+        int j = i;
+        while (j < count && sorted[j] == sorted[i]) j++;
+        Bucket b;
+        b.n = sorted[i];
+        b.leaf = std::min(batched_leaf(b.n, leaf, SPIN_FP64), kPersistMaxLeaf);
+        b.count = j - i;
+        b.first = i;
+        buckets.push_back(b);
+        i = j;
+    }
+    std::vector<PStage> st;
+    std::vector<int64_t> start;
+    order_stages(buckets, st, start);
+    std::map<int, int64_t> seen;  // bucket first -> tasks of its stages so far
+    std::map<int, int> last_leaf;
+    int64_t nl = 0, np = 0;
+    double fl = 0.0;
+    for (size_t i = 0; i < st.size(); i++) {
+        const PStage& x = st[i];
+        if (start[i + 1] - start[i] != (int64_t)x.count * x.tiles) return SPIN_ERR_CUDA;
+        if (x.need != seen[x.first]) return SPIN_ERR_CUDA;
+        seen[x.first] += x.tiles;
+        if (x.kind == PSTAGE_LEAF) {
+            if (x.m > kPersistMaxLeaf || x.leaf_index != last_leaf[x.first]) return SPIN_ERR_CUDA;
+            last_leaf[x.first]++;
+            nl += x.count;
+            fl += 2.0 * (double)x.m * (double)x.m * (double)x.m * x.count;
+        } else {
+            np += x.count;
+            fl += 2.0 * (double)x.m * (double)x.n * (double)x.k * x.count;
+        }
+    }
+    if (stages) *stages = (int64_t)st.size();
+    if (tasks) *tasks = start.back();
+    if (leaves) *leaves = nl;
+    if (products) *products = np;
+    if (flops) *flops = fl;
+    return SPIN_OK;
+}
+
 extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
                                    int count, const spin_opts* opts, int* info_dev, spin_stream_t stream) {
     if (count < 1 || A == nullptr || lda == nullptr || X == nullptr || n == nullptr) return SPIN_ERR_INVALID_ARG;
@@ -765,7 +1061,9 @@ extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, d
     if (o.precision != SPIN_FP64 && o.precision != SPIN_MIXED_BF16X3) return SPIN_ERR_NOT_IMPLEMENTED;
     if (o.pretransform != 0) return SPIN_ERR_NOT_IMPLEMENTED;  // the batch has no butterfly transform
     const bool mixed = o.precision != SPIN_FP64;
-    if (o.leaf < 0) return SPIN_ERR_INVALID_ARG;
+    if (o.leaf < 0 || o.schedule < SPIN_SCHEDULE_DEFAULT || o.schedule > SPIN_SCHEDULE_PERSISTENT)
+        return SPIN_ERR_INVALID_ARG;
+    if (!mixed && o.schedule == SPIN_SCHEDULE_PERSISTENT && o.leaf > kPersistMaxLeaf) return SPIN_ERR_INVALID_ARG;
     if (mixed && (o.residual_slices < 0 || o.residual_slices > 7 || o.max_refine < 0 || !(o.tol > 0.0) ||
                   o.fp64_levels < 0))
         return SPIN_ERR_INVALID_ARG;

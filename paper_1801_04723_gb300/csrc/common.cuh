@@ -75,6 +75,8 @@ struct BatchView {
 // ---- kernel launchers (host) ----
 // FP64 product tile size (64, 32 or 16) for count m x n products side by side.
 int gemm_f64_tile_size(int64_t m, int64_t n, int64_t count);
+// The tile SPIN_F64_TILE forces (64, 32 or 16; for measurement), else 0.
+int forced_f64_tile();
 int launch_gemm_f64(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, const double* C, int64_t ldc, double* D,
                     int64_t ldd, cudaStream_t s);

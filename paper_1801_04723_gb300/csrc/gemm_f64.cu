@@ -195,6 +195,8 @@ int tile_group() {
 
 }  // namespace
 
+int forced_f64_tile() { return forced_tile(); }
+
 // Tile size for an m x n product (count of them side by side): the one
 // whose busiest SM has the fewest FMAs, ceil(tiles / 152) * TM^2 per
 // k, larger tiles preferred unless a smaller one is at least 1.25x better

@@ -99,6 +99,15 @@ def test_invalid_arguments_rejected_on_host(L):
     assert L.spin_gemm_f64(4, 4, 4, 1.0, a, 4, a, 4, 1.0, None, 0, x, 4, None) == 1
     # leaf order above the supported maximum
     assert L.spin_leaf_inverse(a, 5000, x, 5000, 5000, None, None) == 1
+    # batched: a schedule outside 0..2, or the persistent schedule with a leaf above 64
+    ptrs = (ctypes.c_void_p * 1)(ctypes.addressof(buf))
+    outs = (ctypes.c_void_p * 1)(ctypes.addressof(buf) + 8 * 32)
+    lds = (ctypes.c_int64 * 1)(4)
+    ns = (ctypes.c_int64 * 1)(4)
+    ob = binding.make_opts(schedule=3)
+    assert L.spin_invert_batched(ptrs, lds, outs, ns, 1, ctypes.byref(ob), None, None) == 1
+    ob = binding.make_opts(schedule="persistent", leaf=128)
+    assert L.spin_invert_batched(ptrs, lds, outs, ns, 1, ctypes.byref(ob), None, None) == 1
     # leaf exchange timeout hook: order outside 2..256, limit outside (0, 4000] ms
     L.spin_test_leaf_timeout.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_double]
     assert L.spin_test_leaf_timeout(1, 0, 50.0) == 1

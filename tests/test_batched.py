@@ -23,8 +23,18 @@ def spin():
     return s
 
 
+PERSIST_MAX_LEAF = 64
+
+
 def leaf_rule(n, leaf=0):
+    """Leaf of a bucket of order n in the lockstep form (and the library's
+    default leaf)."""
     return min(leaf if leaf > 0 else (n if n <= 128 else 64), n)
+
+
+def persistent_leaf(n, leaf=0):
+    """Leaf of a bucket in the plain form's default, persistent schedule."""
+    return min(leaf_rule(n, leaf), PERSIST_MAX_LEAF)
 
 
 def check(A, X, leaf):
@@ -45,7 +55,7 @@ def test_batch_uneven_orders(spin):
     torch.cuda.synchronize()
     assert int(info.abs().sum()) == 0
     for i in range(0, len(mats), 5):  # oracle on a sample of the batch
-        check(mats[i], Xs[i].cpu().numpy(), leaf_rule(len(mats[i])))
+        check(mats[i], Xs[i].cpu().numpy(), persistent_leaf(len(mats[i])))
 
 
 def test_batch_replay_strided_and_singular(spin):
@@ -183,17 +193,66 @@ def test_batch_autotuned_leaf(spin):
             assert ms > 0.0
         As = [inputs.sdd(o, seed=inputs.SEED_BASE + 700 + i) for i, o in enumerate(orders)]
         dev = [torch.from_numpy(a).cuda() for a in As]
-        X0, info = spin.invert_batched(dev, leaf=0)
-        assert int(info.abs().sum()) == 0
-        for o in set(orders):
-            idx = [i for i, v in enumerate(orders) if v == o]
-            X1, info1 = spin.invert_batched([dev[i] for i in idx], leaf=rec[o][0])
-            assert int(info1.abs().sum()) == 0
-            for i, x in zip(idx, X1):
-                assert torch.equal(X0[i], x)
-        for i in (0, 6, 9):
-            check(As[i], X0[i].cpu().numpy(), rec[orders[i]][0])
+        for schedule, cap in (("lockstep", None), ("default", PERSIST_MAX_LEAF)):
+            X0, info = spin.invert_batched(dev, leaf=0, schedule=schedule)
+            assert int(info.abs().sum()) == 0
+            for o in set(orders):
+                idx = [i for i, v in enumerate(orders) if v == o]
+                want = rec[o][0] if cap is None else min(rec[o][0], cap)
+                X1, info1 = spin.invert_batched([dev[i] for i in idx], leaf=want, schedule=schedule)
+                assert int(info1.abs().sum()) == 0
+                for i, x in zip(idx, X1):
+                    assert torch.equal(X0[i], x)
+            for i in (0, 6, 9):
+                want = rec[orders[i]][0] if cap is None else min(rec[orders[i]][0], cap)
+                check(As[i], X0[i].cpu().numpy(), want)
     finally:
         back = spin.autotune_batched_leaf(sorted(set(orders)), "fp64", candidates=())
     for o, (leaf, ms) in back.items():
         assert leaf == leaf_rule(o) and ms == -1.0
+
+
+def test_batch_persistent_matches_lockstep(spin):
+    """The plain batch as one persistent launch (a device-side task list of
+    leaf inversions and product tiles, dependencies counted per matrix)
+    against the lockstep launches: the same operations on every entry, so
+    the same results bit for bit, at ragged orders, several leaves, strided
+    inputs and a graph replay; a sample is checked against the oracle."""
+    orders = [1, 5, 31, 33, 64, 96, 100, 130, 255, 300, 300, 511, 700, 1024]
+    mats = [inputs.sdd(n, seed=3000 + i) if i % 2 else inputs.spd_gram(n, seed=3000 + i)
+            for i, n in enumerate(orders)]
+    big = torch.zeros((1100, 1300), dtype=torch.float64, device="cuda:0")
+    big[3:703, 7:707] = torch.from_numpy(mats[12]).cuda()  # a strided view
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    As[12] = big[3:703, 7:707]
+    for leaf in (64, 32, 7):
+        Xp, ip = spin.invert_batched(As, leaf=leaf, schedule="persistent")
+        assert spin.batched_stats()["kernels"] == 2  # the persistent kernel and the status scatter
+        Xl, il = spin.invert_batched(As, leaf=leaf, schedule="lockstep")
+        torch.cuda.synchronize()
+        assert ip.cpu().tolist() == [0] * len(orders) and il.cpu().tolist() == [0] * len(orders)
+        for a, b in zip(Xp, Xl):
+            assert torch.equal(a, b)
+        first = [x.clone() for x in Xp]
+        Xp2, _ = spin.invert_batched(As, leaf=leaf, schedule="persistent", outs=Xp)  # graph replay
+        torch.cuda.synchronize()
+        for a, b in zip(first, Xp2):
+            assert torch.equal(a, b)
+        for i in (0, 3, 7, 12, 13):
+            check(mats[i], Xp[i].cpu().numpy(), min(leaf, orders[i]))
+
+
+def test_batch_persistent_singular_matrix_only(spin):
+    """A singular leaf in one matrix of a persistent batch is reported for
+    that matrix alone (the others finish and are right)."""
+    sing = inputs.sdd(200, seed=11)
+    sing[40:80, :] = 0.0
+    sing[:, 40:80] = 0.0  # A11 (leaf 64) has a zero column block: a zero pivot
+    mats = [inputs.sdd(300, seed=12), sing, inputs.spd_gram(150, seed=13)]
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    Xs, info = spin.invert_batched(As, leaf=64, schedule="persistent")
+    torch.cuda.synchronize()
+    st = info.cpu().tolist()
+    assert st == [0, 2, 0]
+    check(mats[0], Xs[0].cpu().numpy(), 64)
+    check(mats[2], Xs[2].cpu().numpy(), 64)
