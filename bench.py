@@ -101,6 +101,8 @@ def parse():
                     "(at most --steps)")
     ap.add_argument("--mixed-warmup", type=int, default=2, help="plain_fp64: warm-up steps of the mixed sub-record "
                     "(at most --warmup, at least 1)")
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
+                    help="batched workloads: matrices per batch (smaller for profiler captures)")
     ap.add_argument("--batch-schedule", default="default", choices=["default", "lockstep", "persistent"],
                     help="batched workloads, plain form: one persistent launch (default) or lockstep launches")
     ap.add_argument("--profile-json", default="", help="write per-launch records here")
@@ -629,7 +631,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
         torch.cuda.synchronize()
 
     if w["family"] == "batch_sdd":
-        work = BatchWork(spin, w, n, leaf, device, BATCH_COUNT, args.batch_schedule)
+        work = BatchWork(spin, w, n, leaf, device, args.batch_count, args.batch_schedule)
     else:
         work = SingleWork(spin, w, n, leaf, device, args.pretransform, args.fp64_levels)
     stream = torch.cuda.current_stream()

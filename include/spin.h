@@ -502,6 +502,16 @@ int spin_take_device_error(spin_stream_t stream);
  * SPIN_ERR_INVALID_ARG for a bad order, rank or limit. */
 int spin_test_leaf_timeout(int64_t L, int mute_rank, double limit_ms);
 
+/* Test hook for the persistent batch kernel's bounded dependency waits: a
+ * plain batch of two matrices 2I of order 128 (leaf 64) in which the first
+ * level product waits for a task count that nothing reaches, every wait
+ * limited to limit_ms (0 < limit_ms <= 4000).  The wait runs out, the
+ * kernel records SPIN_ERR_TIMEOUT, the remaining tasks skip their work, and
+ * the launch ends without a fault or a hang; *status0 and *status1 get the
+ * two matrices' statuses (both SPIN_ERR_TIMEOUT).  Synchronises the device.
+ * SPIN_ERR_INVALID_ARG for a bad limit or a NULL pointer. */
+int spin_test_persistent_timeout(double limit_ms, int* status0, int* status1);
+
 /* ---------------------------------------------------------------------
  * Instrumentation: the paper times each method of the recursion
  * separately (Sec. 5, Table 3: leafNode, multiply, subtract, ...).  With

@@ -25,6 +25,7 @@ from .binding import (  # noqa: F401
     gemm_ozaki,
     take_device_error,
     leaf_exchange_timeout,
+    persistent_wait_timeout,
     invert,
     invert_host,
     invert_noalloc,

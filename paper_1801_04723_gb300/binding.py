@@ -208,6 +208,9 @@ def lib():
         L.spin_take_device_error.restype = ctypes.c_int
         L.spin_test_leaf_timeout.argtypes = [i64, ctypes.c_int, ctypes.c_double]
         L.spin_test_leaf_timeout.restype = ctypes.c_int
+        L.spin_test_persistent_timeout.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                                   ctypes.POINTER(ctypes.c_int)]
+        L.spin_test_persistent_timeout.restype = ctypes.c_int
         L.spin_invert_noalloc.argtypes = [vp, vp, i64, i64, ctypes.c_int, vp]
         L.spin_invert_noalloc.restype = ctypes.c_int
         _lib = L
@@ -478,6 +481,16 @@ def take_device_error(stream=None) -> int:
 def leaf_exchange_timeout(order: int, mute_rank: int, limit_ms: float) -> int:
     """Status of a leaf whose CTA mute_rank sends nothing (spin_test_leaf_timeout)."""
     return int(lib().spin_test_leaf_timeout(int(order), int(mute_rank), float(limit_ms)))
+
+
+def persistent_wait_timeout(limit_ms: float):
+    """Statuses of the two matrices of a persistent batch whose first level
+    product waits for a count nothing reaches (spin_test_persistent_timeout)."""
+    s0, s1 = ctypes.c_int(-1), ctypes.c_int(-1)
+    rc = lib().spin_test_persistent_timeout(float(limit_ms), ctypes.byref(s0), ctypes.byref(s1))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_test_persistent_timeout")
+    return s0.value, s1.value
 
 
 def invert_noalloc(A, *, leaf: int = 0, out=None, stream=None):

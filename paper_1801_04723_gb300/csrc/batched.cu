@@ -1005,6 +1005,101 @@ using namespace spin;
 // checking the task order's invariants (each bucket's stages in recursion
 // order, each stage's `need` equal to the tasks of the bucket's earlier
 // stages, task starts the running sums of count x tiles).
+// Test hook for the persistent kernel's bounded dependency waits: two
+// matrices 2I of order 128 (leaf 64) whose first level product is made to
+// wait for a task count nothing reaches, every wait limited to limit_ms.
+// The wait runs out, the kernel records SPIN_ERR_TIMEOUT, every later task
+// skips its work and the launch ends.  Writes both matrices' statuses.
+extern "C" int spin_test_persistent_timeout(double limit_ms, int* status0, int* status1) {
+    if (!(limit_ms > 0.0) || limit_ms > 4000.0 || status0 == nullptr || status1 == nullptr)
+        return SPIN_ERR_INVALID_ARG;
+    constexpr int64_t n = 128, leaf = 64;
+    constexpr int count = 2;
+    Bucket b;
+    b.n = n;
+    b.leaf = leaf;
+    b.count = count;
+    b.first = 0;
+    std::vector<Bucket> buckets(1, b);
+    std::vector<PStage> st;
+    std::vector<int64_t> start;
+    order_stages(buckets, st, start);
+    if (st.size() < 2 || st[1].kind != PSTAGE_PRODUCT) return SPIN_ERR_CUDA;
+    st[1].need += 1 << 30;  // the first product waits for a count nothing reaches
+    const size_t nn = (size_t)n * n, ws = fp64_workspace_elems(n, leaf);
+    const size_t done_bytes = align256(count * sizeof(unsigned));
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t o_a = take(count * nn * 8), o_x = take(count * nn * 8), o_w = take(count * ws * 8),
+                 o_ptr = take(4 * count * 8), o_rec = take(count * INFO_WORDS * 4), o_ctl = take(done_bytes + 256),
+                 o_st = take(st.size() * sizeof(PStage)), o_start = take(start.size() * 8);
+    unsigned char* d = nullptr;
+    if (cudaMalloc(&d, off) != cudaSuccess) {
+        cudaGetLastError();
+        return SPIN_ERR_OOM;
+    }
+    int rc = SPIN_OK;
+    {
+        std::vector<double> A(count * nn, 0.0);
+        for (int z = 0; z < count; z++)
+            for (int64_t i = 0; i < n; i++) A[z * nn + (size_t)i * n + i] = 2.0;
+        std::vector<uint64_t> ptr(4 * count);
+        for (int z = 0; z < count; z++) {
+            ptr[z] = (uint64_t)(uintptr_t)(d + o_a + z * nn * 8);
+            ptr[count + z] = (uint64_t)n;
+            ptr[2 * count + z] = (uint64_t)(uintptr_t)(d + o_x + z * nn * 8);
+            ptr[3 * count + z] = (uint64_t)(uintptr_t)(d + o_w + z * ws * 8);
+        }
+        cudaError_t e = cudaMemcpy(d + o_a, A.data(), A.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d + o_ptr, ptr.data(), ptr.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d + o_st, st.data(), st.size() * sizeof(PStage), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d + o_start, start.data(), start.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(d + o_rec, 0, count * INFO_WORDS * 4);
+        if (e == cudaSuccess) e = cudaMemset(d + o_ctl, 0, done_bytes + 256);
+        if (e != cudaSuccess) {
+            record_cuda_error(e, "persistent timeout test set-up", __FILE__, __LINE__);
+            cudaGetLastError();
+            rc = SPIN_ERR_CUDA;
+        }
+    }
+    if (rc == SPIN_OK) {
+        PersistentArgs a;
+        a.stages = (const PStage*)(d + o_st);
+        a.start = (const int64_t*)(d + o_start);
+        a.nstages = (int)st.size();
+        a.a_base = (const double* const*)(d + o_ptr);
+        a.a_ld = (const int64_t*)(d + o_ptr + count * 8);
+        a.x_base = (double* const*)(d + o_ptr + 2 * count * 8);
+        a.w_base = (double* const*)(d + o_ptr + 3 * count * 8);
+        a.records = (int32_t*)(d + o_rec);
+        a.done = (unsigned*)(d + o_ctl);
+        a.next = (unsigned long long*)(d + o_ctl + done_bytes);
+        a.err = (int*)(d + o_ctl + done_bytes + 8);
+        a.limit_ns = (uint64_t)(limit_ms * 1e6);
+        const size_t smem = persistent_smem_bytes(leaf);
+        int grid = 0;
+        rc = persistent_grid(smem, start.back(), &grid);
+        if (rc == SPIN_OK) rc = launch_persistent_batch(a, smem, std::min(grid, 4), 0);
+        int32_t rec[count * INFO_WORDS] = {};
+        if (rc == SPIN_OK) {
+            cudaError_t e = cudaMemcpy(rec, d + o_rec, sizeof rec, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                record_cuda_error(e, "persistent timeout test result", __FILE__, __LINE__);
+                cudaGetLastError();
+                rc = SPIN_ERR_CUDA;
+            }
+        }
+        *status0 = rec[INFO_STATUS];
+        *status1 = rec[INFO_WORDS + INFO_STATUS];
+    }
+    cudaFree(d);
+    return rc;
+}
+
 extern "C" int spin_batch_schedule_info(const int64_t* n, int count, int leaf, int64_t* stages, int64_t* tasks,
                                         int64_t* leaves, int64_t* products, double* flops) {
     if (n == nullptr || count < 1 || count > 65535 || leaf < 0 || leaf > kPersistMaxLeaf) return SPIN_ERR_INVALID_ARG;

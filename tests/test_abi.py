@@ -114,6 +114,11 @@ def test_invalid_arguments_rejected_on_host(L):
     assert L.spin_test_leaf_timeout(300, 0, 50.0) == 1
     assert L.spin_test_leaf_timeout(128, 0, 0.0) == 1
     assert L.spin_test_leaf_timeout(128, 0, 5000.0) == 1
+    # persistent batch timeout hook: limit outside (0, 4000] ms, NULL outputs
+    s0, s1 = ctypes.c_int(), ctypes.c_int()
+    assert L.spin_test_persistent_timeout(0.0, ctypes.byref(s0), ctypes.byref(s1)) == 1
+    assert L.spin_test_persistent_timeout(5000.0, ctypes.byref(s0), ctypes.byref(s1)) == 1
+    assert L.spin_test_persistent_timeout(50.0, None, ctypes.byref(s1)) == 1
 
 
 def test_pretransform_workspace(L):

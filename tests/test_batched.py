@@ -256,3 +256,17 @@ def test_batch_persistent_singular_matrix_only(spin):
     assert st == [0, 2, 0]
     check(mats[0], Xs[0].cpu().numpy(), 64)
     check(mats[2], Xs[2].cpu().numpy(), 64)
+
+
+def test_batch_persistent_wait_timeout(spin):
+    """A dependency wait of the persistent kernel that runs out (a count
+    that nothing reaches, 50 ms limit) ends the launch with
+    SPIN_ERR_TIMEOUT for the matrices it left undone, without a fault or a
+    hang; a persistent batch right after it is right."""
+    assert spin.persistent_wait_timeout(50.0) == (6, 6)
+    mats = [inputs.sdd(200, seed=21), inputs.spd_gram(96, seed=22)]
+    Xs, info = spin.invert_batched([torch.from_numpy(a).cuda() for a in mats], schedule="persistent")
+    torch.cuda.synchronize()
+    assert info.cpu().tolist() == [0, 0]
+    for a, x in zip(mats, Xs):
+        check(a, x.cpu().numpy(), persistent_leaf(a.shape[0]))
