@@ -70,6 +70,7 @@ WORKLOADS = {
 BATCH_COUNT = 4096
 BATCH_LEAF_CANDIDATES = (32, 64, 128, 256)
 PERSIST_MAX_LEAF = 64  # largest leaf of the persistent batch kernel
+BATCH_TILE_CANDIDATES = (64, 32, 16)  # largest product tile of a bucket, persistent schedule
 
 
 def measured_peaks() -> dict:
@@ -454,11 +455,20 @@ class BatchWork:
             # per order bucket, the fastest leaf on a bucket of the same size
             # (outside the timed region); leaf 0 then uses the records
             t0 = time.perf_counter()
-            rec = spin.autotune_batched_leaf(self.orders, self.precision, candidates=cands)
+            if persistent:
+                # leaf and largest product tile per order bucket, on the persistent kernel
+                rec = spin.autotune_batched_persistent(self.orders, leaves=cands, tiles=BATCH_TILE_CANDIDATES)
+                tiles = {}
+                for m in sorted(set(self.orders)):
+                    tiles.setdefault(str(rec[m][1]), []).append(m)
+            else:
+                rec = spin.autotune_batched_leaf(self.orders, self.precision, candidates=cands)
             chosen = {}
             for m in sorted(set(self.orders)):
                 chosen.setdefault(str(rec[m][0]), []).append(m)
             self.tuned = {"candidates": list(cands), "leaf_orders": chosen,
+                          **({"tile_candidates": list(BATCH_TILE_CANDIDATES), "tile_orders": tiles}
+                             if persistent else {}),
                           "tuning_s": time.perf_counter() - t0}
 
     def step(self):

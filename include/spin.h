@@ -243,6 +243,38 @@ int spin_autotune_batched_leaf(const int64_t* orders, int count, int precision, 
 int spin_batch_schedule_info(const int64_t* n, int count, int leaf, int64_t* stages, int64_t* tasks,
                              int64_t* leaves, int64_t* products, double* flops);
 
+/*
+ * spin_autotune_batched_persistent: the block-size trade-off of Sec. 5.3
+ * for the persistent schedule of plain batches, per order bucket: leaf
+ * size and product tile shape.  orders: host array of the batch's `count`
+ * orders (repeats give the bucket sizes).  A batch of these orders (seeded
+ * strictly diagonally dominant matrices) runs on the persistent kernel once
+ * per candidate pair of leaf (host array of nleaf orders, each 1..64;
+ * clamped to the order) and largest product tile (host array of ntile
+ * values, each 16, 32 or 64; every product of a bucket then takes the
+ * cheapest allowed tile by the schedule's cost rule), the pair applied to
+ * every bucket, after a warm-up run.  The kernel adds the SM clocks of each
+ * task to its bucket's counter (two counted runs, the smaller count kept),
+ * and each bucket is given the pair under which its tasks took the fewest
+ * clocks -- its share of the whole launch, measured beside the other
+ * buckets -- when that beats the library's own pair (leaf 64, tile 64, or
+ * the first candidate pair if that one is not among them) by 2 %.  The pairs are recorded per order:
+ * plain spin_invert_batched calls with opts.leaf = 0 on the persistent
+ * schedule use them (plans captured before are rebuilt).  leaf_out,
+ * tile_out (host, count): the chosen pair per entry of orders; ms_out
+ * (host, count, optional): the bucket's task time under it, in SM
+ * milliseconds at the maximum SM clock.  Allocates the batch (two copies of
+ * its matrices and its workspace) for the duration of the call;
+ * synchronises the stream.  spin_autotune_batched_leaf with precision
+ * SPIN_FP64 and ncand = 0 forgets both records.  Errors:
+ * SPIN_ERR_INVALID_ARG (null arrays, count outside 1..65535, nleaf or
+ * ntile < 1, an order outside [1, 65536], a leaf outside 1..64, a tile not
+ * 16, 32 or 64), SPIN_ERR_OOM (nothing is recorded).
+ */
+int spin_autotune_batched_persistent(const int64_t* orders, int count, const int* leaves, int nleaf,
+                                     const int* tiles, int ntile, int* leaf_out, int* tile_out, double* ms_out,
+                                     spin_stream_t stream);
+
 /* Shape of the graph the latest spin_invert_batched on `stream` replays:
  * kernel launches per call and order buckets.  SPIN_ERR_INVALID_ARG if none. */
 int spin_batched_stats(spin_stream_t stream, int* kernels, int* buckets);

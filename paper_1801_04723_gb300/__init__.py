@@ -26,6 +26,7 @@ from .binding import (  # noqa: F401
     take_device_error,
     leaf_exchange_timeout,
     persistent_wait_timeout,
+    autotune_batched_persistent,
     invert,
     invert_host,
     invert_noalloc,

@@ -211,6 +211,10 @@ def lib():
         L.spin_test_persistent_timeout.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                                    ctypes.POINTER(ctypes.c_int)]
         L.spin_test_persistent_timeout.restype = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.spin_autotune_batched_persistent.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ip, ctypes.c_int,
+                                                       ip, ctypes.c_int, ip, ip, ctypes.POINTER(ctypes.c_double), vp]
+        L.spin_autotune_batched_persistent.restype = ctypes.c_int
         L.spin_invert_noalloc.argtypes = [vp, vp, i64, i64, ctypes.c_int, vp]
         L.spin_invert_noalloc.restype = ctypes.c_int
         _lib = L
@@ -566,6 +570,25 @@ def autotune_batched_leaf(orders, precision="fp64", candidates=(32, 64, 128), st
     if rc != SPIN_OK:
         raise SpinError(rc, "spin_autotune_batched_leaf")
     return {o: (out[i], ms[i]) for i, o in enumerate(orders)}
+
+
+def autotune_batched_persistent(orders, leaves=(32, 64), tiles=(64, 32, 16), stream=None) -> dict:
+    """Per order bucket of a plain batch, the fastest (leaf, largest product
+    tile) pair of the persistent schedule (spin_autotune_batched_persistent);
+    recorded for later plain batched calls with leaf 0.  Returns
+    {order: (leaf, tile, ms per bucket run)}."""
+    orders = [int(v) for v in orders]
+    la = (ctypes.c_int * len(leaves))(*[int(v) for v in leaves])
+    ta = (ctypes.c_int * len(tiles))(*[int(v) for v in tiles])
+    arr = (ctypes.c_int64 * len(orders))(*orders)
+    lo = (ctypes.c_int * len(orders))()
+    to = (ctypes.c_int * len(orders))()
+    ms = (ctypes.c_double * len(orders))()
+    rc = lib().spin_autotune_batched_persistent(arr, len(orders), la, len(leaves), ta, len(tiles), lo, to, ms,
+                                                _stream(stream))
+    if rc != SPIN_OK:
+        raise SpinError(rc, "spin_autotune_batched_persistent")
+    return {o: (lo[i], to[i], ms[i]) for i, o in enumerate(orders)}
 
 
 def schedule_stats(stream=None) -> dict:

@@ -51,6 +51,7 @@ struct Bucket {
     size_t arena_offset;   // bytes into the plan's arena
     int stream;            // pool stream the bucket runs on
     int sr, s0;            // mixed: digit slices of the certifying residuals and of the first one
+    int tile_cap = 64;     // persistent schedule: largest product tile
 };
 
 // Residual slices of a bucket of order n (the single-matrix rule).
@@ -225,16 +226,17 @@ PView psub(PView v, int64_t dr, int64_t dc) {
 // least CTA time: padded FMAs (one per clock for one of the two CTAs of an
 // SM) plus a fixed cost per task (taking the task, its dependency check and
 // its completion, about 3000 clocks).  The tile never changes a result bit.
-int persist_tile(int64_t m, int64_t n, int64_t k) {
+int persist_tile(int64_t m, int64_t n, int64_t k, int cap) {
     const int forced = forced_f64_tile();
     if (forced) return forced;
     constexpr double kTaskClocks = 3000.0;
-    int best = 64;
+    int best = 0;
     double best_cost = 0.0;
     for (int tm : {64, 32, 16}) {
+        if (tm > cap && tm != 16) continue;
         const double tiles = (double)((m + tm - 1) / tm) * (double)((n + tm - 1) / tm);
         const double cost = tiles * ((double)tm * tm * (double)k + kTaskClocks);
-        if (tm == 64 || cost < best_cost) {
+        if (best == 0 || cost < best_cost) {
             best = tm;
             best_cost = cost;
         }
@@ -248,6 +250,7 @@ struct StageList {
     std::vector<PStage> st;
     int first = 0, count = 0;
     int64_t leaf = 0;
+    int tile_cap = 64;
     int leaf_counter = 0;
     int32_t need = 0;
 
@@ -274,7 +277,7 @@ struct StageList {
     void product(int64_t m, int64_t n, int64_t k, double alpha, PView a, PView b, double beta, PView c, PView d) {
         if (m <= 0 || n <= 0) return;
         PStage x = base(PSTAGE_PRODUCT);
-        x.tm = persist_tile(m, n, k);
+        x.tm = persist_tile(m, n, k, tile_cap);
         x.tiles_n = (int32_t)((n + x.tm - 1) / x.tm);
         x.tiles = (int32_t)((m + x.tm - 1) / x.tm) * x.tiles_n;
         x.m = m;
@@ -331,7 +334,9 @@ void order_stages(const std::vector<Bucket>& buckets, std::vector<PStage>& out, 
         L.first = b.first;
         L.count = b.count;
         L.leaf = b.leaf;
+        L.tile_cap = b.tile_cap;
         pinv(L, pview(0, 0, 0, 0), pview(1, b.n, 0, 0), 0, b.n);
+        for (PStage& x : L.st) x.bucket = (int32_t)i;
         longest = std::max(longest, L.st.size());
     }
     std::vector<size_t> by_order(buckets.size());
@@ -581,6 +586,16 @@ int64_t batched_leaf(int64_t n, int leaf_opt, int precision) {
     return std::min<int64_t>(L, n);
 }
 
+// Largest product tile of a bucket of order n in the persistent schedule:
+// the one spin_autotune_batched_persistent recorded, else 64.
+std::map<int64_t, int> g_btile;  // order -> tile cap (guarded by g_bleaf_mu)
+
+int persist_tile_cap(int64_t n) {
+    std::lock_guard<std::mutex> lk(g_bleaf_mu);
+    auto it = g_btile.find(n);
+    return it == g_btile.end() ? 64 : it->second;
+}
+
 // Plain batches run on the persistent kernel unless the caller asks for the
 // lockstep launches (opts.schedule 1) or passes a leaf above its limit.
 bool use_persistent(const spin_opts& o) {
@@ -627,6 +642,7 @@ int capture_persistent(BatchPlan& p) {
     a.next = (unsigned long long*)(p.pctl + done_bytes);
     a.err = (int*)(p.pctl + done_bytes + 8);
     a.limit_ns = kPersistWaitNs;
+    a.bucket_clocks = nullptr;
     cudaStream_t s = p.cap;
     cudaGraph_t graph = nullptr;
     SPIN_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -674,7 +690,10 @@ int build_plan(BatchPlan& p, const double* const* A, const int64_t* lda, double*
         Bucket b;
         b.n = n[order[i]];
         b.leaf = batched_leaf(b.n, leaf_opt, o.precision);
-        if (p.persistent) b.leaf = std::min(b.leaf, kPersistMaxLeaf);
+        if (p.persistent) {
+            b.leaf = std::min(b.leaf, kPersistMaxLeaf);
+            b.tile_cap = persist_tile_cap(b.n);
+        }
         b.count = j - i;
         b.first = i;
         b.ws_elems = std::max<size_t>(fp64_workspace_elems(b.n, b.leaf), 1);
@@ -1080,6 +1099,7 @@ extern "C" int spin_test_persistent_timeout(double limit_ms, int* status0, int* 
         a.next = (unsigned long long*)(d + o_ctl + done_bytes);
         a.err = (int*)(d + o_ctl + done_bytes + 8);
         a.limit_ns = (uint64_t)(limit_ms * 1e6);
+        a.bucket_clocks = nullptr;
         const size_t smem = persistent_smem_bytes(leaf);
         int grid = 0;
         rc = persistent_grid(smem, start.back(), &grid);
@@ -1114,6 +1134,7 @@ extern "C" int spin_batch_schedule_info(const int64_t* n, int count, int leaf, i
         Bucket b;
         b.n = sorted[i];
         b.leaf = std::min(batched_leaf(b.n, leaf, SPIN_FP64), kPersistMaxLeaf);
+        b.tile_cap = persist_tile_cap(b.n);
         b.count = j - i;
         b.first = i;
         buckets.push_back(b);
@@ -1246,8 +1267,243 @@ __global__ void synth_batch_kernel(double* A, int64_t n, int64_t count, uint64_t
     }
 }
 
+// A whole plain batch on the persistent kernel with given per-bucket leaves
+// and tile caps (matrix z of the sorted order at A[z], result to X[z],
+// leading dimension n), the device memory kept across runs; per-bucket SM
+// clocks accumulate into clocks_dev when it is given.
+struct PersistBatchRun {
+    unsigned char* d = nullptr;
+    size_t bytes = 0;
+    ~PersistBatchRun() { cudaFree(d); }
+
+    int run(const std::vector<Bucket>& buckets, const std::vector<const double*>& A, const std::vector<double*>& X,
+            unsigned long long* clocks_dev, cudaStream_t s) {
+        std::vector<PStage> st;
+        std::vector<int64_t> start;
+        order_stages(buckets, st, start);
+        const size_t c = A.size();
+        std::vector<size_t> wsoff(c);
+        size_t ws_total = 0;
+        int64_t max_leaf = 1;
+        for (const Bucket& b : buckets) {
+            const size_t w = std::max<size_t>(fp64_workspace_elems(b.n, b.leaf), 1);
+            for (int z = 0; z < b.count; z++) {
+                wsoff[b.first + z] = ws_total;
+                ws_total += w;
+            }
+            max_leaf = std::max(max_leaf, std::min(b.leaf, b.n));
+        }
+        const size_t done_bytes = align256(c * sizeof(unsigned));
+        size_t off = 0;
+        auto take = [&](size_t by) {
+            const size_t o = off;
+            off = align256(off + by);
+            return o;
+        };
+        const size_t o_w = take(ws_total * 8), o_ptr = take(4 * c * 8), o_rec = take(c * INFO_WORDS * 4),
+                     o_ctl = take(done_bytes + 256), o_st = take(st.size() * sizeof(PStage)),
+                     o_start = take(start.size() * 8);
+        if (off > bytes) {
+            cudaFree(d);
+            d = nullptr;
+            bytes = 0;
+            if (cudaMalloc(&d, off) != cudaSuccess) {
+                cudaGetLastError();
+                return SPIN_ERR_OOM;
+            }
+            bytes = off;
+        }
+        std::vector<uint64_t> ptr(4 * c);
+        for (size_t z = 0; z < c; z++) {
+            ptr[z] = (uint64_t)(uintptr_t)A[z];
+            ptr[2 * c + z] = (uint64_t)(uintptr_t)X[z];
+            ptr[3 * c + z] = (uint64_t)(uintptr_t)(d + o_w + wsoff[z] * 8);
+        }
+        for (const Bucket& b : buckets)
+            for (int z = 0; z < b.count; z++) ptr[c + b.first + z] = (uint64_t)b.n;
+        SPIN_CUDA_TRY(cudaMemcpyAsync(d + o_ptr, ptr.data(), ptr.size() * 8, cudaMemcpyHostToDevice, s));
+        SPIN_CUDA_TRY(cudaMemcpyAsync(d + o_st, st.data(), st.size() * sizeof(PStage), cudaMemcpyHostToDevice, s));
+        SPIN_CUDA_TRY(cudaMemcpyAsync(d + o_start, start.data(), start.size() * 8, cudaMemcpyHostToDevice, s));
+        SPIN_CUDA_TRY(cudaMemsetAsync(d + o_rec, 0, c * INFO_WORDS * 4, s));
+        SPIN_CUDA_TRY(cudaMemsetAsync(d + o_ctl, 0, done_bytes + 256, s));
+        SPIN_CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors must outlive the copies
+        PersistentArgs a;
+        a.stages = (const PStage*)(d + o_st);
+        a.start = (const int64_t*)(d + o_start);
+        a.nstages = (int)st.size();
+        a.a_base = (const double* const*)(d + o_ptr);
+        a.a_ld = (const int64_t*)(d + o_ptr + c * 8);
+        a.x_base = (double* const*)(d + o_ptr + 2 * c * 8);
+        a.w_base = (double* const*)(d + o_ptr + 3 * c * 8);
+        a.records = (int32_t*)(d + o_rec);
+        a.done = (unsigned*)(d + o_ctl);
+        a.next = (unsigned long long*)(d + o_ctl + done_bytes);
+        a.err = (int*)(d + o_ctl + done_bytes + 8);
+        a.limit_ns = kPersistWaitNs;
+        a.bucket_clocks = clocks_dev;
+        const size_t smem = persistent_smem_bytes(max_leaf);
+        int grid = 0;
+        BRET(persistent_grid(smem, start.back(), &grid));
+        return launch_persistent_batch(a, smem, grid, s);
+    }
+};
+
 }  // namespace
 }  // namespace spin
+
+// The autotuner of the persistent schedule (plain batches), per order
+// bucket in the context of the whole batch: one batch of the given orders
+// (seeded strictly diagonally dominant matrices) runs on the persistent
+// kernel once per candidate pair of leaf (<= 64) and largest product tile
+// (64, 32 or 16), the pair applied to every bucket, after a warm-up run;
+// the kernel adds the SM clocks of each task to its bucket's counter, and
+// each bucket takes the pair under which its tasks took the fewest clocks
+// (the schedule's makespan is about the sum of the task times over the
+// CTAs, so a bucket's task time is its share of it), if that beats the
+// library's own pair (leaf 64, tile 64) by 2 %.  A bucket timed alone
+// would instead favour small tiles that fill the GPU by themselves.
+extern "C" int spin_autotune_batched_persistent(const int64_t* orders, int count, const int* leaves, int nleaf,
+                                                const int* tiles, int ntile, int* leaf_out, int* tile_out,
+                                                double* ms_out, spin_stream_t stream) {
+    using namespace spin;
+    if (orders == nullptr || count < 1 || count > 65535 || nleaf < 1 || ntile < 1 || leaves == nullptr ||
+        tiles == nullptr || leaf_out == nullptr || tile_out == nullptr)
+        return SPIN_ERR_INVALID_ARG;
+    for (int i = 0; i < count; i++)
+        if (orders[i] < 1 || orders[i] > 65536) return SPIN_ERR_INVALID_ARG;
+    for (int i = 0; i < nleaf; i++)
+        if (leaves[i] < 1 || leaves[i] > kPersistMaxLeaf) return SPIN_ERR_INVALID_ARG;
+    for (int i = 0; i < ntile; i++)
+        if (tiles[i] != 16 && tiles[i] != 32 && tiles[i] != 64) return SPIN_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::map<int64_t, int> mult;
+    for (int i = 0; i < count; i++) mult[orders[i]]++;
+    std::vector<Bucket> buckets;
+    size_t elems = 0;
+    int first = 0;
+    for (const auto& kv : mult) {
+        Bucket b;
+        b.n = kv.first;
+        b.count = kv.second;
+        b.first = first;
+        b.leaf = 1;
+        first += kv.second;
+        elems += (size_t)kv.second * (size_t)b.n * (size_t)b.n;
+        buckets.push_back(b);
+    }
+    const size_t nb = buckets.size();
+    double* A = nullptr;
+    double* X = nullptr;
+    unsigned long long* clk = nullptr;
+    if (cudaMalloc(&A, elems * sizeof(double)) != cudaSuccess || cudaMalloc(&X, elems * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&clk, nb * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(A);
+        cudaFree(X);
+        return SPIN_ERR_OOM;
+    }
+    std::vector<const double*> ap(count);
+    std::vector<double*> xp(count);
+    {
+        size_t off = 0;
+        for (const Bucket& b : buckets) {
+            const size_t nn = (size_t)b.n * (size_t)b.n;
+            synth_batch_kernel<<<1024, 256, 0, s>>>(A + off, b.n, b.count, 0x5EEDBA7Cull + (uint64_t)b.n);
+            for (int z = 0; z < b.count; z++) {
+                ap[b.first + z] = A + off + z * nn;
+                xp[b.first + z] = X + off + z * nn;
+            }
+            off += (size_t)b.count * nn;
+        }
+    }
+    int rc = SPIN_OK;
+    {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            record_cuda_error(e, "autotuner inputs", __FILE__, __LINE__);
+            rc = SPIN_ERR_CUDA;
+        }
+    }
+    std::vector<unsigned long long> best_clk(nb, ~0ull), ref_clk(nb, ~0ull), h(nb);
+    std::vector<int64_t> best_leaf(nb, 0), ref_leaf(nb, 0);
+    std::vector<int> best_tile(nb, 0), ref_tile(nb, 0);
+    std::vector<std::pair<int, int>> tried;
+    PersistBatchRun runner;
+    for (int li = 0; li < nleaf && rc == SPIN_OK; li++)
+        for (int ti = 0; ti < ntile && rc == SPIN_OK; ti++) {
+            const std::pair<int, int> key(leaves[li], tiles[ti]);
+            if (std::find(tried.begin(), tried.end(), key) != tried.end()) continue;
+            tried.push_back(key);
+            for (Bucket& b : buckets) {
+                b.leaf = std::min<int64_t>(leaves[li], b.n);
+                b.tile_cap = tiles[ti];
+            }
+            // a warm-up run, then two counted ones (each bucket keeps its smaller count)
+            std::vector<unsigned long long> m(nb, ~0ull);
+            for (int rep = 0; rep < 3 && rc == SPIN_OK; rep++) {
+                if (cudaMemsetAsync(clk, 0, nb * sizeof(unsigned long long), s) != cudaSuccess) rc = SPIN_ERR_CUDA;
+                if (rc == SPIN_OK) rc = runner.run(buckets, ap, xp, clk, s);
+                if (rc == SPIN_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = SPIN_ERR_CUDA;
+                if (rc == SPIN_OK && rep > 0) {
+                    if (cudaMemcpy(h.data(), clk, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
+                        cudaSuccess)
+                        rc = SPIN_ERR_CUDA;
+                    for (size_t i = 0; i < nb && rc == SPIN_OK; i++) m[i] = std::min(m[i], h[i]);
+                }
+            }
+            if (rc != SPIN_OK) break;
+            // the library's own pair (leaf 64, tile 64), or else the first one, is the
+            // reference; another pair must beat it by 2 % (task clocks vary by about
+            // 1 % between runs, as the buckets share the SMs)
+            const bool is_ref = tried.size() == 1 || (leaves[li] == kPersistMaxLeaf && tiles[ti] == 64);
+            for (size_t i = 0; i < nb; i++) {
+                if (is_ref) {
+                    ref_clk[i] = m[i];
+                    ref_leaf[i] = buckets[i].leaf;
+                    ref_tile[i] = tiles[ti];
+                }
+                if (m[i] < best_clk[i]) {
+                    best_clk[i] = m[i];
+                    best_leaf[i] = buckets[i].leaf;
+                    best_tile[i] = tiles[ti];
+                }
+            }
+        }
+    for (size_t i = 0; i < nb && rc == SPIN_OK; i++)
+        if (!((double)best_clk[i] < 0.98 * (double)ref_clk[i])) {
+            best_clk[i] = ref_clk[i];
+            best_leaf[i] = ref_leaf[i];
+            best_tile[i] = ref_tile[i];
+        }
+    int dev = 0, khz = 0;
+    if (rc == SPIN_OK && (cudaGetDevice(&dev) != cudaSuccess ||
+                          cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0))
+        rc = SPIN_ERR_CUDA;
+    cudaFree(A);
+    cudaFree(X);
+    cudaFree(clk);
+    if (rc != SPIN_OK) {
+        cudaGetLastError();
+        return rc;
+    }
+    std::map<int64_t, size_t> index;
+    {
+        std::lock_guard<std::mutex> lk(g_bleaf_mu);
+        for (size_t i = 0; i < nb; i++) {
+            index[buckets[i].n] = i;
+            g_bleaf[std::make_pair((int)SPIN_FP64, buckets[i].n)] = best_leaf[i];
+            g_btile[buckets[i].n] = best_tile[i];
+        }
+        g_bleaf_gen++;
+    }
+    for (int i = 0; i < count; i++) {
+        const size_t b = index[orders[i]];
+        leaf_out[i] = (int)best_leaf[b];
+        tile_out[i] = best_tile[b];
+        if (ms_out) ms_out[i] = (double)best_clk[b] / (double)khz;
+    }
+    return SPIN_OK;
+}
 
 // Batched leaf autotuning: for every distinct order of `orders` (with its
 // multiplicity in the list, i.e. the bucket that order forms in a batch), one
@@ -1265,7 +1521,10 @@ extern "C" int spin_autotune_batched_leaf(const int64_t* orders, int count, int 
     if (ncand == 0) {  // forget the records of these orders
         {
             std::lock_guard<std::mutex> lk(g_bleaf_mu);
-            for (int i = 0; i < count; i++) g_bleaf.erase(std::make_pair(precision, orders[i]));
+            for (int i = 0; i < count; i++) {
+                g_bleaf.erase(std::make_pair(precision, orders[i]));
+                if (precision == SPIN_FP64) g_btile.erase(orders[i]);
+            }
             g_bleaf_gen++;
         }
         for (int i = 0; i < count; i++) {

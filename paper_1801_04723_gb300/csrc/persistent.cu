@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(NT, 2) persistent_batch_kernel(PersistentArgs 
         }
         __syncthreads();
         if (s_stage < 0) break;
+        const long long clk0 = (tid == 0 && p.bucket_clocks != nullptr) ? clock64() : 0;
         const int z = s_z;
         int32_t* info = p.records + (int64_t)z * INFO_WORDS;
         if (s_skip) {
@@ -253,7 +254,11 @@ __global__ void __launch_bounds__(NT, 2) persistent_batch_kernel(PersistentArgs 
         // the task's writes are visible device-wide before it counts as finished
         __threadfence();
         __syncthreads();
-        if (tid == 0) atomicAdd(p.done + z, 1u);
+        if (tid == 0) {
+            atomicAdd(p.done + z, 1u);
+            if (p.bucket_clocks != nullptr)
+                atomicAdd(p.bucket_clocks + s_st.bucket, (unsigned long long)(clock64() - clk0));
+        }
     }
 }
 

@@ -31,6 +31,8 @@ struct PStage {
     int32_t tiles;       // tasks per matrix (leaf: 1)
     int32_t need;        // tasks of the matrix's earlier stages
     int32_t leaf_index;  // leaf: index reported with a failure
+    int32_t bucket;      // index of the bucket (per-bucket clock counters)
+    int32_t pad;
     int64_t m, n, k;
     double alpha, beta;
     PView a, b, c, d;
@@ -55,6 +57,7 @@ struct PersistentArgs {
     unsigned long long* next;  // task counter (zero before the launch)
     int* err;                // SPIN_ERR_TIMEOUT once a dependency wait ran out (zero before the launch)
     uint64_t limit_ns;       // bound of one dependency wait
+    unsigned long long* bucket_clocks;  // optional: SM clocks spent on each bucket's tasks (autotuner)
 };
 
 // Dynamic shared memory of the kernel for leaves up to max_leaf.

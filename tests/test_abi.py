@@ -119,6 +119,16 @@ def test_invalid_arguments_rejected_on_host(L):
     assert L.spin_test_persistent_timeout(0.0, ctypes.byref(s0), ctypes.byref(s1)) == 1
     assert L.spin_test_persistent_timeout(5000.0, ctypes.byref(s0), ctypes.byref(s1)) == 1
     assert L.spin_test_persistent_timeout(50.0, None, ctypes.byref(s1)) == 1
+    # persistent autotuner: a leaf above 64, a tile that is not 16, 32 or 64, no candidates
+    orders = (ctypes.c_int64 * 2)(64, 128)
+    lo, to, ms = (ctypes.c_int * 2)(), (ctypes.c_int * 2)(), (ctypes.c_double * 2)()
+    for leaves, tiles in (((65,), (64,)), ((32,), (48,)), ((0,), (64,))):
+        la = (ctypes.c_int * 1)(*leaves)
+        ta = (ctypes.c_int * 1)(*tiles)
+        assert L.spin_autotune_batched_persistent(orders, 2, la, 1, ta, 1, lo, to, ms, None) == 1
+    la = (ctypes.c_int * 1)(32)
+    ta = (ctypes.c_int * 1)(64)
+    assert L.spin_autotune_batched_persistent(orders, 2, la, 0, ta, 1, lo, to, ms, None) == 1
 
 
 def test_pretransform_workspace(L):

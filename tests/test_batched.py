@@ -270,3 +270,30 @@ def test_batch_persistent_wait_timeout(spin):
     assert info.cpu().tolist() == [0, 0]
     for a, x in zip(mats, Xs):
         check(a, x.cpu().numpy(), persistent_leaf(a.shape[0]))
+
+
+def test_batch_persistent_autotuner(spin):
+    """The persistent schedule's autotuner picks, per order bucket, a leaf
+    and a largest product tile among the candidates; a plain batch with leaf
+    0 then runs every bucket with them (bitwise the results of that leaf
+    given explicitly: the tile never changes a bit), until forgotten."""
+    orders = [64] * 6 + [300] * 3 + [1024] * 2
+    try:
+        rec = spin.autotune_batched_persistent(orders, leaves=(32, 64), tiles=(64, 32, 16))
+        for o in set(orders):
+            leaf, tile, ms = rec[o]
+            assert leaf in {min(c, o) for c in (32, 64)} and tile in (16, 32, 64) and ms > 0.0
+        As = [inputs.sdd(o, seed=inputs.SEED_BASE + 900 + i) for i, o in enumerate(orders)]
+        dev = [torch.from_numpy(a).cuda() for a in As]
+        X0, info = spin.invert_batched(dev, leaf=0, schedule="persistent")
+        assert int(info.abs().sum()) == 0
+        for o in set(orders):
+            idx = [i for i, v in enumerate(orders) if v == o]
+            X1, info1 = spin.invert_batched([dev[i] for i in idx], leaf=rec[o][0], schedule="lockstep")
+            assert int(info1.abs().sum()) == 0
+            for i, x in zip(idx, X1):
+                assert torch.equal(X0[i], x)
+        for i in (0, 6, 9):
+            check(As[i], X0[i].cpu().numpy(), rec[orders[i]][0])
+    finally:
+        spin.autotune_batched_leaf(sorted(set(orders)), "fp64", candidates=())
