@@ -1141,7 +1141,7 @@ def run_gemm_probe(args):
     B = inputs.sdd_device(n, SEED_BASE + 12, "cuda")
     D = torch.empty_like(A)
     out = {"probe": "tensor-core products", "n": n,
-           "variant": {k: os.environ.get(k, "") for k in ("SPIN_TC_WIDE", "SPIN_TC_PAIR")}}
+           "variant": {k: os.environ.get(k, "") for k in ("SPIN_TC_WIDE", "SPIN_TC_PAIR", "SPIN_TC_PERSIST")}}
     for name, fn, pairs in (("ozaki6", lambda: spin.gemm_ozaki(A, B, slices=6, out=D), 21),
                             ("bf16x3", lambda: spin.gemm_bf16x3(A, B, out=D), 3)):
         fn()  # warm

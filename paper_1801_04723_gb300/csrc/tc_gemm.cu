@@ -25,7 +25,8 @@
 //       128 x 128 tile needs that whole rate to keep up with the MMAs, and the
 //       kernel measured 970 against 1265 TFLOP/s (n = 32768 residual).
 //
-// Kernel (tc_gemm_kernel): one CTA per output tile, warp-specialised:
+// Kernel (tc_gemm_kernel): one CTA per output tile (float mode: one CTA per
+// SM looping over the tiles, see use_persistent_tiles), warp-specialised:
 //   warp 0      TMA producer (one lane): a ~192 KB ring of BF16 operand
 //               stages, 128-byte swizzled, mbarrier complete_tx.  Float mode:
 //               128 x 256 tiles, 4 stages of one 64-wide k-block; exact mode:
@@ -187,7 +188,7 @@ template <int BN, int HALF, bool PAIR, bool TMEM_SUMS = true, int DRAIN = 32>
 __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl* ctl, volatile int* abort,
                                                  uint32_t lane_addr, int half, int grow, int col0,
                                                  int nchunks_per_pair, int lane, uint32_t tempty_c0,
-                                                 uint32_t tempty_c1, int z) {
+                                                 uint32_t tempty_c1, int z, int& chunk) {
     const bool row_ok = grow < p.M;
     // the sum of squares covers the leading sum_order x sum_order block only
     const int so = p.sum_order ? p.sum_order[z] : 0x7fffffff;
@@ -200,7 +201,7 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
     int acc[HALF];
 #pragma unroll
     for (int j = 0; j < HALF; j++) acc[j] = 0;
-    int chunk = 0, since_flush = 0;
+    int since_flush = 0;
     bool first_flush = true, ok = true;
     const int* col_exp = p.col_exp ? p.col_exp + (p.batch ? (int64_t)z * p.N : 0) : nullptr;
     const int erow = (p.row_exp && row_ok) ? p.row_exp[(p.batch ? (int64_t)z * p.M : 0) + grow] : 0;
@@ -320,13 +321,18 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
     return sumsq;
 }
 
-template <int BN, bool EXACT, int EPI_WARPS>
+// PERSIST: one CTA per SM walks the output tiles of every problem
+// (t = blockIdx.x, blockIdx.x + gridDim.x, ...), so that the epilogue of
+// one tile overlaps the MMAs of the next in the other TMEM accumulator and
+// the set-up (barriers, TMEM, tensor maps) is paid once per SM; otherwise
+// one CTA per tile (blockIdx.x) and problem (blockIdx.y).
+template <int BN, bool EXACT, int EPI_WARPS, bool PERSIST = false>
 __global__ void __maxnreg__(Epi<EPI_WARPS>::MAXREG)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const TcGemmParams p) {
     // a problem switched off by its active flag does nothing (every thread
     // of the CTA reads the same flag, before any barrier or TMEM is set up)
-    if (p.active != nullptr && p.active[p.batch ? blockIdx.y : 0] == 0) return;
+    if (!PERSIST && p.active != nullptr && p.active[p.batch ? blockIdx.y : 0] == 0) return;
     // k-blocks per stage (256-wide exact tiles: one, for a 4-stage ring)
     constexpr int KS = EXACT ? (BN >= 256 ? 1 : KSUB_EXACT) : KSUB_FLOAT;
     // exact mode keeps the FP64 running sums in TMEM when they fit beside the
@@ -348,22 +354,33 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     SmemCtl* ctl = reinterpret_cast<SmemCtl*>(base + STAGES * STAGE_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int z = p.batch ? (int)blockIdx.y : 0;  // problem of a batched launch
-    // Grouped rasterisation: consecutive CTAs sweep a band of GROUP_M row
-    // blocks column by column, so the CTAs resident at one time share a few
-    // B column blocks and a few A row blocks (L2 reuse) instead of streaming
-    // every B block once per row block.
-    int m0, n0;
-    {
-        const int num_m = (p.M + BM - 1) / BM, num_n = (p.N + BN - 1) / BN;
-        const int pid = blockIdx.x;
+    // Tiles: t = z * tiles_pp + pid (problem z of a batched launch, tile pid
+    // of it).  Grouped rasterisation: consecutive tiles sweep a band of
+    // GROUP_M row blocks column by column, so the CTAs resident at one time
+    // share a few B column blocks and a few A row blocks (L2 reuse) instead
+    // of streaming every B block once per row block.
+    const int num_m = (p.M + BM - 1) / BM, num_n = (p.N + BN - 1) / BN;
+    const int64_t tiles_pp = (int64_t)num_m * num_n;
+    const int64_t t_end = PERSIST ? tiles_pp * (p.batch ? p.batch : 1) : 1;
+    const int64_t t_first = PERSIST ? (int64_t)blockIdx.x : 0, t_step = PERSIST ? (int64_t)gridDim.x : 1;
+    // tile t: problem z, origin (m0, n0); false if its problem is switched off
+    auto tile_of = [&](int64_t t, int& z, int& m0, int& n0) -> bool {
+        int pid;
+        if (PERSIST) {
+            z = p.batch ? (int)(t / tiles_pp) : 0;
+            pid = (int)(t - (int64_t)z * tiles_pp);
+        } else {
+            z = p.batch ? (int)blockIdx.y : 0;
+            pid = (int)blockIdx.x;
+        }
         const int per_group = GROUP_M * num_n;
         const int first_m = (pid / per_group) * GROUP_M;
         const int gsize = min(num_m - first_m, GROUP_M);
         const int in_group = pid % per_group;
         m0 = (first_m + in_group % gsize) * BM;
         n0 = (in_group / gsize) * BN;
-    }
+        return !(PERSIST && p.active != nullptr && p.active[z] == 0);
+    };
     const int KB = (p.K + BK - 1) / BK;
     const int chunk_kb = EXACT ? p.chunk_kb : KB;
     const int nchunks_per_pair = (KB + chunk_kb - 1) / chunk_kb;
@@ -398,6 +415,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (lane == 0) {
             int it = 0;
             bool ok = true;
+            int z = 0, m0 = 0, n0 = 0;
             // one stage = k-blocks kb .. kb + KS - 1 of one slice pair (past K: zero fill)
             auto issue = [&](int pair, int kb) -> bool {
                 const int s = it % STAGES;
@@ -414,15 +432,18 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 it++;
                 return true;
             };
-            if (!EXACT) {
-                for (int kb = 0; kb < KB && ok; kb += KS)
-                    for (int q = 0; q < p.num_pairs && ok; q++) ok = issue(q, kb);
-            } else {
-                for (int q = 0; q < p.num_pairs && ok; q++)
-                    for (int c = 0; c < nchunks_per_pair && ok; c++) {
-                        const int kb1 = min(KB, (c + 1) * chunk_kb);
-                        for (int kb = c * chunk_kb; kb < kb1 && ok; kb += KS) ok = issue(q, kb);
-                    }
+            for (int64_t t = t_first; t < t_end && ok; t += t_step) {
+                if (!tile_of(t, z, m0, n0)) continue;
+                if (!EXACT) {
+                    for (int kb = 0; kb < KB && ok; kb += KS)
+                        for (int q = 0; q < p.num_pairs && ok; q++) ok = issue(q, kb);
+                } else {
+                    for (int q = 0; q < p.num_pairs && ok; q++)
+                        for (int c = 0; c < nchunks_per_pair && ok; c++) {
+                            const int kb1 = min(KB, (c + 1) * chunk_kb);
+                            for (int kb = c * chunk_kb; kb < kb1 && ok; kb += KS) ok = issue(q, kb);
+                        }
+                }
             }
             if (!ok) raise_timeout(ctl, p.err);
             // own copies still in flight: the last min(STAGES, it) loads
@@ -467,25 +488,31 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 tc_fence_after();
                 return true;
             };
-            if (!EXACT) {
-                int buf = 0;
-                ok = begin_chunk(buf);
-                const uint32_t d = tmem_base + (uint32_t)(buf * BN);
-                for (int kb = 0; kb < KB && ok; kb += KS)
-                    for (int q = 0; q < p.num_pairs && ok; q++) ok = consume(d, kb == 0 && q == 0, min(KS, KB - kb));
-                if (ok) mma_commit(&ctl->tfull[buf]);
-                chunk++;
-            } else {
-                for (int q = 0; q < p.num_pairs && ok; q++)
-                    for (int c = 0; c < nchunks_per_pair && ok; c++) {
-                        int buf = 0;
-                        ok = begin_chunk(buf);
-                        const uint32_t d = tmem_base + (uint32_t)(buf * BN);
-                        const int kb0 = c * chunk_kb, kb1 = min(KB, (c + 1) * chunk_kb);
-                        for (int kb = kb0; kb < kb1 && ok; kb += KS) ok = consume(d, kb == kb0, min(KS, kb1 - kb));
-                        if (ok) mma_commit(&ctl->tfull[buf]);
-                        chunk++;
-                    }
+            int z = 0, m0 = 0, n0 = 0;
+            for (int64_t t = t_first; t < t_end && ok; t += t_step) {
+                if (!tile_of(t, z, m0, n0)) continue;
+                if (!EXACT) {
+                    int buf = 0;
+                    ok = begin_chunk(buf);
+                    const uint32_t d = tmem_base + (uint32_t)(buf * BN);
+                    for (int kb = 0; kb < KB && ok; kb += KS)
+                        for (int q = 0; q < p.num_pairs && ok; q++)
+                            ok = consume(d, kb == 0 && q == 0, min(KS, KB - kb));
+                    if (ok) mma_commit(&ctl->tfull[buf]);
+                    chunk++;
+                } else {
+                    for (int q = 0; q < p.num_pairs && ok; q++)
+                        for (int c = 0; c < nchunks_per_pair && ok; c++) {
+                            int buf = 0;
+                            ok = begin_chunk(buf);
+                            const uint32_t d = tmem_base + (uint32_t)(buf * BN);
+                            const int kb0 = c * chunk_kb, kb1 = min(KB, (c + 1) * chunk_kb);
+                            for (int kb = kb0; kb < kb1 && ok; kb += KS)
+                                ok = consume(d, kb == kb0, min(KS, kb1 - kb));
+                            if (ok) mma_commit(&ctl->tfull[buf]);
+                            chunk++;
+                        }
+                }
             }
             if (!ok) raise_timeout(ctl, p.err);
             // every MMA issued so far has completed once final_bar flips
@@ -500,51 +527,59 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int quarter = warp & 3;   // TMEM lane quarter this warp may access
         const int half = e >> 2;        // column group of the tile
         const int row = quarter * 32 + lane;
-        const int grow = m0 + row;
-        const bool row_ok = grow < p.M;
         const uint32_t lane_addr = tmem_base + ((uint32_t)(quarter * 32) << 16);
-        const int col0 = n0 + half * HALF;
-        double sumsq = 0.0;
-
-        if (!EXACT) {
-            const int so = p.sum_order ? p.sum_order[z] : 0x7fffffff;
-            bool ok = mbar_wait(&ctl->tfull[0], 0u, abort, WAIT_LIMIT_NS);
-            if (!ok) raise_timeout(ctl, p.err);
-            tc_fence_after();
-            if (ok) {
+        int chunk = 0;  // accumulator uses so far (buffer chunk & 1, parity (chunk >> 1) & 1)
+        int z = 0, m0 = 0, n0 = 0;
+        for (int64_t t = t_first; t < t_end; t += t_step) {
+            if (*abort) break;
+            if (!tile_of(t, z, m0, n0)) continue;
+            const int grow = m0 + row;
+            const bool row_ok = grow < p.M;
+            const int col0 = n0 + half * HALF;
+            double sumsq = 0.0;
+            if (!EXACT) {
+                const int so = p.sum_order ? p.sum_order[z] : 0x7fffffff;
+                const int buf = chunk & 1;
+                bool ok = mbar_wait(&ctl->tfull[buf], (uint32_t)((chunk >> 1) & 1), abort, WAIT_LIMIT_NS);
+                if (!ok) raise_timeout(ctl, p.err);
+                tc_fence_after();
+                if (ok) {
 #pragma unroll 1
-                for (int cc = 0; cc < HALF; cc += 16) {
-                    uint32_t v[16];
-                    tmem_ld_32x32b_x16(lane_addr + (uint32_t)(half * HALF + cc), v);
-                    tmem_ld_wait();
-                    if (row_ok) {
-                        const double* crow = in_row(p, z, grow);
-                        double* drow = out_row(p, z, grow);
+                    for (int cc = 0; cc < HALF; cc += 16) {
+                        uint32_t v[16];
+                        tmem_ld_32x32b_x16(lane_addr + (uint32_t)(buf * BN + half * HALF + cc), v);
+                        tmem_ld_wait();
+                        if (row_ok) {
+                            const double* crow = in_row(p, z, grow);
+                            double* drow = out_row(p, z, grow);
 #pragma unroll
-                        for (int j = 0; j < 16; j++) {
-                            const int gcol = col0 + cc + j;
-                            if (gcol < p.N) {
-                                double val = p.alpha * (double)__uint_as_float(v[j]);
-                                if (p.beta != 0.0) val = fma(p.beta, crow[gcol], val);
-                                if (p.add_identity && gcol == grow) val += 1.0;
-                                drow[gcol] = val;
-                                if (grow < so && gcol < so) sumsq = fma(val, val, sumsq);
+                            for (int j = 0; j < 16; j++) {
+                                const int gcol = col0 + cc + j;
+                                if (gcol < p.N) {
+                                    double val = p.alpha * (double)__uint_as_float(v[j]);
+                                    if (p.beta != 0.0) val = fma(p.beta, crow[gcol], val);
+                                    if (p.add_identity && gcol == grow) val += 1.0;
+                                    drow[gcol] = val;
+                                    if (grow < so && gcol < so) sumsq = fma(val, val, sumsq);
+                                }
                             }
                         }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ctl->tempty[buf]);
+                chunk++;
+                if (!ok) break;
+            } else {
+                sumsq = exact_epilogue<BN, HALF, false, TMEM_SUMS, (EPI_WARPS >= 16 ? 16 : 32)>(
+                    p, ctl, abort, lane_addr, half, grow, col0, nchunks_per_pair, lane, 0u, 0u, z, chunk);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl->tempty[0]);
-        } else {
-            sumsq = exact_epilogue<BN, HALF, false, TMEM_SUMS, (EPI_WARPS >= 16 ? 16 : 32)>(
-                p, ctl, abort, lane_addr, half, grow, col0, nchunks_per_pair, lane, 0u, 0u, z);
-        }
-        if (p.sumsq) {
+            if (p.sumsq) {
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) sumsq += __shfl_down_sync(0xffffffffu, sumsq, off);
-            if (lane == 0 && sumsq != 0.0) atomicAdd(p.sumsq + (p.batch ? z : 0), sumsq);
+                for (int off = 16; off > 0; off >>= 1) sumsq += __shfl_down_sync(0xffffffffu, sumsq, off);
+                if (lane == 0 && sumsq != 0.0) atomicAdd(p.sumsq + (p.batch ? z : 0), sumsq);
+            }
         }
     }
 
@@ -728,9 +763,10 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         const int half = e >> 2;
         const int grow = my_m0 + quarter * 32 + lane;
         const uint32_t lane_addr = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        int chunk = 0;
         double sumsq = exact_epilogue<PBN, HALF, true, C::TMEM_SUMS, (EPI_WARPS >= 16 ? 16 : 32)>(
             p, ctl, abort, lane_addr, half, grow, n0 + half * HALF, nchunks_per_pair, lane,
-            mapa_u32(smem_u32(&ctl->tempty[0]), 0u), mapa_u32(smem_u32(&ctl->tempty[1]), 0u), z);
+            mapa_u32(smem_u32(&ctl->tempty[0]), 0u), mapa_u32(smem_u32(&ctl->tempty[1]), 0u), z, chunk);
         if (p.sumsq) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) sumsq += __shfl_down_sync(0xffffffffu, sumsq, off);
@@ -1109,6 +1145,39 @@ int make_map(CUtensorMap* m, const uint16_t* base, int64_t inner, int64_t outer,
     return r == CUDA_SUCCESS ? SPIN_OK : SPIN_ERR_CUDA;
 }
 
+// Float-mode products (bf16x3, bf16x6) run on persistent CTAs, one per SM
+// looping over the tiles: a float tile drains its one accumulator after its
+// last MMA, which the next tile's MMAs now overlap (n = 8192 bf16x3: 2.51
+// against 2.86 ms).  Exact-mode tiles already overlap their many runs'
+// drains within the tile and measured the same or 1 % slower persistent
+// (n = 8192: 19.49 and 19.30 against 19.31 and 19.34 ms), so they keep one
+// CTA per tile.  At n = 32768 the mixed inversion's level products went from
+// 1314 to 1356 TFLOP/s and its update from 1499 to 1603 (3.18 -> 3.15 s).
+// SPIN_TC_PERSIST=0 turns persistence off, =2 on for both modes (for
+// measurement); read once.
+int persistent_tiles_mode() {
+    static const int v = [] {
+        const char* e = getenv("SPIN_TC_PERSIST");
+        if (e && e[0] == '0') return 0;
+        if (e && e[0] == '2') return 2;
+        return 1;
+    }();
+    return v;
+}
+bool use_persistent_tiles(bool exact) {
+    const int m = persistent_tiles_mode();
+    return m == 2 || (m == 1 && !exact);
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 152;
+    }
+    return n > 0 ? n : 152;
+}
+
 template <int BN, bool EXACT, int EPI_WARPS>
 int launch_impl(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, cudaStream_t s) {
     CUtensorMap ta, tb;
@@ -1117,18 +1186,26 @@ int launch_impl(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, c
     if (rc) return rc;
     rc = make_map(&tb, b.base, p.K, (int64_t)b.rows * b.slices * nz, b.ld, BN);
     if (rc) return rc;
+    constexpr size_t smem = Cfg<BN, EXACT ? (BN >= 256 ? 1 : KSUB_EXACT) : KSUB_FLOAT>::SMEM_BYTES;
     static PerDeviceOnce attrs;
-    auto kern = tc_gemm_kernel<BN, EXACT, EPI_WARPS>;
+    auto kern = tc_gemm_kernel<BN, EXACT, EPI_WARPS, false>;
+    auto kern_p = tc_gemm_kernel<BN, EXACT, EPI_WARPS, true>;
     rc = attrs.run([&]() -> int {
-        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)Cfg<BN, EXACT ? (BN >= 256 ? 1 : KSUB_EXACT) : KSUB_FLOAT>::SMEM_BYTES));
+        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         return SPIN_OK;
     });
     if (rc) return rc;
     const int64_t tiles = (int64_t)((p.N + BN - 1) / BN) * ((p.M + BM - 1) / BM);
     if (tiles > INT32_MAX) return SPIN_ERR_INVALID_ARG;
-    kern<<<dim3((unsigned)tiles, (unsigned)nz), Epi<EPI_WARPS>::THREADS,
-           Cfg<BN, EXACT ? (BN >= 256 ? 1 : KSUB_EXACT) : KSUB_FLOAT>::SMEM_BYTES, s>>>(ta, tb, p);
+    if (use_persistent_tiles(EXACT)) {
+        // one CTA per SM (the ring takes most of the shared memory), each
+        // walking every gridDim.x-th tile of all problems
+        const int64_t grid = std::min<int64_t>(tiles * nz, sm_count());
+        kern_p<<<dim3((unsigned)grid, 1), Epi<EPI_WARPS>::THREADS, smem, s>>>(ta, tb, p);
+    } else {
+        kern<<<dim3((unsigned)tiles, (unsigned)nz), Epi<EPI_WARPS>::THREADS, smem, s>>>(ta, tb, p);
+    }
     SPIN_CUDA_TRY(cudaGetLastError());
     return SPIN_OK;
 }
