@@ -36,8 +36,11 @@ sys.path.insert(0, ROOT)
 METRIC = "2n³/t TFLOP/s vs FP64/BF16 peak at residual ≤1e-10; served req/s with p50/p99"
 T_START = time.perf_counter()
 # The batched and serving sub-records of the default run start only before
-# this many seconds (the driver's limit for the whole run is 1800 s).
-SUBRECORD_DEADLINE_S = 1540.0
+# these many seconds of run time (the limit for the whole run is 1800 s; the
+# batched sub-record takes about 35 s, the serving one about 25 s, and the
+# serving run aborts after 60 s without progress).
+BATCHED_DEADLINE_S = 1600.0
+SERVE_DEADLINE_S = 1650.0
 
 SEED_BASE = 0x5EED0000
 
@@ -664,27 +667,40 @@ def run_ours(args, w: dict, n: int, leaf: int):
     mixed = batched = served = None
     # seconds since the start of the process at the end of each phase
     timeline = {"plain_s": time.perf_counter() - T_START}
+    # A sub-record that fails is reported as such; the plain line (measured
+    # above) is printed either way.
+    def guarded(fn):
+        try:
+            return fn()
+        except Exception as e:  # noqa: BLE001 -- reported in the line
+            print(f"[bench] sub-record failed: {e!r}", file=sys.stderr, flush=True)
+            return {"error": repr(e)[:400]}
+
     if args.workload == "plain_fp64" and not args.no_mixed:
-        mixed = mixed_subrecord(args, spin, work, n, ms, device, stream, barrier, local, world, peak_fp64)
+        mixed = guarded(lambda: mixed_subrecord(args, spin, work, n, ms, device, stream, barrier, local, world,
+                                                peak_fp64))
         timeline["mixed_s"] = time.perf_counter() - T_START
     # the batching and serving forms, while the run stays well inside its
     # time limit (the plain steps take most of it)
     if args.workload == "plain_fp64" and not args.no_batched and world == 1:
-        if time.perf_counter() - T_START < SUBRECORD_DEADLINE_S:
-            batched = batched_subrecord(args, spin, device, stream, barrier, local, world, peak_fp64)
+        if time.perf_counter() - T_START < BATCHED_DEADLINE_S:
+            batched = guarded(lambda: batched_subrecord(args, spin, device, stream, barrier, local, world,
+                                                        peak_fp64))
             timeline["batched_s"] = time.perf_counter() - T_START
         else:
-            batched = {"skipped": f"run time above {SUBRECORD_DEADLINE_S:.0f} s"}
+            batched = {"skipped": f"run time above {BATCHED_DEADLINE_S:.0f} s"}
     if args.workload == "plain_fp64" and not args.no_serve and world == 1:
-        if time.perf_counter() - T_START < SUBRECORD_DEADLINE_S:
-            sargs = argparse.Namespace(**vars(args))
-            sargs.serve_seconds = args.serve_sub_seconds
-            served = run_serve(sargs, dict(WORKLOADS["serve"]), sub=True)
-            served = {k: v for k, v in served.items()
-                      if k not in ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data")}
+        if time.perf_counter() - T_START < SERVE_DEADLINE_S:
+            def serve_sub():
+                sargs = argparse.Namespace(**vars(args))
+                sargs.serve_seconds = args.serve_sub_seconds
+                out = run_serve(sargs, dict(WORKLOADS["serve"]), sub=True)
+                return {k: v for k, v in out.items()
+                        if k not in ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data")}
+            served = guarded(serve_sub)
             timeline["serve_s"] = time.perf_counter() - T_START
         else:
-            served = {"skipped": f"run time above {SUBRECORD_DEADLINE_S:.0f} s"}
+            served = {"skipped": f"run time above {SERVE_DEADLINE_S:.0f} s"}
 
     if rank != 0:
         if world > 1:
@@ -746,7 +762,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
         "cold": {"first_call_ms": e2e_times[0] * 1e3 if e2e_times else None,
                  "how": "the first end-to-end call of the process: workspace allocation, module load and "
                         "copies included"},
-        "gpu_launches": work.launches(recs, args.steps) + (mixed["gpu_launches"] if mixed else 0)
+        "gpu_launches": work.launches(recs, args.steps) + (mixed.get("gpu_launches", 0) if mixed else 0)
         + sum(batched[k]["gpu_launches"] for k in ("batched_fp64", "batched_mixed") if batched and k in batched),
         "roofline": roof,
         "status": info["status"],
