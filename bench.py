@@ -105,6 +105,9 @@ def parse():
                     "(at most --steps)")
     ap.add_argument("--mixed-warmup", type=int, default=2, help="plain_fp64: warm-up steps of the mixed sub-record "
                     "(at most --warmup, at least 1)")
+    ap.add_argument("--schedule", default="default", choices=["default", "lockstep", "persistent"],
+                    help="single-matrix workloads: II and C21 on a second stream where it pays (default), "
+                         "one stream (lockstep) or the second stream at every order (persistent)")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
                     help="batched workloads: matrices per batch (smaller for profiler captures)")
     ap.add_argument("--batch-schedule", default="default", choices=["default", "lockstep", "persistent"],
@@ -395,10 +398,11 @@ def oracle_size_sweep(w: dict, sizes: list) -> list:
 class SingleWork:
     """One matrix per rank: spin_invert_ex on a device-resident input."""
 
-    def __init__(self, spin, w, n, leaf, device, pretransform=0, fp64_levels=2):
+    def __init__(self, spin, w, n, leaf, device, pretransform=0, fp64_levels=2, schedule="default"):
         import torch
 
         self.spin, self.w, self.n, self.leaf = spin, w, n, leaf
+        self.schedule = schedule
         self.pt = pretransform
         self.fl = fp64_levels
         self.A, self.known = make_input(w, n, device)
@@ -411,7 +415,7 @@ class SingleWork:
 
     def step(self):
         self.spin.invert(self.A, leaf=self.leaf, precision=self.w["precision"], out=self.X, blocking=False,
-                         pretransform=self.pt, rbt_seed=SEED_BASE + 5, fp64_levels=self.fl)
+                         pretransform=self.pt, rbt_seed=SEED_BASE + 5, fp64_levels=self.fl, schedule=self.schedule)
 
     def launches(self, recs, steps):
         return len(recs)
@@ -421,7 +425,7 @@ class SingleWork:
 
     def e2e_step(self):
         self.spin.invert_host(self.Ah.numpy(), leaf=self.leaf, precision=self.w["precision"], out=self.Xh.numpy(),
-                              pretransform=self.pt, rbt_seed=SEED_BASE + 5)
+                              pretransform=self.pt, rbt_seed=SEED_BASE + 5, schedule=self.schedule)
 
     def accuracy(self, probes):
         out = {"rel_residual_est": freivalds_rel(self.A, self.X, probes, SEED_BASE + 77) if probes > 0 else None}
@@ -646,7 +650,7 @@ def run_ours(args, w: dict, n: int, leaf: int):
     if w["family"] == "batch_sdd":
         work = BatchWork(spin, w, n, leaf, device, args.batch_count, args.batch_schedule)
     else:
-        work = SingleWork(spin, w, n, leaf, device, args.pretransform, args.fp64_levels)
+        work = SingleWork(spin, w, n, leaf, device, args.pretransform, args.fp64_levels, args.schedule)
     stream = torch.cuda.current_stream()
     flops = work.flops
 

@@ -105,15 +105,23 @@ typedef struct spin_opts {
                                     to a multiple of 4); the mixed modes then refine X against A;
                                   2 the plain recursion first, and on a zero or non-finite pivot
                                     the transform (the call then waits for the first attempt)  */
-    int32_t schedule;          /* spin_invert_batched, plain form (spin_batch_schedule):
-                                  0 (default) the persistent kernel -- one launch that walks a
-                                  device-side task list -- unless leaf > 64; 1 lockstep
-                                  launches per order bucket on a pool of streams; 2 the
-                                  persistent kernel (leaf > 64 refused).  The persistent
-                                  kernel inverts leaves of order <= 64 on one CTA each: a
-                                  larger leaf chosen by the library (n for n <= 128, or an
-                                  autotuned one) becomes 64.  Ignored by the other calls and
-                                  by the mixed form                                          */
+    int32_t schedule;          /* launch schedule (spin_batch_schedule).
+                                  spin_invert_batched, plain form: 0 (default) the persistent
+                                  kernel -- one launch that walks a device-side task list --
+                                  unless leaf > 64; 1 lockstep launches per order bucket on a
+                                  pool of streams; 2 the persistent kernel (leaf > 64 refused).
+                                  The persistent kernel inverts leaves of order <= 64 on one
+                                  CTA each: a larger leaf chosen by the library (n for
+                                  n <= 128, or an autotuned one) becomes 64.  The mixed batch
+                                  ignores it.
+                                  spin_invert_ex and the calls built on it: 0 (default) each
+                                  level's II = A21 I and C21 run on a second stream beside the
+                                  recursion on S up to order 8192 (plain) or 16384 (mixed);
+                                  1 one stream, in Algorithm 1's order; 2 the second stream at
+                                  every order.  The same products on the same operands either
+                                  way, so the same results bit for bit; the second stream
+                                  needs II's slab and (mixed) a second split arena in the
+                                  workspace (spin_workspace_bytes takes the schedule)        */
     uint64_t rbt_seed;         /* seed of the butterflies' random diagonals (splitmix64)      */
 } spin_opts;
 

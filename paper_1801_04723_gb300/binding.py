@@ -273,7 +273,7 @@ def make_opts(precision="fp64", leaf=0, tol=1e-10, max_refine=6, fp64_levels=2, 
 
 def invert(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e-10, max_refine: int = 6,
            fp64_levels: int = 2, stream=None, check: bool = True, workspace=None, blocking: bool = True,
-           residual_slices: int = 0, pretransform: int = 0, rbt_seed: int = 0):
+           residual_slices: int = 0, pretransform: int = 0, rbt_seed: int = 0, schedule="default"):
     """X = A^-1 on the device (spin_invert_ex).  Returns (X, info dict).
 
     With ``blocking=False`` the call only enqueues the work on the stream and
@@ -289,7 +289,7 @@ def invert(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e-10, 
     X = out if out is not None else torch.empty((n, n), dtype=torch.float64, device=A.device)
     _check_matrix(X, "X")
     o = make_opts(precision, leaf, tol, max_refine, fp64_levels, blocking, workspace, residual_slices,
-                  pretransform, rbt_seed)
+                  pretransform, rbt_seed, schedule)
     if not blocking:
         rc = lib().spin_invert_ex(ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(X.data_ptr()),
                                   X.stride(0), n, ctypes.byref(o), None, _stream(stream))
@@ -315,7 +315,7 @@ def sync(stream=None, check: bool = True) -> dict:
 
 
 def invert_host(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e-10, stream=None,
-                pretransform: int = 0, rbt_seed: int = 0):
+                pretransform: int = 0, rbt_seed: int = 0, schedule="default"):
     """X = A^-1 with host (numpy or CPU torch, float64, C-contiguous) buffers."""
     import numpy as np
 
@@ -325,7 +325,7 @@ def invert_host(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e
         out = np.empty((n, n), dtype=np.float64)
     pa = A.ctypes.data if isinstance(A, np.ndarray) else A.data_ptr()
     px = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
-    o = make_opts(precision, leaf, tol, pretransform=pretransform, rbt_seed=rbt_seed)
+    o = make_opts(precision, leaf, tol, pretransform=pretransform, rbt_seed=rbt_seed, schedule=schedule)
     info = Info()
     rc = lib().spin_invert_host(ctypes.c_void_p(pa), n, ctypes.c_void_p(px), n, n, ctypes.byref(o),
                                 ctypes.byref(info), _stream(stream))
@@ -335,9 +335,9 @@ def invert_host(A, *, leaf: int = 0, precision="fp64", out=None, tol: float = 1e
 
 
 def workspace_bytes(n: int, *, leaf: int = 0, precision="fp64", fp64_levels: int = 2,
-                    residual_slices: int = 0, pretransform: int = 0) -> int:
+                    residual_slices: int = 0, pretransform: int = 0, schedule="default") -> int:
     o = make_opts(precision, leaf, fp64_levels=fp64_levels, residual_slices=residual_slices,
-                  pretransform=pretransform)
+                  pretransform=pretransform, schedule=schedule)
     return int(lib().spin_workspace_bytes(int(n), ctypes.byref(o)))
 
 

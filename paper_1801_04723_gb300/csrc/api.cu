@@ -65,13 +65,19 @@ static size_t ws_fp64_elems(int64_t n, int64_t leaf, bool overlap = false) {
     return a > b ? a : b;
 }
 
-// The plain method runs II = A21 I on a second stream, beside the recursion
-// on S (which depends only on III = I A12), for problems up to this order:
-// there the leaves (one cluster of at most 16 SMs) and the small products
-// leave SMs idle.  Above it the products fill the GPU and the schedule stays
-// sequential.
-constexpr int64_t kOverlapMaxN = 8192;
-bool overlap_schedule(int64_t n, int precision) { return precision == SPIN_FP64 && n <= kOverlapMaxN; }
+// II = A21 I runs on a second stream, beside the recursion on S (which
+// depends only on III = I A12), for problems up to these orders: there the
+// leaves (one cluster of at most 16 SMs) and the small products leave SMs
+// idle.  Above them the products fill the GPU and the schedule stays on one
+// stream.  spin_opts.schedule 1 keeps every order on one stream, 2 takes
+// the second stream at every order.
+constexpr int64_t kOverlapMaxN = 8192;        // plain method
+constexpr int64_t kOverlapMaxNMixed = 16384;  // mixed forms
+bool overlap_schedule(int64_t n, int precision, int schedule) {
+    if (schedule == SPIN_SCHEDULE_LOCKSTEP) return false;
+    if (schedule == SPIN_SCHEDULE_PERSISTENT) return true;
+    return n <= (precision == SPIN_FP64 ? kOverlapMaxN : kOverlapMaxNMixed);
+}
 
 namespace {
 
@@ -178,7 +184,7 @@ struct Run {
     int leaf_counter;
     int64_t leaf;
     Profiler* prof;  // nullptr when not recording
-    // overlapped schedule (plain method): II on `side`, events from `events`
+    // overlapped schedule: II and C21 on `side`, events from `events`
     cudaStream_t side = nullptr;
     std::vector<cudaEvent_t>* events = nullptr;
     size_t next_event = 0;
@@ -187,6 +193,8 @@ struct Run {
     int fp64_levels = 0;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    void* side_scratch = nullptr;  // split arena of the side stream's products
+    size_t side_scratch_bytes = 0;
     int* err = nullptr;
 };
 
@@ -341,7 +349,9 @@ int inv_rec(Run& r, int depth, const double* A, int64_t lda, double* X, int64_t 
             Run rs = r;  // II alone on the side stream (a product, no recursion)
             rs.s = r.side;
             rs.side = nullptr;
-            RET(gemm_f64_prof(rs, d, n2, n1, n1, 1.0, A21, lda, X11, ldx, 0.0, nullptr, 0, II, n1));  // II
+            rs.scratch = r.side_scratch;
+            rs.scratch_bytes = r.side_scratch_bytes;
+            RET(level_gemm(rs, d, false, n2, n1, n1, 1.0, A21, lda, X11, ldx, 0.0, nullptr, 0, II, n1));  // II
         }
         SPIN_CUDA_TRY(cudaEventRecord(e_ii, r.side));
         RET(level_gemm(r, d, false, n1, n2, n1, 1.0, X11, ldx, A12, lda, 0.0, nullptr, 0, T, n2));   // III
@@ -356,7 +366,9 @@ int inv_rec(Run& r, int depth, const double* A, int64_t lda, double* X, int64_t 
             Run rs = r;  // C21 on the side stream, after II
             rs.s = r.side;
             rs.side = nullptr;
-            RET(gemm_f64_prof(rs, d, n2, n1, n2, -1.0, X22, ldx, II, n1, 0.0, nullptr, 0, X21, ldx));  // C21
+            rs.scratch = r.side_scratch;
+            rs.scratch_bytes = r.side_scratch_bytes;
+            RET(level_gemm(rs, d, false, n2, n1, n2, -1.0, X22, ldx, II, n1, 0.0, nullptr, 0, X21, ldx));  // C21
         }
         SPIN_CUDA_TRY(cudaEventRecord(e_c21, r.side));
         RET(level_gemm(r, d, false, n1, n2, n2, -1.0, T, n2, X22, ldx, 0.0, nullptr, 0, X12, ldx)); // C12
@@ -436,6 +448,7 @@ int read_info(StreamState* st, cudaStream_t s, spin_info* info) {
 // of A for the refinement residual.
 struct MixLayout {
     size_t region0, scratch, apl, off_scratch, off_apl, off_norms, total;
+    size_t side_scratch, off_side;  // split arena of the side stream (overlapped schedule), else 0
     int sr;  // digit slices of the certifying residuals (and of A's cached planes)
     int s0;  // slices of the first residual's pairs (<= sr)
 };
@@ -450,7 +463,8 @@ MixLayout mix_layout(int64_t n, int64_t leaf, const spin_opts& o) {
     L.sr = o.residual_slices > 0 ? o.residual_slices : residual_slices_for(n, o.tol);
     L.s0 = o.residual_slices > 0 ? o.residual_slices : first_residual_slices_for(n, o.tol, L.sr);
     const size_t nn = (size_t)n * (size_t)n;
-    L.region0 = round256(std::max(ws_fp64_elems(n, leaf), nn) * sizeof(double));
+    const bool overlap = n > leaf && overlap_schedule(n, o.precision, o.schedule);
+    L.region0 = round256(std::max(ws_fp64_elems(n, leaf, overlap), nn) * sizeof(double));
     size_t sc = 0;
     if (n > leaf) {
         const int64_t n1 = split_order(n);
@@ -462,15 +476,25 @@ MixLayout mix_layout(int64_t n, int64_t leaf, const spin_opts& o) {
     sc = std::max(sc, bf16x6_scratch_bytes(n, n, n));
     L.scratch = round256(sc);
     L.apl = round256((size_t)L.sr * (size_t)n * (size_t)tc_ld(n) * 2 + (size_t)n * 4 + 512);
+    // the side stream's products (II and C21 of every level: at most n2 x n1 x n1)
+    size_t side = 0;
+    if (overlap) {
+        const int64_t n1 = split_order(n);
+        side = bf16x3_scratch_bytes(n1, n1, n1);
+        if (o.precision == SPIN_MIXED_DIGITS) side = std::max(side, ozaki_scratch_bytes(n1, n1, n1, kLevelSlices));
+    }
+    L.side_scratch = round256(side);
     L.off_scratch = L.region0;
     L.off_apl = L.off_scratch + L.scratch;
     L.off_norms = L.off_apl + L.apl;
-    L.total = L.off_norms + 256;
+    L.off_side = L.off_norms + 256;
+    L.total = L.off_side + L.side_scratch;
     return L;
 }
 
 size_t inner_bytes(int64_t n, int64_t leaf, const spin_opts& o) {
-    if (o.precision == SPIN_FP64) return ws_fp64_elems(n, leaf, overlap_schedule(n, o.precision)) * sizeof(double);
+    if (o.precision == SPIN_FP64)
+        return ws_fp64_elems(n, leaf, n > leaf && overlap_schedule(n, o.precision, o.schedule)) * sizeof(double);
     return mix_layout(n, leaf, o).total;
 }
 
@@ -594,7 +618,7 @@ int enqueue_once(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n
         inner = ws + R.off_inner;
     }
     if (!mixed) {
-        if (overlap_schedule(n_in, o.precision) && n_in > leaf) {
+        if (overlap_schedule(n_in, o.precision, o.schedule) && n_in > leaf) {
             if (st->side == nullptr) SPIN_CUDA_TRY(cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking));
             r.side = st->side;
             r.events = &st->events;
@@ -608,6 +632,13 @@ int enqueue_once(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n
     r.fp64_levels = o.fp64_levels;
     r.scratch = inner + Lin.off_scratch;
     r.scratch_bytes = Lin.scratch;
+    if (Lin.side_scratch > 0) {
+        if (st->side == nullptr) SPIN_CUDA_TRY(cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking));
+        r.side = st->side;
+        r.events = &st->events;
+        r.side_scratch = inner + Lin.off_side;
+        r.side_scratch_bytes = Lin.side_scratch;
+    }
     r.err = st->err_dev;
     SPIN_CUDA_TRY(cudaMemsetAsync(st->err_dev, 0, sizeof(int), s));
     RET(inv_rec(r, 0, Ain, lda_in, Xout, ldx_out, n_in, (double*)inner));
@@ -639,6 +670,7 @@ std::vector<uint64_t> call_key(const double* A, int64_t lda, double* X, int64_t 
     return {(uint64_t)(uintptr_t)A, (uint64_t)lda, (uint64_t)(uintptr_t)X, (uint64_t)ldx, (uint64_t)n,
             (uint64_t)leaf, (uint64_t)o.precision, bits_of(o.tol), (uint64_t)o.max_refine,
             (uint64_t)o.fp64_levels, (uint64_t)o.residual_slices, (uint64_t)o.pretransform, o.rbt_seed,
+            (uint64_t)(int64_t)o.schedule,
             (uint64_t)(uintptr_t)ws};
 }
 
@@ -681,6 +713,7 @@ int enqueue(const double* A, int64_t lda, double* X, int64_t ldx, int64_t n, con
     if (mixed && (o.residual_slices < 0 || o.residual_slices > 7 || o.max_refine < 0 || !(o.tol > 0.0)))
         return SPIN_ERR_INVALID_ARG;
     if (o.pretransform < 0 || o.pretransform > 2) return SPIN_ERR_INVALID_ARG;
+    if (o.schedule < SPIN_SCHEDULE_DEFAULT || o.schedule > SPIN_SCHEDULE_PERSISTENT) return SPIN_ERR_INVALID_ARG;
     const size_t need = workspace_bytes_for(n, leaf, o);
     unsigned char* ws;
     if (o.workspace != nullptr) {

@@ -101,3 +101,35 @@ def test_other_arguments_launch_directly(spin):
         spin.invert(A, leaf=64, out=X1 if i % 2 == 0 else X2)
     assert spin.schedule_stats()["replays"] == before
     np.testing.assert_array_equal(X1.cpu().numpy(), X2.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision,n,leaf", [("fp64", 1500, 128), ("fp64", 700, 64), ("bf16x3", 1500, 128),
+                                              ("bf16x3", 2048, 128), ("digits", 1024, 128)])
+def test_second_stream_schedule_matches_one_stream(spin, precision, n, leaf):
+    """Each level's II and C21 on a second stream (the default up to order
+    8192 plain, 16384 mixed; schedule "persistent" forces it) against the
+    one-stream order of Algorithm 1 (schedule "lockstep"): the same products
+    on the same operands, so the same inverse -- bit for bit in FP64; in the
+    mixed forms the same refinement steps and the same X up to the order of
+    the atomically summed norms that decide them."""
+    A = inputs.spd_gram_device(n, inputs.SEED_BASE + 77 + n, "cuda:0", alpha=1.0)
+    out = {}
+    for sched in ("lockstep", "default", "persistent"):
+        X, info = spin.invert(A, precision=precision, leaf=leaf, schedule=sched)
+        torch.cuda.synchronize()
+        assert info["status"] == 0
+        out[sched] = (X.cpu().numpy(), info["refine_iters"])
+        assert spin.workspace_bytes(n, leaf=leaf, precision=precision, schedule=sched) > 0
+    ref, it = out["lockstep"]
+    for sched in ("default", "persistent"):
+        x, it2 = out[sched]
+        if precision == "fp64":
+            np.testing.assert_array_equal(x, ref)
+        else:
+            assert it2 == it
+            assert np.max(np.abs(x - ref)) <= 1e-13 * np.max(np.abs(ref))
+    A_h = A.cpu().numpy()
+    assert oracle.residual(A_h, out["default"][0])[0] <= (1e-13 if precision == "fp64" else 1e-10)
+    # the second stream needs more workspace than one stream
+    assert spin.workspace_bytes(n, leaf=leaf, precision=precision, schedule="persistent") > \
+        spin.workspace_bytes(n, leaf=leaf, precision=precision, schedule="lockstep")
