@@ -38,6 +38,7 @@
 #include <cooperative_groups.h>
 #include <limits.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -606,9 +607,21 @@ size_t leaf_smem_bytes(int64_t L, int C, bool rows, bool push) {
 // so it takes the widest cluster (latency); a batch runs many leaves side
 // by side, so it takes the narrowest that fits shared memory (SM time).
 // Rows are pushed to every CTA when L <= 256 and the slots fit.
+// SPIN_LEAF_CLUSTER_MAX caps the single inversions' cluster width (1..16,
+// for measurement: a narrower cluster takes longer per leaf but holds fewer
+// SMs while other work could use them); read once.
+int leaf_cluster_cap() {
+    static const int v = [] {
+        const char* e = getenv("SPIN_LEAF_CLUSTER_MAX");
+        const int x = e ? atoi(e) : 0;
+        return (x >= 1 && x <= 16) ? x : 16;
+    }();
+    return v;
+}
+
 LeafConfig leaf_config(int64_t L, bool have_scratch, bool batched = false) {
     LeafConfig c;
-    const int cmax = max_cluster_size();
+    const int cmax = batched ? max_cluster_size() : std::min(max_cluster_size(), leaf_cluster_cap());
     const bool push_ok = L <= kPushMaxL;
     c.C = 1;
     if (batched) {
