@@ -283,6 +283,18 @@ int spin_autotune_batched_persistent(const int64_t* orders, int count, const int
                                      const int* tiles, int ntile, int* leaf_out, int* tile_out, double* ms_out,
                                      spin_stream_t stream);
 
+/* The persistent task list itself (host only, for checks of the device-side
+ * schedule): per stage, in task order, five int64 -- kind (0 leaf
+ * inversion, 1 level product), first matrix of its bucket (matrices sorted
+ * by order, stable), matrices of the bucket, tasks per matrix, and the
+ * dependency count (tasks of the matrix's earlier stages that must be done
+ * before any of this stage's tasks starts) -- written to out (5 * max_stages
+ * entries); *stages gets the stage count.  SPIN_ERR_INVALID_ARG for bad
+ * orders or leaf (as spin_batch_schedule_info), or when the list has more
+ * than max_stages stages (*stages is then set, out untouched). */
+int spin_batch_schedule_stages(const int64_t* n, int count, int leaf, int64_t* out, int64_t max_stages,
+                               int64_t* stages);
+
 /* Shape of the graph the latest spin_invert_batched on `stream` replays:
  * kernel launches per call and order buckets.  SPIN_ERR_INVALID_ARG if none. */
 int spin_batched_stats(spin_stream_t stream, int* kernels, int* buckets);

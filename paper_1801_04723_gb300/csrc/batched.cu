@@ -1170,6 +1170,48 @@ extern "C" int spin_batch_schedule_info(const int64_t* n, int count, int leaf, i
     return SPIN_OK;
 }
 
+// The persistent task list itself, for host-side checks: per stage (task
+// order) five int64 -- kind (0 leaf, 1 product), first matrix (sorted
+// order), matrices, tasks per matrix, dependency count -- into out (5 *
+// max_stages entries); *stages gets the stage count (SPIN_ERR_INVALID_ARG
+// if above max_stages, with nothing written).
+extern "C" int spin_batch_schedule_stages(const int64_t* n, int count, int leaf, int64_t* out, int64_t max_stages,
+                                          int64_t* stages) {
+    if (n == nullptr || out == nullptr || stages == nullptr || count < 1 || count > 65535 || leaf < 0 ||
+        leaf > kPersistMaxLeaf)
+        return SPIN_ERR_INVALID_ARG;
+    std::vector<int64_t> sorted(n, n + count);
+    for (int64_t v : sorted)
+        if (v < 1 || v > 65536) return SPIN_ERR_INVALID_ARG;
+    std::stable_sort(sorted.begin(), sorted.end());
+    std::vector<Bucket> buckets;
+    for (int i = 0; i < count;) {
+        int j = i;
+        while (j < count && sorted[j] == sorted[i]) j++;
+        Bucket b;
+        b.n = sorted[i];
+        b.leaf = std::min(batched_leaf(b.n, leaf, SPIN_FP64), kPersistMaxLeaf);
+        b.tile_cap = persist_tile_cap(b.n);
+        b.count = j - i;
+        b.first = i;
+        buckets.push_back(b);
+        i = j;
+    }
+    std::vector<PStage> st;
+    std::vector<int64_t> start;
+    order_stages(buckets, st, start);
+    *stages = (int64_t)st.size();
+    if ((int64_t)st.size() > max_stages) return SPIN_ERR_INVALID_ARG;
+    for (size_t i = 0; i < st.size(); i++) {
+        out[5 * i + 0] = st[i].kind;
+        out[5 * i + 1] = st[i].first;
+        out[5 * i + 2] = st[i].count;
+        out[5 * i + 3] = st[i].tiles;
+        out[5 * i + 4] = st[i].need;
+    }
+    return SPIN_OK;
+}
+
 extern "C" int spin_invert_batched(const double* const* A, const int64_t* lda, double* const* X, const int64_t* n,
                                    int count, const spin_opts* opts, int* info_dev, spin_stream_t stream) {
     if (count < 1 || A == nullptr || lda == nullptr || X == nullptr || n == nullptr) return SPIN_ERR_INVALID_ARG;

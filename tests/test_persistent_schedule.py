@@ -82,3 +82,109 @@ def test_schedule_rejects_bad_arguments(L):
     assert rc == 1
     rc, _ = info(L, [70000], 0)
     assert rc == 1
+
+
+def stages_of(L, orders, leaf):
+    arr = (ctypes.c_int64 * len(orders))(*[int(v) for v in orders])
+    cnt = ctypes.c_int64()
+    L.spin_batch_schedule_stages.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                                             ctypes.POINTER(ctypes.c_int64)]
+    probe = (ctypes.c_int64 * 5)()
+    L.spin_batch_schedule_stages(arr, len(orders), leaf, probe, 0, ctypes.byref(cnt))
+    out = (ctypes.c_int64 * (5 * cnt.value))()
+    assert L.spin_batch_schedule_stages(arr, len(orders), leaf, out, cnt.value, ctypes.byref(cnt)) == 0
+    return np.array(out, dtype=np.int64).reshape(-1, 5)
+
+
+def simulate(st, workers, seed):
+    """The persistent kernel's protocol with `workers` CTAs: each holds the
+    task it runs and the index of the next one (taken when it starts the
+    current task, before its dependency wait); a task of matrix z starts once
+    z's finished-task counter reaches its stage's dependency count.  Random
+    task durations.  Returns the finished-task counter per matrix; raises if
+    at some point no CTA can run while tasks remain (a deadlock)."""
+    import heapq
+
+    rng = np.random.default_rng(seed)
+    starts = np.concatenate([[0], np.cumsum(st[:, 2] * st[:, 3])])
+    total = int(starts[-1])
+    nmat = int((st[:, 1] + st[:, 2]).max())
+    done = np.zeros(nmat, dtype=np.int64)
+    nxt = 0
+
+    def task(t):
+        g = int(np.searchsorted(starts, t, side="right") - 1)
+        z = int(st[g, 1] + (t - starts[g]) // st[g, 3])
+        return z, int(st[g, 4])
+
+    # per worker: [current task, prefetched task]; waiting set; running heap
+    held = []
+    for _ in range(workers):
+        held.append([nxt, None])
+        nxt += 1
+    waiting = set()
+    for w in range(workers):
+        if held[w][0] < total:
+            held[w][1] = nxt  # taken as the worker starts on its first task
+            nxt += 1
+            waiting.add(w)
+    running = []  # (end time, worker, z)
+    now = 0.0
+    finished = 0
+    while finished < total:
+        started = False
+        for w in sorted(waiting):
+            z, need = task(held[w][0])
+            if done[z] >= need:
+                heapq.heappush(running, (now + float(rng.exponential(1.0)), w, z))
+                waiting.discard(w)
+                started = True
+        if not running:
+            raise AssertionError(f"deadlock with {len(waiting)} CTAs waiting, {finished} of {total} tasks done")
+        if started:
+            continue
+        now, w, z = heapq.heappop(running)
+        done[z] += 1
+        finished += 1
+        t = held[w][1]
+        held[w] = [t, None]
+        if t < total:
+            held[w][1] = nxt
+            nxt += 1
+            waiting.add(w)
+    return done
+
+
+@pytest.mark.parametrize("workers", [1, 3, 16, 64])
+def test_persistent_protocol_completes(L, workers):
+    """Every task only depends on tasks before it in the list, and the
+    kernel's take-one-ahead protocol finishes the whole list for any number
+    of CTAs (no deadlock), each matrix ending with all its tasks counted."""
+    orders = [int(v) for v in inputs.batch_orders(120, seed=inputs.SEED_BASE + 31, lo=32, hi=512)] + [1, 5, 33]
+    st = stages_of(L, orders, 0)
+    # dependency counts are the matrix's tasks of earlier stages of its bucket,
+    # all of which come earlier in the list
+    seen = {}
+    for kind, first, count, tiles, need in st:
+        assert need == seen.get(first, 0)
+        seen[first] = seen.get(first, 0) + tiles
+    done = simulate(st, workers, seed=workers)
+    per_matrix = {}
+    for kind, first, count, tiles, need in st:
+        for z in range(first, first + count):
+            per_matrix[z] = per_matrix.get(z, 0) + tiles
+    assert all(done[z] == v for z, v in per_matrix.items())
+    assert len(per_matrix) == len(orders)
+
+
+def test_protocol_simulation_catches_a_bad_order(L):
+    """The simulation is not vacuous: a list whose second stage of a bucket
+    comes before its first (a task waiting on tasks after it) deadlocks."""
+    st = stages_of(L, [96, 96, 200], 0)
+    bad = st.copy()
+    first_rows = [i for i in range(len(bad)) if bad[i, 1] == bad[0, 1]]
+    i0, i1 = first_rows[0], first_rows[1]
+    bad[[i0, i1]] = bad[[i1, i0]]
+    with pytest.raises(AssertionError, match="deadlock"):
+        simulate(bad, 1, seed=0)
