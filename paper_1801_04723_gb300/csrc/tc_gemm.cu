@@ -184,11 +184,11 @@ struct Epi {
 // accumulators belong to a CTA pair whose MMA issuer waits on the even
 // CTA's tempty barriers (cluster addresses tempty_c0 / tempty_c1); the
 // tfull barriers are this CTA's own (the issuer multicasts its commits).
-template <int BN, int HALF, bool PAIR, bool TMEM_SUMS = true, int DRAIN = 32>
+template <int BN, int HALF, bool PAIR, bool TMEM_SUMS = true, int DRAIN = 32, bool PACK = false>
 __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl* ctl, volatile int* abort,
                                                  uint32_t lane_addr, int half, int grow, int col0,
                                                  int nchunks_per_pair, int lane, uint32_t tempty_c0,
-                                                 uint32_t tempty_c1, int z, int& chunk) {
+                                                 uint32_t tempty_c1, int z, int& chunk, int pack = 1) {
     const bool row_ok = grow < p.M;
     // the sum of squares covers the leading sum_order x sum_order block only
     const int so = p.sum_order ? p.sum_order[z] : 0x7fffffff;
@@ -205,7 +205,11 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
     bool first_flush = true, ok = true;
     const int* col_exp = p.col_exp ? p.col_exp + (p.batch ? (int64_t)z * p.N : 0) : nullptr;
     const int erow = (p.row_exp && row_ok) ? p.row_exp[(p.batch ? (int64_t)z * p.M : 0) + grow] : 0;
-    for (int q = 0; q < p.num_pairs && ok; q++) {
+    // a run covers chunk c of pairs q .. q1-1 (several pairs of one weight
+    // when pack > 1: their products then share the run's exact sum)
+    for (int q = 0, q1 = 1; q < p.num_pairs && ok; q = q1, q1 = q + 1) {
+        if constexpr (PACK)
+            while (q1 < p.num_pairs && q1 - q < pack && p.pg[q1] == p.pg[q]) q1++;
         for (int c = 0; c < nchunks_per_pair && ok; c++) {
             const int buf = chunk & 1;
             const uint32_t use = (uint32_t)(chunk >> 1);
@@ -243,9 +247,8 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
             }
             chunk++;
             since_flush++;
-            const bool group_end =
-                (c == nchunks_per_pair - 1) && (q == p.num_pairs - 1 || p.pg[q + 1] != p.pg[q]);
-            const bool last = (c == nchunks_per_pair - 1) && (q == p.num_pairs - 1);
+            const bool group_end = (c == nchunks_per_pair - 1) && (q1 == p.num_pairs || p.pg[q1] != p.pg[q]);
+            const bool last = (c == nchunks_per_pair - 1) && (q1 == p.num_pairs);
             if (group_end || since_flush >= FLUSH_LIMIT) {
                 // acc * 2^(e_row + e_col + shift) is built from the integer's
                 // bits (exact, no FP64 arithmetic); the running FP64 sum of
@@ -326,7 +329,9 @@ __device__ __forceinline__ double exact_epilogue(const TcGemmParams& p, SmemCtl*
 // one tile overlaps the MMAs of the next in the other TMEM accumulator and
 // the set-up (barriers, TMEM, tensor maps) is paid once per SM; otherwise
 // one CTA per tile (blockIdx.x) and problem (blockIdx.y).
-template <int BN, bool EXACT, int EPI_WARPS, bool PERSIST = false>
+// PACK (exact mode, K within one run): consecutive slice pairs of one
+// weight share a run while their products fit in it.
+template <int BN, bool EXACT, int EPI_WARPS, bool PERSIST = false, bool PACK = false>
 __global__ void __maxnreg__(Epi<EPI_WARPS>::MAXREG)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const TcGemmParams p) {
@@ -384,6 +389,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int KB = (p.K + BK - 1) / BK;
     const int chunk_kb = EXACT ? p.chunk_kb : KB;
     const int nchunks_per_pair = (KB + chunk_kb - 1) / chunk_kb;
+    // exact mode, K within one run: consecutive pairs of one weight share a
+    // run while the run holds at most chunk_kb k-blocks of products (the sum
+    // stays an integer of magnitude <= 2^24), which divides the drains
+    const int pack = (PACK && nchunks_per_pair == 1) ? max(1, chunk_kb / KB) : 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -500,6 +509,18 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             ok = consume(d, kb == 0 && q == 0, min(KS, KB - kb));
                     if (ok) mma_commit(&ctl->tfull[buf]);
                     chunk++;
+                } else if constexpr (PACK) {
+                    // pairs q .. q1-1 of one weight share a run (one chunk each: K fits a run)
+                    for (int q = 0, q1 = 1; q < p.num_pairs && ok; q = q1, q1 = q + 1) {
+                        while (q1 < p.num_pairs && q1 - q < pack && p.pg[q1] == p.pg[q]) q1++;
+                        int buf = 0;
+                        ok = begin_chunk(buf);
+                        const uint32_t d = tmem_base + (uint32_t)(buf * BN);
+                        for (int qq = q; qq < q1 && ok; qq++)
+                            for (int kb = 0; kb < KB && ok; kb += KS) ok = consume(d, qq == q && kb == 0, min(KS, KB - kb));
+                        if (ok) mma_commit(&ctl->tfull[buf]);
+                        chunk++;
+                    }
                 } else {
                     for (int q = 0; q < p.num_pairs && ok; q++)
                         for (int c = 0; c < nchunks_per_pair && ok; c++) {
@@ -572,8 +593,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 chunk++;
                 if (!ok) break;
             } else {
-                sumsq = exact_epilogue<BN, HALF, false, TMEM_SUMS, (EPI_WARPS >= 16 ? 16 : 32)>(
-                    p, ctl, abort, lane_addr, half, grow, col0, nchunks_per_pair, lane, 0u, 0u, z, chunk);
+                sumsq = exact_epilogue<BN, HALF, false, TMEM_SUMS, (EPI_WARPS >= 16 ? 16 : 32), PACK>(
+                    p, ctl, abort, lane_addr, half, grow, col0, nchunks_per_pair, lane, 0u, 0u, z, chunk, pack);
             }
             if (p.sumsq) {
 #pragma unroll
@@ -1190,19 +1211,31 @@ int launch_impl(const TcOperand& a, const TcOperand& b, const TcGemmParams& p, c
     static PerDeviceOnce attrs;
     auto kern = tc_gemm_kernel<BN, EXACT, EPI_WARPS, false>;
     auto kern_p = tc_gemm_kernel<BN, EXACT, EPI_WARPS, true>;
+    auto kern_k = tc_gemm_kernel<BN, EXACT, EPI_WARPS, false, EXACT>;
     rc = attrs.run([&]() -> int {
         SPIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         SPIN_CUDA_TRY(cudaFuncSetAttribute(kern_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SPIN_CUDA_TRY(cudaFuncSetAttribute(kern_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         return SPIN_OK;
     });
     if (rc) return rc;
     const int64_t tiles = (int64_t)((p.N + BN - 1) / BN) * ((p.M + BM - 1) / BM);
     if (tiles > INT32_MAX) return SPIN_ERR_INVALID_ARG;
+    // exact products whose K fits one run take the packing form: two or more
+    // slice pairs per run when K fits half a run, and one chunk per pair
+    // without the chunk loop otherwise (the mixed batch of 4096 matrices:
+    // 192.1 against 207.3 ms).  Longer K keeps the other form: the packing
+    // form's registers spill more, and the n = 32768 residual ran 1.7x
+    // slower in it.
+    const int KB = (p.K + BK - 1) / BK;
+    const bool pack = EXACT && KB <= p.chunk_kb;
     if (use_persistent_tiles(EXACT)) {
         // one CTA per SM (the ring takes most of the shared memory), each
         // walking every gridDim.x-th tile of all problems
         const int64_t grid = std::min<int64_t>(tiles * nz, sm_count());
         kern_p<<<dim3((unsigned)grid, 1), Epi<EPI_WARPS>::THREADS, smem, s>>>(ta, tb, p);
+    } else if (pack) {
+        kern_k<<<dim3((unsigned)tiles, (unsigned)nz), Epi<EPI_WARPS>::THREADS, smem, s>>>(ta, tb, p);
     } else {
         kern<<<dim3((unsigned)tiles, (unsigned)nz), Epi<EPI_WARPS>::THREADS, smem, s>>>(ta, tb, p);
     }
