@@ -433,7 +433,10 @@ int spin_schedule_stats(spin_stream_t stream, int64_t* replays, int64_t* nodes);
 int spin_sync(spin_stream_t stream, spin_info* info);
 
 /* Device workspace, in bytes, that spin_invert_ex needs for this order and
- * these options (the value to pass as opts->workspace_bytes). */
+ * these options (the value to pass as opts->workspace_bytes); it depends on
+ * opts->schedule (the two-stream schedule keeps II per level and, in the
+ * mixed forms, a second split arena).  0 for an order below 1, a leaf out
+ * of range or a schedule outside 0..2. */
 size_t spin_workspace_bytes(int64_t n, const spin_opts* opts);
 
 /* The leaf order the library picks for n and a precision when leaf = 0:

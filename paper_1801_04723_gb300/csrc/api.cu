@@ -966,6 +966,7 @@ int spin_autotune_leaf(int64_t n, int precision, const int* candidates, int ncan
 size_t spin_workspace_bytes(int64_t n, const spin_opts* opts) {
     spin_opts o = opts ? *opts : spin_opts_default();
     if (n < 1) return 0;
+    if (o.schedule < SPIN_SCHEDULE_DEFAULT || o.schedule > SPIN_SCHEDULE_PERSISTENT) return 0;
     const int64_t leaf = resolve_leaf(n, o.leaf, o.precision);
     if (leaf < 1 || leaf > kMaxLeaf) return 0;
     return workspace_bytes_for(n, leaf, o);

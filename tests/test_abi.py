@@ -159,3 +159,32 @@ def test_cost_model_shape(L):
     r = spin.model_seconds(16384, 256) / spin.model_seconds(8192, 256)
     assert 7.0 < r < 8.0
     assert spin.model_seconds(100, 64, precision="bf16x3") == -1.0
+
+
+def test_workspace_follows_the_schedule(L):
+    """Workspace sizing per schedule (host logic): one stream needs T and S
+    per level, n1 n2 + n2^2 = n^2 / 2 for n = 2^p, i.e. n^2 (1/2)(1 + 1/4 +
+    ...) down to the leaf; the two-stream schedule adds II (n2 n1) per level,
+    3 n^2 / 4.  The plain method takes the second stream up to order 8192
+    by default, the mixed forms up to 16384, and everywhere when forced."""
+    n, leaf = 1024, 128
+    levels = [n, n // 2, n // 4]  # orders above the leaf
+    one = 8 * sum(m * m // 2 for m in levels)
+    two = 8 * sum(3 * m * m // 4 for m in levels)
+    assert spin.workspace_bytes(n, leaf=leaf, schedule="lockstep") == one
+    assert spin.workspace_bytes(n, leaf=leaf, schedule="default") == two
+    assert spin.workspace_bytes(n, leaf=leaf, schedule="persistent") == two
+    big = 16384
+    assert spin.workspace_bytes(big, leaf=leaf, schedule="default") == \
+        spin.workspace_bytes(big, leaf=leaf, schedule="lockstep")
+    assert spin.workspace_bytes(big, leaf=leaf, schedule="persistent") > \
+        spin.workspace_bytes(big, leaf=leaf, schedule="lockstep")
+    for m in (1024, 16384):
+        mixed = {s: spin.workspace_bytes(m, leaf=leaf, precision="bf16x3", schedule=s)
+                 for s in ("lockstep", "default", "persistent")}
+        assert mixed["default"] == mixed["persistent"] > mixed["lockstep"]
+    assert spin.workspace_bytes(32768, leaf=leaf, precision="bf16x3", schedule="default") == \
+        spin.workspace_bytes(32768, leaf=leaf, precision="bf16x3", schedule="lockstep")
+    # a schedule outside 0..2 is refused: no workspace size
+    o = binding.make_opts(schedule=3)
+    assert L.spin_workspace_bytes(1024, ctypes.byref(o)) == 0
